@@ -1,0 +1,198 @@
+/*
+ * gslens — general spherical harmonic transforms for CMB lensing on GB300.
+ *
+ * C ABI of the CUDA library libgslens.so.  The operations are those of
+ * Reinecke, Belkner & Carron, "Improved CMB (de-)lensing using general
+ * spherical harmonic transforms" (arXiv:2304.10431):
+ *
+ *   forward  (Sect. 2, Eq. "forward"; spin s > 0: Eq. "forwardpol")
+ *       spin 0: T_i        =                sum_lm a_lm          Y_lm(n'_i)
+ *       spin s: (Q+iU)_i   = - e^{i s chi_i} sum_lm (G+iC)_lm   sY_lm(n'_i)
+ *   adjoint  (Sect. 2, Eq. "adjoint"; spin s: the pair of equations and the
+ *             G/C decomposition that follow Eq. "forwardpol")
+ *       spin 0: a_lm = sum_i T_i Y*_lm(n'_i)
+ *       spin s: +-sA_lm = sum_i e^{-+ i s chi_i} (Q +- iU)_i +-sY*_lm(n'_i),
+ *               G = -(sA + (-1)^s (-s)A)/2,  C = -(sA - (-1)^s (-s)A)/(2i)
+ *
+ * computed as in Sect. 3: Legendre synthesis on an equiangular grid with a
+ * ring on each pole, doubling of the sphere onto a torus, 2D FFT with kernel
+ * deconvolution and zero padding, and non-uniform FFT interpolation (type 2);
+ * the adjoint runs type-1 spreading, FFT, folding and adjoint synthesis.
+ *
+ * Conventions.
+ *   - a_lm storage: index(l, m) = m (2 lmax + 1 - m) / 2 + l for
+ *     0 <= m <= mmax, m <= l <= lmax; complex interleaved (re, im).  Element
+ *     type: float (LENS_FP32) or double (LENS_FP64).  Real fields:
+ *     a_{l,-m} = (-1)^m conj(a_lm).  For spin s the two components G and C are
+ *     stored one after the other: [2][nalm] complex.
+ *   - Y_lm orthonormal with the Condon-Shortley phase; spin-weighted
+ *     sY_lm = sqrt((l-s)!/(l+s)!) eth^s Y_lm (equivalently
+ *     (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta) e^{i m phi}).
+ *   - Maps: real, [ncomp][npoints] (spin 0: T; spin s: Q then U), element
+ *     type float or double as above.
+ *   - Points: double theta in [0, pi], any finite phi, optional chi (the spin
+ *     phase of Fig. 1; NULL = 0), always FP64 on input.
+ *   - The adjoint returns m >= 0 only.  With the real-field inner product
+ *     <a,b> = sum_l Re(a_l0 conj b_l0) + 2 sum_{m>0} Re(a_lm conj b_lm) it is
+ *     the exact transpose of the forward operator.
+ *
+ * Ownership and threading.
+ *   - All buffer arguments are raw pointers; the caller owns them.  "_d"
+ *     pointers are CUDA device pointers on the device that was current when
+ *     the plan was created; "_h" pointers are host memory (pinned or not).
+ *   - A plan owns its sorted point tables, tables and workspace (device
+ *     memory).  One plan may be used by one call at a time; calls are
+ *     asynchronous on the given stream (NULL: the plan's stream) unless stated.
+ *   - Outputs are overwritten, never accumulated.
+ *
+ * Errors.  Every function returns a lens_status.  The status of the last
+ * failing call on the calling thread and a one-line message are kept
+ * (lens_get_last_error, lens_last_error_message).  No function aborts the
+ * process or traps on the GPU.
+ */
+#ifndef GSLENS_H
+#define GSLENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LENS_OK = 0,
+    LENS_ERR_INVALID = 1,   /* bad argument (sizes, spin, NULL pointer, ...) */
+    LENS_ERR_DOMAIN = 2,    /* a coordinate is not finite or theta is outside [0, pi] */
+    LENS_ERR_PRECISION = 3, /* epsilon not reachable at this precision */
+    LENS_ERR_NOMEM = 4,     /* device or host allocation failed */
+    LENS_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+    LENS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+    LENS_ERR_UNSUPPORTED = 7 /* size outside what this build handles (see message) */
+} lens_status;
+
+typedef enum { LENS_FP32 = 0, LENS_FP64 = 1 } lens_prec;
+
+typedef struct lens_plan_s *lens_plan;
+
+/* Optional overrides for lens_plan_create_ex; zero fields mean "choose". */
+typedef struct {
+    double sigma;   /* oversampling factor of the NUFFT grid (1.2 .. 2.5) */
+    int W;          /* kernel support in grid cells (4 .. 16) */
+    double beta;    /* ES kernel shape parameter */
+    int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
+} lens_plan_params;
+
+typedef struct {
+    int lmax, mmax, spin, prec;
+    int64_t npoints;
+    double epsilon;
+    int ntheta;         /* equiangular rings, poles included (Sect. 3 "synthesis") */
+    int ntheta_fft;     /* 2 ntheta - 2, length of the doubled theta transform */
+    int n1, n2;         /* oversampled torus (theta, phi) */
+    int W;              /* kernel support */
+    double beta, sigma; /* ES kernel exp(beta (sqrt(1 - (2z/W)^2) - 1)), oversampling */
+    int rows_kept;      /* torus rows stored (theta in [0, pi] plus kernel halo) */
+    int row_pitch;      /* grid row stride in elements */
+    size_t workspace_bytes;    /* per-call work buffers */
+    size_t plan_bytes;         /* point tables and coefficient tables */
+} lens_plan_info_t;
+
+/*
+ * Create a plan for one geometry (Sect. 3: the geometry is reused by many
+ * maps, so everything that depends only on it is prepared here).
+ *   out        receives the plan.
+ *   lmax, mmax band limit (0 <= mmax <= lmax).
+ *   spin       0, or s >= 1 (s <= lmax).
+ *   npoints    number of points (>= 0).
+ *   theta_d, phi_d   device double[npoints] deflected coordinates.
+ *   chi_d      device double[npoints] spin phase, or NULL (ignored for spin 0).
+ *   epsilon    target relative accuracy (Sect. 4, eps_eff); FP32 plans accept
+ *              epsilon >= 1e-6, FP64 plans epsilon >= 1e-13.
+ *   prec       LENS_FP32 or LENS_FP64.
+ *   flags      reserved, must be 0.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Synchronises the stream once (coordinate validation).  LENS_ERR_DOMAIN if a
+ * coordinate is not finite or theta is outside [0, pi].
+ */
+int lens_plan_create(lens_plan *out, int lmax, int mmax, int spin, int64_t npoints,
+                     const double *theta_d, const double *phi_d, const double *chi_d,
+                     double epsilon, int prec, unsigned flags, void *stream);
+
+/* As lens_plan_create, with explicit kernel / grid parameters (NULL = none). */
+int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t npoints,
+                        const double *theta_d, const double *phi_d, const double *chi_d,
+                        double epsilon, int prec, unsigned flags, void *stream,
+                        const lens_plan_params *params);
+
+int lens_plan_destroy(lens_plan p);
+int lens_plan_info(lens_plan p, lens_plan_info_t *info);
+
+/*
+ * Forward lensing (Sect. 2 Eq. "forward" / "forwardpol"; Sect. 3 steps
+ * synthesis, doubling, FFT, NUFFT).
+ *   alm_d  device [nmaps][ncomp][nalm] complex (ncomp = 1 for spin 0, 2 for spin s)
+ *   map_d  device [nmaps][ncomp][npoints] real
+ * Entries with l < spin are ignored.  Imaginary parts of m = 0 entries are
+ * ignored (real fields).
+ */
+int lens_synthesis(lens_plan p, const void *alm_d, void *map_d, int nmaps, void *stream);
+
+/*
+ * Adjoint lensing (Sect. 2 Eq. "adjoint" and its spin-s form; Sect. 3 adjoint
+ * steps NUFFT type 1, FFT, undoubling, adjoint synthesis).
+ *   map_d  device [nmaps][ncomp][npoints] real
+ *   alm_d  device [nmaps][ncomp][nalm] complex (written)
+ */
+int lens_adjoint(lens_plan p, const void *map_d, void *alm_d, int nmaps, void *stream);
+
+/*
+ * The same two operations on host buffers: the inputs are copied to the
+ * device, the transform runs, the outputs are copied back; returns after the
+ * stream has finished.  Pinned host memory gives full copy bandwidth.
+ */
+int lens_synthesis_host(lens_plan p, const void *alm_h, void *map_h, int nmaps, void *stream);
+int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream);
+
+/*
+ * Legendre step alone (Sect. 3 "synthesis" restricted to the theta direction):
+ * ring Fourier coefficients on the plan's equiangular rings
+ * theta_j = j pi / (ntheta - 1), j = 0..ntheta-1.
+ *   ring_d  device complex [ncol][ntheta], ncol = mmax + 1 (spin 0, column m)
+ *           or 2 mmax + 1 (spin s, column m + mmax); spin 0 holds
+ *           sum_l a_lm lambda_lm(theta_j), spin s holds
+ *           -sum_l (G + iC)_lm s lambda_lm(theta_j) (the sign of Eq. "forwardpol").
+ */
+int lens_ring_synthesis(lens_plan p, const void *alm_d, void *ring_d, void *stream);
+
+/* Transpose of lens_ring_synthesis: a_lm (spin 0) or G, C (spin s, with the
+ * G/C decomposition of Sect. 2) from ring coefficients of the same layout. */
+int lens_ring_adjoint(lens_plan p, const void *ring_d, void *alm_d, void *stream);
+
+/*
+ * Pointing (Sect. 3, the unlensed-direction formula; Fig. 1 for chi):
+ *   n' = cos(a) n + sin(a)/a (a_theta e_theta + a_phi e_phi),  a = |alpha|,
+ *   chi = beta - beta' (angle of the geodesic at n minus its angle at n',
+ *   both from e_theta towards e_phi), wrapped to (-pi, pi].
+ * All arrays device double[n]; chi_out_d may be NULL.  theta' in [0, pi],
+ * phi' in [0, 2 pi).
+ */
+int lens_pointing(int64_t n, const double *theta_d, const double *phi_d,
+                  const double *alpha_theta_d, const double *alpha_phi_d,
+                  double *theta_out_d, double *phi_out_d, double *chi_out_d, void *stream);
+
+/* Number of a_lm for (lmax, mmax). */
+int64_t lens_nalm(int lmax, int mmax);
+
+const char *lens_status_string(int status);
+int lens_get_last_error(void);
+const char *lens_last_error_message(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int lens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSLENS_H */

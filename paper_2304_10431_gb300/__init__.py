@@ -1,0 +1,202 @@
+"""gslens: general spherical harmonic transforms for CMB lensing on GB300.
+
+Python binding of libgslens (include/gslens.h).  Every step of the transform
+runs in the library's CUDA kernels; this module only marshals torch tensors
+into raw device pointers and sizes.  PyTorch provides device memory and streams.
+
+    plan = LensPlan(lmax, theta, phi, chi=None, spin=0, epsilon=1e-5, precision="fp32")
+    m = plan.synthesis(alm)    # forward lensing (Eq. "forward" / "forwardpol")
+    a = plan.adjoint(m)        # adjoint (Eq. "adjoint" and its spin-s form)
+
+a_lm layout: complex tensor [ncomp, nalm] (or [nmaps, ncomp, nalm]) with
+index(l, m) = m (2 lmax + 1 - m)/2 + l; ncomp = 1 (spin 0) or 2 (G, C).
+Maps: real tensor [ncomp, npoints] (or [nmaps, ncomp, npoints]).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import LensError, PlanInfo, PlanParams
+
+__all__ = ["LensPlan", "LensError", "pointing", "nalm", "lib_path"]
+
+_PREC = {"fp32": 0, "fp64": 1}
+
+
+def lib_path() -> str:
+    return _native.lib_path()
+
+
+def nalm(lmax: int, mmax: int | None = None) -> int:
+    return int(_native.load().lens_nalm(lmax, lmax if mmax is None else mmax))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_f64(x, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
+
+
+class LensPlan:
+    """One geometry (deflected points) at one band limit, spin and precision."""
+
+    def __init__(self, lmax: int, theta, phi, chi=None, spin: int = 0, mmax: int | None = None,
+                 epsilon: float = 1e-5, precision: str = "fp32", sigma: float | None = None,
+                 W: int | None = None, beta: float | None = None, ntheta: int | None = None,
+                 device=None, stream=None):
+        lib = _native.load()
+        if precision not in _PREC:
+            raise ValueError("precision must be 'fp32' or 'fp64'")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.lmax, self.mmax, self.spin = int(lmax), int(lmax if mmax is None else mmax), int(spin)
+        self.precision = precision
+        self.real_dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.complex_dtype = torch.complex64 if precision == "fp32" else torch.complex128
+        self.ncomp = 1 if self.spin == 0 else 2
+        with torch.cuda.device(self.device):
+            th = _dev_f64(theta, self.device)
+            ph = _dev_f64(phi, self.device)
+            ch = _dev_f64(chi, self.device) if (chi is not None and self.spin) else None
+            if th.numel() != ph.numel() or (ch is not None and ch.numel() != th.numel()):
+                raise ValueError("theta, phi (and chi) must have the same length")
+            self.npoints = int(th.numel())
+            prm = PlanParams(float(sigma or 0.0), int(W or 0), float(beta or 0.0), int(ntheta or 0))
+            handle = ctypes.c_void_p()
+            st = _stream_handle(stream)
+            rc = lib.lens_plan_create_ex(ctypes.byref(handle), self.lmax, self.mmax, self.spin, self.npoints,
+                                         th.data_ptr() if self.npoints else None,
+                                         ph.data_ptr() if self.npoints else None,
+                                         ch.data_ptr() if ch is not None else None, float(epsilon),
+                                         _PREC[precision], 0, st, ctypes.byref(prm))
+            _native.check(rc)
+        self._h = handle
+        self.nalm = nalm(self.lmax, self.mmax)
+        self.epsilon = float(epsilon)
+
+    # ------------------------------------------------------------ utilities
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _native.check(_native.load().lens_plan_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _native.load().lens_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _alm_arg(self, alm):
+        if not isinstance(alm, torch.Tensor) or alm.device != self.device:
+            raise TypeError("alm must be a CUDA tensor on the plan's device")
+        if alm.dtype != self.complex_dtype:
+            raise TypeError("alm must be %s for a %s plan" % (self.complex_dtype, self.precision))
+        alm = alm.contiguous()
+        if alm.shape[-1] != self.nalm or (alm.dim() >= 2 and alm.shape[-2] != self.ncomp) or \
+                (alm.dim() == 1 and self.ncomp != 1):
+            raise ValueError("alm must have shape [..., %d, %d]" % (self.ncomp, self.nalm))
+        nmaps = 1 if alm.dim() <= 2 else int(np.prod(alm.shape[:-2]))
+        return alm, nmaps
+
+    def _map_arg(self, m):
+        if not isinstance(m, torch.Tensor) or m.device != self.device:
+            raise TypeError("map must be a CUDA tensor on the plan's device")
+        if m.dtype != self.real_dtype:
+            raise TypeError("map must be %s for a %s plan" % (self.real_dtype, self.precision))
+        m = m.contiguous()
+        if m.shape[-1] != self.npoints or (m.dim() >= 2 and m.shape[-2] != self.ncomp) or \
+                (m.dim() == 1 and self.ncomp != 1):
+            raise ValueError("map must have shape [..., %d, %d]" % (self.ncomp, self.npoints))
+        nmaps = 1 if m.dim() <= 2 else int(np.prod(m.shape[:-2]))
+        return m, nmaps
+
+    # ------------------------------------------------------------ transforms
+    def synthesis(self, alm: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Forward lensing: a_lm -> values at the deflected points."""
+        alm, nmaps = self._alm_arg(alm)
+        lead = alm.shape[:-2] if alm.dim() > 2 else ()
+        if out is None:
+            out = torch.empty(*lead, self.ncomp, self.npoints, dtype=self.real_dtype, device=self.device)
+        _native.check(_native.load().lens_synthesis(self._h, alm.data_ptr(), out.data_ptr(), nmaps,
+                                                    _stream_handle(stream)))
+        return out
+
+    def adjoint(self, m: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Adjoint lensing: values at the deflected points -> a_lm (m >= 0)."""
+        m, nmaps = self._map_arg(m)
+        lead = m.shape[:-2] if m.dim() > 2 else ()
+        if out is None:
+            out = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+        _native.check(_native.load().lens_adjoint(self._h, m.data_ptr(), out.data_ptr(), nmaps,
+                                                  _stream_handle(stream)))
+        return out
+
+    def synthesis_host(self, alm_h, out_h=None, stream=None):
+        """Forward on host (CPU) tensors: copies in, transform, copies out (synchronous)."""
+        alm_h = torch.as_tensor(alm_h).to(self.complex_dtype).contiguous()
+        nmaps = 1 if alm_h.dim() <= 2 else int(np.prod(alm_h.shape[:-2]))
+        lead = alm_h.shape[:-2] if alm_h.dim() > 2 else ()
+        if out_h is None:
+            out_h = torch.empty(*lead, self.ncomp, self.npoints, dtype=self.real_dtype)
+        _native.check(_native.load().lens_synthesis_host(self._h, alm_h.data_ptr(), out_h.data_ptr(), nmaps,
+                                                         _stream_handle(stream)))
+        return out_h
+
+    def adjoint_host(self, m_h, out_h=None, stream=None):
+        m_h = torch.as_tensor(m_h).to(self.real_dtype).contiguous()
+        nmaps = 1 if m_h.dim() <= 2 else int(np.prod(m_h.shape[:-2]))
+        lead = m_h.shape[:-2] if m_h.dim() > 2 else ()
+        if out_h is None:
+            out_h = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype)
+        _native.check(_native.load().lens_adjoint_host(self._h, m_h.data_ptr(), out_h.data_ptr(), nmaps,
+                                                       _stream_handle(stream)))
+        return out_h
+
+    def ring_synthesis(self, alm: torch.Tensor, stream=None) -> torch.Tensor:
+        """Legendre step only: ring Fourier coefficients [ncol, ntheta] on the plan's rings."""
+        alm, _ = self._alm_arg(alm)
+        inf = self.info()
+        ncol = self.mmax + 1 if self.spin == 0 else 2 * self.mmax + 1
+        out = torch.empty(ncol, inf["ntheta"], dtype=self.complex_dtype, device=self.device)
+        _native.check(_native.load().lens_ring_synthesis(self._h, alm.data_ptr(), out.data_ptr(),
+                                                         _stream_handle(stream)))
+        return out
+
+    def ring_adjoint(self, ring: torch.Tensor, stream=None) -> torch.Tensor:
+        ring = ring.contiguous()
+        out = torch.empty(self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+        _native.check(_native.load().lens_ring_adjoint(self._h, ring.data_ptr(), out.data_ptr(),
+                                                       _stream_handle(stream)))
+        return out
+
+
+def pointing(theta: torch.Tensor, phi: torch.Tensor, alpha_theta: torch.Tensor, alpha_phi: torch.Tensor,
+             stream=None):
+    """Unlensed angles and spin phase from a deflection field (Sect. 3); FP64 CUDA tensors."""
+    n = theta.numel()
+    dev = theta.device
+    args = [x.to(dtype=torch.float64).contiguous() for x in (theta, phi, alpha_theta, alpha_phi)]
+    t2 = torch.empty(n, dtype=torch.float64, device=dev)
+    p2 = torch.empty_like(t2)
+    c2 = torch.empty_like(t2)
+    _native.check(_native.load().lens_pointing(n, *[a.data_ptr() for a in args], t2.data_ptr(), p2.data_ptr(),
+                                               c2.data_ptr(), _stream_handle(stream)))
+    return t2, p2, c2

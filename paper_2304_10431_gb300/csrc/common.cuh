@@ -1,0 +1,79 @@
+// Shared device helpers: complex arithmetic on float2/double2 and
+// double-float ("df32") arithmetic on pairs of FP32 numbers.
+//
+// df32 numbers represent x = h + l with |l| <= ulp(h)/2 after normalisation.
+// Products use the FMA error-free transform (p = a*b, e = fma(a, b, -p)),
+// sums use Knuth's two-sum; every rounding step is written with the
+// __f*_rn intrinsics so the compiler cannot contract or reassociate it.
+// The Legendre recursion of FP32 plans runs in df32 because a plain FP32
+// three-term recursion loses 1e-5..1e-3 relative accuracy at lmax ~ 4096
+// (rounding of the recursion state accumulates over thousands of steps),
+// while GB300's FP64 pipe is a small fraction of its FP32 rate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsl {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_of<T>::type;
+
+__host__ __device__ __forceinline__ float2 mkc(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ double2 mkc(double r, double i) { return make_double2(r, i); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { return mkc(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b)
+{
+    return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return mkc(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// multiply by +i or -i
+template <typename C> __host__ __device__ __forceinline__ C cmul_i(C a) { return mkc(-a.y, a.x); }
+template <typename C> __host__ __device__ __forceinline__ C cmul_mi(C a) { return mkc(a.y, -a.x); }
+
+// ------------------------------------------------------------------ df32
+struct df32 {
+    float h, l;
+};
+
+// a * b for df32 a, b (result not renormalised: |l| is small but may exceed ulp(h)/2)
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b)
+{
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return {p, e};
+}
+
+// a - b, renormalised (two-sum on the high parts, low parts added to the error)
+__device__ __forceinline__ df32 df_sub(df32 a, df32 b)
+{
+    float s = __fsub_rn(a.h, b.h);
+    float bb = __fsub_rn(s, a.h);
+    float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(-b.h, bb));
+    err = __fadd_rn(err, __fsub_rn(a.l, b.l));
+    float h = __fadd_rn(s, err);
+    float l = __fsub_rn(err, __fsub_rn(h, s));
+    return {h, l};
+}
+
+__device__ __forceinline__ df32 df_scale_pow2(df32 a, float p2) { return {a.h * p2, a.l * p2}; }
+
+// Status flags written by kernels (bitwise OR).  No kernel traps.
+enum : unsigned {
+    FLAG_DOMAIN = 1u,     // point coordinate not finite / theta outside [0, pi]
+    FLAG_OOB = 2u,        // an index check failed; the access was skipped
+};
+
+}  // namespace gsl

@@ -1,0 +1,258 @@
+// Shared-memory mixed-radix FFT used by the torus transforms (Sect. 3 "FFT").
+//
+// One CTA transforms one vector held in shared memory.  The algorithm is the
+// iterative decimation-in-time Cooley-Tukey scheme: the input is stored in
+// digit-reversed order (element i at position perm[i]); stage k combines
+// r_k sub-transforms of length L_{k-1} into length L_k = L_{k-1} r_k with
+// twiddles W_{L_k}^{j q}; the output comes out in natural order.  Within a
+// stage the butterflies touch disjoint positions, so one barrier per stage
+// suffices.  Radices 2, 3, 4, 5, 7, 8; odd radices use the symmetric-pair
+// form y_k = x_0 + sum_q (x_q + x_{p-q}) cos(2 pi qk/p) -+ i (x_q - x_{p-q}) sin(2 pi qk/p).
+//
+// DIR = -1: forward, sum x_n e^{-2 pi i nk/N};  DIR = +1: inverse (unnormalised).
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gsl {
+
+template <typename T> struct FftConst;
+#define GSL_FFT_CONSTS(T)                                                                                  \
+    template <> struct FftConst<T> {                                                                       \
+        static __device__ __forceinline__ T c3() { return T(-0.5); }                                       \
+        static __device__ __forceinline__ T s3() { return T(0.866025403784438646764); }                     \
+        static __device__ __forceinline__ T c5(int t)                                                      \
+        {                                                                                                  \
+            return (t == 1 || t == 4) ? T(0.309016994374947424102) : T(-0.809016994374947424102);         \
+        }                                                                                                  \
+        static __device__ __forceinline__ T s5(int t)                                                      \
+        {                                                                                                  \
+            return t == 1 ? T(0.951056516295153572116)                                                     \
+                          : t == 2 ? T(0.587785252292473129169)                                            \
+                                   : t == 3 ? T(-0.587785252292473129169) : T(-0.951056516295153572116);   \
+        }                                                                                                  \
+        static __device__ __forceinline__ T c7(int t)                                                      \
+        {                                                                                                  \
+            return (t == 1 || t == 6) ? T(0.623489801858733530525)                                         \
+                                      : (t == 2 || t == 5) ? T(-0.222520933956314404289)                   \
+                                                           : T(-0.900968867902419126236);                  \
+        }                                                                                                  \
+        static __device__ __forceinline__ T s7(int t)                                                      \
+        {                                                                                                  \
+            return t == 1 ? T(0.781831482468029808708)                                                     \
+                          : t == 2 ? T(0.974927912181823607018)                                            \
+                                   : t == 3 ? T(0.433883739117558120476)                                   \
+                                            : t == 4 ? T(-0.433883739117558120476)                         \
+                                                     : t == 5 ? T(-0.974927912181823607018)                \
+                                                              : T(-0.781831482468029808708);               \
+        }                                                                                                  \
+        static __device__ __forceinline__ T r2() { return T(0.707106781186547524401); }                    \
+    };
+GSL_FFT_CONSTS(float)
+GSL_FFT_CONSTS(double)
+#undef GSL_FFT_CONSTS
+
+// multiply by -i (DIR=-1) or +i (DIR=+1)
+template <int DIR, typename C> __device__ __forceinline__ C mul_dir_i(C a)
+{
+    return DIR < 0 ? cmul_mi(a) : cmul_i(a);
+}
+
+template <int R, int DIR, typename T> struct SmallDft;
+
+template <int DIR, typename T> struct SmallDft<2, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        cplx<T> a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    }
+};
+
+template <int DIR, typename T> struct SmallDft<4, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        cplx<T> s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
+        cplx<T> s13 = cadd(x[1], x[3]), d13 = mul_dir_i<DIR>(csub(x[1], x[3]));
+        x[0] = cadd(s02, s13);
+        x[2] = csub(s02, s13);
+        x[1] = cadd(d02, d13);
+        x[3] = csub(d02, d13);
+    }
+};
+
+template <int DIR, typename T> struct SmallDft<8, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        cplx<T> e[4] = {x[0], x[2], x[4], x[6]};
+        cplx<T> o[4] = {x[1], x[3], x[5], x[7]};
+        SmallDft<4, DIR, T>::run(e);
+        SmallDft<4, DIR, T>::run(o);
+        const T r = FftConst<T>::r2();
+        // W8^1 = (1 + DIR i) r,  W8^2 = DIR i,  W8^3 = (-1 + DIR i) r
+        cplx<T> t1 = mkc(r * (o[1].x - DIR * o[1].y), r * (o[1].y + DIR * o[1].x));
+        cplx<T> t2 = mul_dir_i<DIR>(o[2]);
+        cplx<T> t3 = mkc(r * (-o[3].x - DIR * o[3].y), r * (-o[3].y + DIR * o[3].x));
+        x[0] = cadd(e[0], o[0]);
+        x[4] = csub(e[0], o[0]);
+        x[1] = cadd(e[1], t1);
+        x[5] = csub(e[1], t1);
+        x[2] = cadd(e[2], t2);
+        x[6] = csub(e[2], t2);
+        x[3] = cadd(e[3], t3);
+        x[7] = csub(e[3], t3);
+    }
+};
+
+template <int DIR, typename T> struct SmallDft<3, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        cplx<T> s = cadd(x[1], x[2]), d = csub(x[1], x[2]);
+        cplx<T> a = mkc(x[0].x + FftConst<T>::c3() * s.x, x[0].y + FftConst<T>::c3() * s.y);
+        cplx<T> b = cscale(d, FftConst<T>::s3());
+        // forward: y1 = a - i b, y2 = a + i b
+        cplx<T> ib = mul_dir_i<DIR>(b);  // DIR=-1: -i b
+        x[0] = cadd(x[0], s);
+        x[1] = cadd(a, ib);
+        x[2] = csub(a, ib);
+    }
+};
+
+template <int P, int DIR, typename T> struct OddDft {
+    static __device__ __forceinline__ T cs(int t) { return P == 5 ? FftConst<T>::c5(t) : FftConst<T>::c7(t); }
+    static __device__ __forceinline__ T sn(int t) { return P == 5 ? FftConst<T>::s5(t) : FftConst<T>::s7(t); }
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        constexpr int H = (P - 1) / 2;
+        cplx<T> s[H], d[H];
+        cplx<T> y0 = x[0];
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            s[q - 1] = cadd(x[q], x[P - q]);
+            d[q - 1] = csub(x[q], x[P - q]);
+            y0 = cadd(y0, s[q - 1]);
+        }
+        cplx<T> out[P];
+        out[0] = y0;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            cplx<T> a = x[0], b = mkc(T(0), T(0));
+#pragma unroll
+            for (int q = 1; q <= H; ++q) {
+                const int t = (q * k) % P;
+                const T c = cs(t), sv = sn(t);
+                a.x += c * s[q - 1].x; a.y += c * s[q - 1].y;
+                b.x += sv * d[q - 1].x; b.y += sv * d[q - 1].y;
+            }
+            cplx<T> ib = mul_dir_i<DIR>(b);
+            out[k] = cadd(a, ib);
+            out[P - k] = csub(a, ib);
+        }
+#pragma unroll
+        for (int k = 0; k < P; ++k) x[k] = out[k];
+    }
+};
+template <int DIR, typename T> struct SmallDft<5, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { OddDft<5, DIR, T>::run(x); }
+};
+template <int DIR, typename T> struct SmallDft<7, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { OddDft<7, DIR, T>::run(x); }
+};
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void fft_stage(cplx<T> *buf, int N, int Lp, const cplx<T> *__restrict__ tw)
+{
+    const int L = Lp * R;
+    const int nb = N / R;
+    const int tstep = N / L;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int g = b / Lp;
+        const int j = b - g * Lp;
+        const int base = g * L + j;
+        cplx<T> x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = buf[base + q * Lp];
+        if (j != 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                cplx<T> w = __ldg(tw + (int64_t)j * q * tstep);
+                x[q] = DIR < 0 ? cmul(x[q], w) : cmulc(x[q], w);
+            }
+        }
+        SmallDft<R, DIR, T>::run(x);
+#pragma unroll
+        for (int q = 0; q < R; ++q) buf[base + q * Lp] = x[q];
+    }
+}
+
+// Full transform of buf (digit-reversed input -> natural output).  Ends with
+// a barrier.
+template <int DIR, typename T> __device__ void fft_smem(cplx<T> *buf, const FftDesc &d)
+{
+    const cplx<T> *tw = (const cplx<T> *)d.tw;
+    int Lp = 1;
+    for (int st = 0; st < d.nst; ++st) {
+        const int r = d.radix[st];
+        switch (r) {
+        case 2: fft_stage<2, DIR, T>(buf, d.n, Lp, tw); break;
+        case 3: fft_stage<3, DIR, T>(buf, d.n, Lp, tw); break;
+        case 4: fft_stage<4, DIR, T>(buf, d.n, Lp, tw); break;
+        case 5: fft_stage<5, DIR, T>(buf, d.n, Lp, tw); break;
+        case 7: fft_stage<7, DIR, T>(buf, d.n, Lp, tw); break;
+        default: fft_stage<8, DIR, T>(buf, d.n, Lp, tw); break;
+        }
+        Lp *= r;
+        __syncthreads();
+    }
+}
+
+// Decimation-in-frequency variant (the transpose of fft_smem): natural-order
+// input, output element i at position perm[i].  Stages run in reverse order
+// and the twiddles are applied after each small DFT.  Ends with a barrier.
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void fft_stage_dif(cplx<T> *buf, int N, int Lp, const cplx<T> *__restrict__ tw)
+{
+    const int L = Lp * R;
+    const int nb = N / R;
+    const int tstep = N / L;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int g = b / Lp;
+        const int j = b - g * Lp;
+        const int base = g * L + j;
+        cplx<T> x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = buf[base + q * Lp];
+        SmallDft<R, DIR, T>::run(x);
+        if (j != 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                cplx<T> w = __ldg(tw + (int64_t)j * q * tstep);
+                x[q] = DIR < 0 ? cmul(x[q], w) : cmulc(x[q], w);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) buf[base + q * Lp] = x[q];
+    }
+}
+
+template <int DIR, typename T> __device__ void fft_smem_dif(cplx<T> *buf, const FftDesc &d)
+{
+    const cplx<T> *tw = (const cplx<T> *)d.tw;
+    int Lp = d.n;
+    for (int st = d.nst - 1; st >= 0; --st) {
+        const int r = d.radix[st];
+        Lp /= r;
+        switch (r) {
+        case 2: fft_stage_dif<2, DIR, T>(buf, d.n, Lp, tw); break;
+        case 3: fft_stage_dif<3, DIR, T>(buf, d.n, Lp, tw); break;
+        case 4: fft_stage_dif<4, DIR, T>(buf, d.n, Lp, tw); break;
+        case 5: fft_stage_dif<5, DIR, T>(buf, d.n, Lp, tw); break;
+        case 7: fft_stage_dif<7, DIR, T>(buf, d.n, Lp, tw); break;
+        default: fft_stage_dif<8, DIR, T>(buf, d.n, Lp, tw); break;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace gsl

@@ -1,0 +1,102 @@
+// Internal plan layout and kernel-launcher declarations of libgslens.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gslens.h"
+
+namespace gsl {
+
+constexpr int kMaxFftStages = 24;
+constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
+
+// One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
+// and the digit-reversal table (input element i is stored at position perm[i]).
+struct FftDesc {
+    int n = 0;
+    int nst = 0;
+    int radix[kMaxFftStages] = {0};
+    const void *tw = nullptr;   // float2[n] or double2[n]
+    const int *perm = nullptr;  // int[n]
+};
+
+// Per-ring tables of the equiangular grid, north half (theta <= pi/2).
+struct RingTab {
+    const double *x = nullptr;        // cos(theta_j)
+    const float2 *xdf = nullptr;      // cos(theta_j) as a df32 pair
+    const double *lsin2 = nullptr;    // log2 sin(theta_j / 2)  (-inf at the pole)
+    const double *lcos2 = nullptr;    // log2 cos(theta_j / 2)
+};
+
+struct Plan {
+    // problem
+    int lmax = 0, mmax = 0, spin = 0, prec = LENS_FP32;
+    int64_t npts = 0;
+    double eps = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    // geometry of the equiangular grid and the torus
+    int ntheta = 0;   // rings incl. poles
+    int nnorth = 0;   // rings with theta <= pi/2 (ring pairs)
+    int M = 0;        // 2 ntheta - 2
+    int N1 = 0, N2 = 0;
+    int W = 0;
+    double beta = 0, sigma = 0;
+    int r_lo = 0, R = 0;  // kept torus rows r in [r_lo, r_lo + R)
+    int pitch = 0;        // grid row stride (elements)
+    int ncol = 0;         // m columns: mmax+1 (spin 0) or 2 mmax + 1
+    int64_t nalm = 0;
+
+    // Legendre launch shape
+    int leg_rpt = 0, leg_warps = 0, leg_chunks = 0;
+
+    // tables (device)
+    void *rec_ab = nullptr;   // per alm index: df32 (Ah, Al, Bh, Bl) or double2 (A, B)
+    void *rec_c = nullptr;    // spin s: per alm index: float2 (Ch, Cl) or double
+    double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
+    RingTab rings;
+    void *w1 = nullptr;       // [2 lmax + 1]  1/psihat(2 pi k / N1), k = -lmax..lmax
+    void *w2 = nullptr;       // [ncol]        1/(M psihat(2 pi m / N2))
+    FftDesc fM, fN1, fN2;
+
+    // points, sorted by grid tile
+    uint32_t *cell = nullptr;  // row * pitch + col of the first tap
+    void *frac = nullptr;      // float2 / double2 (u - i0, v - j0)
+    int32_t *perm = nullptr;   // sorted -> user index
+    void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
+
+    // per-call workspace
+    void *ring = nullptr;      // [ncol][ntheta] complex
+    void *X = nullptr;         // [R][ncol] complex
+    void *grid = nullptr;      // [R][pitch] real (spin 0) or complex
+    unsigned *flags = nullptr; // device status flags
+
+    size_t plan_bytes = 0, work_bytes = 0;
+    void *allocs[64];
+    int nallocs = 0;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_rec_tables(Plan &p);
+cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st);
+cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st);
+cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st);
+cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st);
+cudaError_t launch_phi_fwd(const Plan &p, const void *X, void *grid, cudaStream_t st);
+cudaError_t launch_phi_adj(const Plan &p, const void *grid, void *X, cudaStream_t st);
+cudaError_t launch_interp(const Plan &p, const void *grid, void *map, cudaStream_t st);
+cudaError_t launch_spread(const Plan &p, const void *map, void *grid, cudaStream_t st);
+cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, const double *chi,
+                               cudaStream_t st, std::string &err);
+cudaError_t launch_pointing(int64_t n, const double *theta, const double *phi, const double *ath,
+                            const double *aph, double *theta_out, double *phi_out, double *chi_out,
+                            cudaStream_t st);
+
+size_t theta_smem_bytes(const Plan &p);
+size_t phi_smem_bytes(const Plan &p);
+
+}  // namespace gsl

@@ -1,0 +1,333 @@
+// Non-uniform FFT steps (Sect. 3 "NUFFT": type 2 for the forward operator,
+// type 1 for the adjoint) on the oversampled torus grid.
+//
+// Kernel: exponential of semicircle, psi(z) = exp(beta (sqrt(1 - (2z/W)^2) - 1))
+// for |z| < W/2 (grid units), zero outside.  A point at grid coordinates
+// (u, v) = (theta N1 / 2pi, phi N2 / 2pi) touches the W x W cells
+// i0 + a, j0 + b with i0 = ceil(u - W/2), j0 = ceil(v - W/2), a, b < W:
+//   type 2:  f = sum_ab psi(u - i0 - a) psi(v - j0 - b) g[i0 + a, j0 + b]
+//   type 1:  g[i0 + a, j0 + b] += psi(u - i0 - a) psi(v - j0 - b) f
+// The two use the same weights, so they are exact transposes.
+//
+// Points are prepared once per plan (Sect. 4: the geometry is reused): cell
+// offset into the row-padded grid, fractional offsets (u - i0, v - j0) from
+// FP64 coordinates, the spin phase e^{i s chi}, and a permutation that sorts
+// points by 16 x 32 grid tiles so that neighbouring threads share grid rows.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <cub/cub.cuh>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gsl {
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.141592653589793238462643383280;
+constexpr int kTileR = 16, kTileC = 32;
+
+__global__ void k_prep(const double *__restrict__ theta, const double *__restrict__ phi,
+                       const double *__restrict__ chi, int64_t n, int N1, int N2, int W, int r_lo, int R, int pitch,
+                       int spin, uint32_t *__restrict__ key, int32_t *__restrict__ idx, uint32_t *__restrict__ cell_u,
+                       double2 *__restrict__ frac_u, double2 *__restrict__ phase_u, unsigned *__restrict__ flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double th = theta[i], ph = phi[i];
+    bool bad = !(isfinite(th) && isfinite(ph)) || th < 0.0 || th > kPi;
+    if (bad) {
+        atomicOr(flags, FLAG_DOMAIN);
+        th = 0.0;
+        ph = 0.0;
+    }
+    ph = fmod(ph, kTwoPi);
+    if (ph < 0.0) ph += kTwoPi;
+    if (ph >= kTwoPi) ph = 0.0;
+    const double hw = 0.5 * W;
+    const double u = th * (N1 / kTwoPi);
+    const double v = ph * (N2 / kTwoPi);
+    const int i0 = (int)ceil(u - hw);
+    int j0 = (int)ceil(v - hw);
+    const double fu = u - i0, fv = v - j0;
+    if (j0 < 0) j0 += N2;
+    if (j0 >= N2) j0 -= N2;
+    int row = i0 - r_lo;
+    if (row < 0 || row > R - W) {  // cannot happen for theta in [0, pi]; guard the table
+        atomicOr(flags, FLAG_OOB);
+        row = row < 0 ? 0 : R - W;
+    }
+    cell_u[i] = (uint32_t)row * (uint32_t)pitch + (uint32_t)j0;
+    frac_u[i] = make_double2(fu, fv);
+    const int ntc = (N2 + kTileC - 1) / kTileC;
+    key[i] = (uint32_t)(row / kTileR) * (uint32_t)ntc + (uint32_t)(j0 / kTileC);
+    idx[i] = (int32_t)i;
+    if (spin) {
+        const double c = chi ? chi[i] : 0.0;
+        double sn, cs;
+        sincos(spin * c, &sn, &cs);
+        phase_u[i] = make_double2(cs, sn);
+    }
+}
+
+__global__ void k_gather_points(const int32_t *__restrict__ perm, int64_t n, const uint32_t *__restrict__ cell_u,
+                                const double2 *__restrict__ frac_u, const double2 *__restrict__ phase_u, int prec,
+                                int spin, uint32_t *__restrict__ cell, void *__restrict__ frac,
+                                void *__restrict__ phase)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t i = perm[p];
+    cell[p] = cell_u[i];
+    const double2 f = frac_u[i];
+    if (prec == LENS_FP32) ((float2 *)frac)[p] = make_float2((float)f.x, (float)f.y);
+    else ((double2 *)frac)[p] = f;
+    if (spin) {
+        const double2 ph = phase_u[i];
+        if (prec == LENS_FP32) ((float2 *)phase)[p] = make_float2((float)ph.x, (float)ph.y);
+        else ((double2 *)phase)[p] = ph;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta)
+{
+    const T t = z * twoW;
+    const T q = T(1) - t * t;
+    return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
+}
+
+template <typename T, int W, bool SPIN>
+__global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, const uint32_t *__restrict__ cell,
+                                                const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
+                                                const cplx<T> *__restrict__ phase, T *__restrict__ map, int64_t n,
+                                                int pitch, T beta)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t c0 = cell[p];
+    const cplx<T> f = frac[p];
+    const T twoW = T(2) / T(W);
+    T wa[W], wb[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        wa[a] = es_kernel<T>(f.x - T(a), twoW, beta);
+        wb[a] = es_kernel<T>(f.y - T(a), twoW, beta);
+    }
+    const int32_t dst = perm[p];
+    if (!SPIN) {
+        const T *g = (const T *)grid + c0;
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            T r = T(0);
+#pragma unroll
+            for (int b = 0; b < W; ++b) r += wb[b] * __ldg(g + (int64_t)a * pitch + b);
+            acc += wa[a] * r;
+        }
+        map[dst] = acc;
+    } else {
+        const cplx<T> *g = (const cplx<T> *)grid + c0;
+        T ax = T(0), ay = T(0);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            T rx = T(0), ry = T(0);
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const cplx<T> v = __ldg(g + (int64_t)a * pitch + b);
+                rx += wb[b] * v.x;
+                ry += wb[b] * v.y;
+            }
+            ax += wa[a] * rx;
+            ay += wa[a] * ry;
+        }
+        const cplx<T> ph = phase[p];
+        map[dst] = ax * ph.x - ay * ph.y;
+        map[n + dst] = ax * ph.y + ay * ph.x;
+    }
+}
+
+template <typename T, int W, bool SPIN>
+__global__ void __launch_bounds__(256) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
+                                                const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
+                                                const cplx<T> *__restrict__ phase, const T *__restrict__ map,
+                                                int64_t n, int pitch, T beta)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t c0 = cell[p];
+    const cplx<T> f = frac[p];
+    const T twoW = T(2) / T(W);
+    T wa[W], wb[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        wa[a] = es_kernel<T>(f.x - T(a), twoW, beta);
+        wb[a] = es_kernel<T>(f.y - T(a), twoW, beta);
+    }
+    const int32_t src = perm[p];
+    if (!SPIN) {
+        const T x = map[src];
+        T *g = (T *)grid + c0;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            const T xa = wa[a] * x;
+#pragma unroll
+            for (int b = 0; b < W; ++b) atomicAdd(g + (int64_t)a * pitch + b, xa * wb[b]);
+        }
+    } else {
+        // e^{-i s chi} (Q + i U)
+        const cplx<T> ph = phase[p];
+        const T q = map[src], u = map[n + src];
+        const T zx = ph.x * q + ph.y * u, zy = ph.x * u - ph.y * q;
+        T *g = (T *)grid + 2 * (int64_t)c0;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            const T xa = wa[a] * zx, ya = wa[a] * zy;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                T *q2 = g + 2 * ((int64_t)a * pitch + b);
+                atomicAdd(q2, xa * wb[b]);
+                atomicAdd(q2 + 1, ya * wb[b]);
+            }
+        }
+    }
+}
+
+template <typename T, bool SPIN, int W>
+cudaError_t interp_w(const Plan &p, const void *grid, void *map, cudaStream_t st)
+{
+    const int thr = 256;
+    const int64_t blocks = (p.npts + thr - 1) / thr;
+    if (blocks == 0) return cudaSuccess;
+    k_interp<T, W, SPIN><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                           (const cplx<T> *)p.phase, (T *)map, p.npts, p.pitch,
+                                                           (T)p.beta);
+    return cudaGetLastError();
+}
+
+template <typename T, bool SPIN, int W>
+cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st)
+{
+    const int thr = 256;
+    const int64_t blocks = (p.npts + thr - 1) / thr;
+    if (blocks == 0) return cudaSuccess;
+    k_spread<T, W, SPIN><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                           (const cplx<T> *)p.phase, (const T *)map, p.npts, p.pitch,
+                                                           (T)p.beta);
+    return cudaGetLastError();
+}
+
+template <typename T, bool SPIN>
+cudaError_t interp_dispatch(const Plan &p, const void *grid, void *map, cudaStream_t st)
+{
+    switch (p.W) {
+    case 4: return interp_w<T, SPIN, 4>(p, grid, map, st);
+    case 5: return interp_w<T, SPIN, 5>(p, grid, map, st);
+    case 6: return interp_w<T, SPIN, 6>(p, grid, map, st);
+    case 7: return interp_w<T, SPIN, 7>(p, grid, map, st);
+    case 8: return interp_w<T, SPIN, 8>(p, grid, map, st);
+    case 9: return interp_w<T, SPIN, 9>(p, grid, map, st);
+    case 10: return interp_w<T, SPIN, 10>(p, grid, map, st);
+    case 11: return interp_w<T, SPIN, 11>(p, grid, map, st);
+    case 12: return interp_w<T, SPIN, 12>(p, grid, map, st);
+    case 13: return interp_w<T, SPIN, 13>(p, grid, map, st);
+    case 14: return interp_w<T, SPIN, 14>(p, grid, map, st);
+    case 15: return interp_w<T, SPIN, 15>(p, grid, map, st);
+    case 16: return interp_w<T, SPIN, 16>(p, grid, map, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, bool SPIN>
+cudaError_t spread_dispatch(const Plan &p, const void *map, void *grid, cudaStream_t st)
+{
+    switch (p.W) {
+    case 4: return spread_w<T, SPIN, 4>(p, map, grid, st);
+    case 5: return spread_w<T, SPIN, 5>(p, map, grid, st);
+    case 6: return spread_w<T, SPIN, 6>(p, map, grid, st);
+    case 7: return spread_w<T, SPIN, 7>(p, map, grid, st);
+    case 8: return spread_w<T, SPIN, 8>(p, map, grid, st);
+    case 9: return spread_w<T, SPIN, 9>(p, map, grid, st);
+    case 10: return spread_w<T, SPIN, 10>(p, map, grid, st);
+    case 11: return spread_w<T, SPIN, 11>(p, map, grid, st);
+    case 12: return spread_w<T, SPIN, 12>(p, map, grid, st);
+    case 13: return spread_w<T, SPIN, 13>(p, map, grid, st);
+    case 14: return spread_w<T, SPIN, 14>(p, map, grid, st);
+    case 15: return spread_w<T, SPIN, 15>(p, map, grid, st);
+    case 16: return spread_w<T, SPIN, 16>(p, map, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_interp(const Plan &p, const void *grid, void *map, cudaStream_t st)
+{
+    if (p.prec == LENS_FP32)
+        return p.spin ? interp_dispatch<float, true>(p, grid, map, st) : interp_dispatch<float, false>(p, grid, map, st);
+    return p.spin ? interp_dispatch<double, true>(p, grid, map, st) : interp_dispatch<double, false>(p, grid, map, st);
+}
+
+cudaError_t launch_spread(const Plan &p, const void *map, void *grid, cudaStream_t st)
+{
+    const size_t eb = (p.prec == LENS_FP32 ? 4 : 8) * (p.spin ? 2 : 1);
+    cudaError_t e = cudaMemsetAsync(grid, 0, eb * (size_t)p.R * p.pitch, st);
+    if (e != cudaSuccess) return e;
+    if (p.prec == LENS_FP32)
+        return p.spin ? spread_dispatch<float, true>(p, map, grid, st) : spread_dispatch<float, false>(p, map, grid, st);
+    return p.spin ? spread_dispatch<double, true>(p, map, grid, st) : spread_dispatch<double, false>(p, map, grid, st);
+}
+
+// Point preparation: validate, compute cells/offsets/phases in user order,
+// radix-sort by tile key, gather into sorted order.  Temporary buffers are
+// released before returning; the stream is synchronised once.
+cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, const double *chi,
+                               cudaStream_t st, std::string &err)
+{
+    const int64_t n = p.npts;
+    if (n == 0) return cudaSuccess;
+    if (n > (int64_t)0x7fffffff) { err = "npoints above 2^31 - 1"; return cudaErrorInvalidValue; }
+    uint32_t *key = nullptr, *key2 = nullptr, *cell_u = nullptr;
+    int32_t *idx = nullptr;
+    double2 *frac_u = nullptr, *phase_u = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        cudaFree(key); cudaFree(key2); cudaFree(cell_u); cudaFree(idx);
+        cudaFree(frac_u); cudaFree(phase_u); cudaFree(tmp);
+    };
+#define GSL_TRY(x) do { e = (x); if (e != cudaSuccess) { cleanup(); return e; } } while (0)
+    GSL_TRY(cudaMalloc(&key, n * sizeof(uint32_t)));
+    GSL_TRY(cudaMalloc(&key2, n * sizeof(uint32_t)));
+    GSL_TRY(cudaMalloc(&idx, n * sizeof(int32_t)));
+    GSL_TRY(cudaMalloc(&cell_u, n * sizeof(uint32_t)));
+    GSL_TRY(cudaMalloc(&frac_u, n * sizeof(double2)));
+    if (p.spin) GSL_TRY(cudaMalloc(&phase_u, n * sizeof(double2)));
+    GSL_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned), st));
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((n + thr - 1) / thr);
+    k_prep<<<blocks, thr, 0, st>>>(theta, phi, chi, n, p.N1, p.N2, p.W, p.r_lo, p.R, p.pitch, p.spin, key, idx,
+                                   cell_u, frac_u, phase_u, p.flags);
+    GSL_TRY(cudaGetLastError());
+    const int ntc = (p.N2 + kTileC - 1) / kTileC;
+    const uint64_t nkeys = (uint64_t)((p.R + kTileR - 1) / kTileR) * ntc;
+    int bits = 1;
+    while (bits < 32 && (1ull << bits) < nkeys) ++bits;
+    GSL_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, key2, idx, p.perm, (int)n, 0, bits, st));
+    GSL_TRY(cudaMalloc(&tmp, tmp_bytes));
+    GSL_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, key, key2, idx, p.perm, (int)n, 0, bits, st));
+    k_gather_points<<<blocks, thr, 0, st>>>(p.perm, n, cell_u, frac_u, phase_u, p.prec, p.spin, p.cell, p.frac,
+                                            p.phase);
+    GSL_TRY(cudaGetLastError());
+    unsigned hflags = 0;
+    GSL_TRY(cudaMemcpyAsync(&hflags, p.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    GSL_TRY(cudaStreamSynchronize(st));
+#undef GSL_TRY
+    cleanup();
+    if (hflags & FLAG_DOMAIN) { err = "a coordinate is not finite or theta is outside [0, pi]"; return cudaErrorInvalidValue; }
+    if (hflags & FLAG_OOB) { err = "internal: a point fell outside the kept rows"; return cudaErrorInvalidValue; }
+    return cudaSuccess;
+}
+
+}  // namespace gsl

@@ -1,0 +1,615 @@
+// Plan creation and the C ABI of libgslens (see include/gslens.h).
+//
+// Plan-time work (Sect. 4: excluded from the timed transform because the
+// geometry is shared by many maps): grid sizes, the accuracy heuristic
+// epsilon -> (sigma, W, beta), recursion-coefficient and ring tables, kernel
+// deconvolution factors, FFT descriptors, and the sorted point tables.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gsl {
+int legendre_rpt(int prec, int spin);
+}
+
+using namespace gsl;
+
+namespace {
+
+thread_local int g_last_status = LENS_OK;
+thread_local char g_last_msg[512] = "";
+
+int fail(int status, const std::string &msg)
+{
+    g_last_status = status;
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg.c_str());
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? LENS_ERR_NOMEM : LENS_ERR_CUDA, m);
+}
+
+constexpr double kPi = 3.141592653589793238462643383280;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+bool smooth7(int n)
+{
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int good_even(int n)
+{
+    if (n < 2) n = 2;
+    if (n & 1) ++n;
+    while (!smooth7(n)) n += 2;
+    return n;
+}
+
+// ES kernel and its Fourier transform by Gauss-Legendre quadrature after
+// z = (W/2) sin t, which removes the square-root endpoint behaviour:
+//   psihat(xi) = W/2 int_{-pi/2}^{pi/2} exp(beta (cos t - 1)) cos(xi W/2 sin t) cos t dt
+struct Quad {
+    std::vector<double> x, w;
+    explicit Quad(int n)
+    {
+        x.resize(n);
+        w.resize(n);
+        for (int i = 0; i < n; ++i) {  // Newton on P_n
+            double z = cos(kPi * (i + 0.75) / (n + 0.5));
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                double dp = n * (z * p1 - p0) / (z * z - 1.0);
+                double dz = p1 / dp;
+                z -= dz;
+                if (fabs(dz) < 1e-16) break;
+            }
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (z * p1 - p0) / (z * z - 1.0);
+            x[i] = z;
+            w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+    }
+};
+
+double psihat(const Quad &q, double xi, int W, double beta)
+{
+    // integrate over t in [0, pi/2] (even integrand), nodes mapped from [-1, 1]
+    double s = 0.0;
+    const double h = 0.25 * kPi;
+    for (size_t i = 0; i < q.x.size(); ++i) {
+        const double t = h * (q.x[i] + 1.0);
+        s += q.w[i] * exp(beta * (cos(t) - 1.0)) * cos(xi * 0.5 * W * sin(t)) * cos(t);
+    }
+    return 2.0 * 0.5 * W * h * s;
+}
+
+// Kernel support for a target accuracy at oversampling sigma:
+// smallest W with 3 exp(-pi W sqrt(1 - 1/sigma)) <= eps (Barnett et al.'s
+// estimate with a safety factor measured against direct summation).
+int support_for(double eps, double sigma)
+{
+    const double r = kPi * sqrt(1.0 - 1.0 / sigma);
+    int W = (int)ceil(log(3.0 / eps) / r);
+    return std::max(W, 4);
+}
+
+std::vector<int> factorize(int n)
+{
+    std::vector<int> f;
+    while (n % 8 == 0) { f.push_back(8); n /= 8; }
+    if (n % 4 == 0) { f.push_back(4); n /= 4; }
+    if (n % 2 == 0) { f.push_back(2); n /= 2; }
+    for (int p : {3, 5, 7})
+        while (n % p == 0) { f.push_back(p); n /= p; }
+    return f;
+}
+
+struct Builder {
+    Plan &p;
+    explicit Builder(Plan &pl) : p(pl) {}
+    cudaError_t alloc(void **ptr, size_t bytes, bool work)
+    {
+        *ptr = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) return e;
+        p.allocs[p.nallocs++] = *ptr;
+        (work ? p.work_bytes : p.plan_bytes) += bytes;
+        return cudaSuccess;
+    }
+    template <typename V> cudaError_t upload(void **ptr, const std::vector<V> &v)
+    {
+        cudaError_t e = alloc(ptr, v.size() * sizeof(V), false);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(*ptr, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice);
+    }
+    cudaError_t fft(FftDesc &d, int n)
+    {
+        d.n = n;
+        std::vector<int> f = factorize(n);
+        d.nst = (int)f.size();
+        for (int i = 0; i < d.nst; ++i) d.radix[i] = f[i];
+        std::vector<int> perm(n);
+        for (int i = 0; i < n; ++i) {
+            int v = i, scale = n, pos = 0;
+            for (int st = d.nst - 1; st >= 0; --st) {
+                const int r = f[st];
+                scale /= r;
+                pos += (v % r) * scale;
+                v /= r;
+            }
+            perm[i] = pos;
+        }
+        void *dp = nullptr;
+        cudaError_t e = upload(&dp, perm);
+        if (e != cudaSuccess) return e;
+        d.perm = (const int *)dp;
+        void *tw = nullptr;
+        if (p.prec == LENS_FP32) {
+            std::vector<float2> t(n);
+            for (int i = 0; i < n; ++i) t[i] = make_float2((float)cos(2 * kPi * i / n), (float)-sin(2 * kPi * i / n));
+            e = upload(&tw, t);
+        } else {
+            std::vector<double2> t(n);
+            for (int i = 0; i < n; ++i) t[i] = make_double2(cos(2 * kPi * i / n), -sin(2 * kPi * i / n));
+            e = upload(&tw, t);
+        }
+        d.tw = tw;
+        return e;
+    }
+};
+
+struct Choice {
+    double sigma = 0, beta = 0;
+    int W = 0, N1 = 0, N2 = 0;
+    double cost = 1e300;
+};
+
+// Grid sizes for a given sigma / W (N1 >= M so the theta kernels can move
+// coefficients in place; N1 >= 4W + 4 so the kept rows never alias).
+void sizes_for(int lmax, int mmax, int M, double sigma, int W, int &N1, int &N2)
+{
+    N1 = good_even(std::max({(int)ceil(sigma * (2 * lmax + 2)), M, 4 * W + 4}));
+    N2 = good_even(std::max({(int)ceil(sigma * (2 * mmax + 2)), 4 * W + 4}));
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t lens_nalm(int lmax, int mmax)
+{
+    if (lmax < 0 || mmax < 0 || mmax > lmax) return 0;
+    return (int64_t)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
+}
+
+const char *lens_status_string(int s)
+{
+    switch (s) {
+    case LENS_OK: return "ok";
+    case LENS_ERR_INVALID: return "invalid argument";
+    case LENS_ERR_DOMAIN: return "coordinate outside the domain";
+    case LENS_ERR_PRECISION: return "accuracy not reachable at this precision";
+    case LENS_ERR_NOMEM: return "out of memory";
+    case LENS_ERR_CUDA: return "CUDA error";
+    case LENS_ERR_TIMEOUT: return "device wait timed out";
+    case LENS_ERR_UNSUPPORTED: return "size not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+int lens_get_last_error(void) { return g_last_status; }
+const char *lens_last_error_message(void) { return g_last_msg; }
+int lens_version(void) { return 100; }
+
+int lens_plan_destroy(lens_plan pl)
+{
+    if (!pl) return LENS_OK;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    int dev0 = 0;
+    cudaGetDevice(&dev0);
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
+    cudaSetDevice(dev0);
+    delete p;
+    return LENS_OK;
+}
+
+int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t npoints, const double *theta_d,
+                        const double *phi_d, const double *chi_d, double epsilon, int prec, unsigned flags,
+                        void *stream, const lens_plan_params *prm)
+{
+    if (!out) return fail(LENS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (lmax < 0 || mmax < 0 || mmax > lmax) return fail(LENS_ERR_INVALID, "need 0 <= mmax <= lmax");
+    if (spin < 0 || spin > lmax) return fail(LENS_ERR_INVALID, "need 0 <= spin <= lmax");
+    if (npoints < 0 || npoints > 0x7fffffffLL) return fail(LENS_ERR_INVALID, "npoints must be in [0, 2^31 - 1]");
+    if (npoints > 0 && (!theta_d || !phi_d)) return fail(LENS_ERR_INVALID, "theta/phi pointers are NULL");
+    if (prec != LENS_FP32 && prec != LENS_FP64) return fail(LENS_ERR_INVALID, "prec must be LENS_FP32 or LENS_FP64");
+    if (flags != 0) return fail(LENS_ERR_INVALID, "flags must be 0");
+    if (!(epsilon > 0) || !(epsilon < 1)) return fail(LENS_ERR_INVALID, "epsilon must be in (0, 1)");
+    if (prec == LENS_FP32 && epsilon < 1e-6)
+        return fail(LENS_ERR_PRECISION, "FP32 plans reach epsilon >= 1e-6; use LENS_FP64");
+    if (epsilon < 1e-13) return fail(LENS_ERR_PRECISION, "epsilon below 1e-13 is not supported");
+    if (lmax > 16383) return fail(LENS_ERR_UNSUPPORTED, "lmax above 16383");
+
+    Plan *p = new Plan();
+    p->lmax = lmax; p->mmax = mmax; p->spin = spin; p->prec = prec;
+    p->npts = npoints; p->eps = epsilon;
+    p->stream = (cudaStream_t)stream;
+    cudaGetDevice(&p->device);
+    p->nalm = lens_nalm(lmax, mmax);
+    p->ncol = spin ? 2 * mmax + 1 : mmax + 1;
+    Builder B(*p);
+    auto bail = [&](int st, const std::string &m) { lens_plan_destroy(reinterpret_cast<lens_plan>(p)); return fail(st, m); };
+    auto bailc = [&](cudaError_t e, const char *w) {
+        lens_plan_destroy(reinterpret_cast<lens_plan>(p));
+        return cuda_fail(e, w);
+    };
+
+    // ---- equiangular grid: ntheta >= lmax + 2, 2 ntheta - 2 7-smooth (Sect. 3, App. A)
+    int nt = std::max(lmax + 2, 2);
+    if (prm && prm->ntheta > 0) {
+        if (prm->ntheta < lmax + 2 || !smooth7(2 * prm->ntheta - 2))
+            return bail(LENS_ERR_INVALID, "ntheta must be >= lmax + 2 with 2 ntheta - 2 7-smooth");
+        nt = prm->ntheta;
+    } else {
+        while (!smooth7(2 * nt - 2)) ++nt;
+    }
+    p->ntheta = nt;
+    p->nnorth = (nt + 1) / 2;
+    p->M = 2 * nt - 2;
+
+    // ---- accuracy heuristic.  The NUFFT gets eps/2 of the error budget in FP64
+    // plans and eps/4 in FP32 plans, where FP32 rounding in the Legendre sums and
+    // the FFTs takes ~1e-6 at lmax ~ 4096.  sigma is then picked by a cost model.
+    const size_t esz = prec == LENS_FP32 ? 8 : 16;
+    const size_t fft_max = kSmemLimit / esz;
+    const double eps_nufft = (prec == LENS_FP32 ? 0.25 : 0.5) * epsilon;
+    const int ncomp = spin ? 2 : 1;
+    Choice best;
+    const double sig_cand[] = {1.2, 1.25, 1.3, 1.4, 1.5, 1.6, 1.75, 2.0, 2.25, 2.5};
+    for (double sg : sig_cand) {
+        if (prm && prm->sigma > 0 && fabs(prm->sigma - sg) > 1e-12) continue;
+        int W = (prm && prm->W > 0) ? prm->W : support_for(eps_nufft, sg);
+        if (W > 16) continue;
+        int N1, N2;
+        sizes_for(lmax, mmax, p->M, sg, W, N1, N2);
+        if ((size_t)N1 > fft_max || (size_t)N2 > fft_max) continue;
+        // per-point taps + kernel evaluations, grid passes (FFT + interp)
+        const double pts = (double)npoints * ncomp * ((double)W * W + 16.0 * W);
+        const double grd = 12.0 * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1;
+        const double cost = pts + grd;
+        if (cost < best.cost) { best.cost = cost; best.sigma = sg; best.W = W; best.N1 = N1; best.N2 = N2; }
+    }
+    if (prm && prm->sigma > 0 && best.W == 0) {  // explicit sigma not in the candidate list
+        int W = prm->W > 0 ? prm->W : support_for(eps_nufft, prm->sigma);
+        sizes_for(lmax, mmax, p->M, prm->sigma, W, best.N1, best.N2);
+        best.sigma = prm->sigma; best.W = W;
+    }
+    if (best.W == 0)
+        return bail(LENS_ERR_UNSUPPORTED, "no oversampling factor fits the shared-memory FFT at this lmax/precision");
+    if (best.W < 4 || best.W > 16) return bail(LENS_ERR_INVALID, "kernel support W must be in [4, 16]");
+    if ((size_t)best.N1 > fft_max || (size_t)best.N2 > fft_max || (size_t)p->M > fft_max)
+        return bail(LENS_ERR_UNSUPPORTED, "FFT length above the shared-memory limit of this build");
+    p->W = best.W;
+    p->N1 = best.N1;
+    p->N2 = best.N2;
+    {
+        const double s1 = (double)p->N1 / (2 * lmax + 2), s2 = (double)p->N2 / (2 * mmax + 2);
+        p->sigma = std::min(s1, s2);
+    }
+    p->beta = (prm && prm->beta > 0) ? prm->beta : kPi * p->W * (1.0 - 0.5 / p->sigma);
+    p->r_lo = -p->W;
+    p->R = p->N1 / 2 + 2 * p->W + 1;
+    p->pitch = ((p->N2 + p->W - 1) + 31) / 32 * 32;
+
+    // ---- Legendre launch shape
+    p->leg_rpt = legendre_rpt(prec, spin);
+    {
+        const int nw = (p->nnorth + 32 * p->leg_rpt - 1) / (32 * p->leg_rpt);
+        p->leg_chunks = (nw + 15) / 16;
+        p->leg_warps = (nw + p->leg_chunks - 1) / p->leg_chunks;
+    }
+
+    cudaError_t e;
+    // ---- device buffers
+    if ((e = B.alloc((void **)&p->flags, sizeof(unsigned) * 4, false)) != cudaSuccess) return bailc(e, "alloc flags");
+    if ((e = B.alloc(&p->rec_ab, (size_t)p->nalm * (prec == LENS_FP32 ? 16 : 16), false)) != cudaSuccess)
+        return bailc(e, "alloc rec_ab");
+    if (spin && (e = B.alloc(&p->rec_c, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_c");
+    if ((e = B.alloc(&p->ring, esz * (size_t)p->ncol * p->ntheta, true)) != cudaSuccess) return bailc(e, "alloc ring");
+    if ((e = B.alloc(&p->X, esz * (size_t)p->R * p->ncol, true)) != cudaSuccess) return bailc(e, "alloc X");
+    if ((e = B.alloc(&p->grid, (esz / 2) * ncomp * (size_t)p->R * p->pitch, true)) != cudaSuccess)
+        return bailc(e, "alloc grid");
+    if (npoints > 0) {
+        if ((e = B.alloc((void **)&p->cell, sizeof(uint32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc cell");
+        if ((e = B.alloc(&p->frac, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc frac");
+        if ((e = B.alloc((void **)&p->perm, sizeof(int32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc perm");
+        if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
+    }
+
+    // ---- host tables: start-value norms, rings, deconvolution factors
+    {
+        // lognorm[m] = log2 sqrt((2 l0 + 1)/(4 pi) C(2 l0, k)),
+        //   m >= s: l0 = m, C(2m, m + s) via the running ratio (2m)(2m-1)/((m+s)(m-s))
+        //   m <  s: l0 = s, C(2s, s + m)
+        std::vector<double> ln(mmax + 1);
+        double lb = 0.0, cmp = 0.0;  // log2 C(2m, m+s), Neumaier-compensated running sum
+        for (int m = 0; m <= mmax; ++m) {
+            int l0;
+            double logbin;
+            if (m < spin) {
+                l0 = spin;
+                logbin = 0.0;
+                for (int i = 1; i <= spin + m; ++i) logbin += log2((double)(2 * spin - (spin + m) + i) / i);
+            } else {
+                l0 = m;
+                if (m == spin) {
+                    lb = 0.0; cmp = 0.0;  // C(2s, 2s) = 1
+                } else {
+                    const double term = log2((2.0 * m) * (2.0 * m - 1.0) / ((double)(m + spin) * (m - spin)));
+                    const double t = lb + term;
+                    if (fabs(lb) >= fabs(term)) cmp += (lb - t) + term; else cmp += (term - t) + lb;
+                    lb = t;
+                }
+                logbin = lb + cmp;
+            }
+            ln[m] = 0.5 * (log2((2.0 * l0 + 1.0) / (4.0 * kPi)) + logbin);
+        }
+        void *d = nullptr;
+        if ((e = B.upload(&d, ln)) != cudaSuccess) return bailc(e, "upload lognorm");
+        p->lognorm = (double *)d;
+
+        std::vector<double> x(p->nnorth), ls(p->nnorth), lc(p->nnorth);
+        std::vector<float2> xdf(p->nnorth);
+        for (int j = 0; j < p->nnorth; ++j) {
+            const double th = kPi * j / (nt - 1);
+            x[j] = cos(th);
+            if (2 * j == nt - 1) x[j] = 0.0;
+            const float h = (float)x[j];
+            xdf[j] = make_float2(h, (float)(x[j] - (double)h));
+            ls[j] = j == 0 ? -INFINITY : log2(sin(0.5 * th));
+            lc[j] = log2(cos(0.5 * th));
+        }
+        if ((e = B.upload(&d, x)) != cudaSuccess) return bailc(e, "upload rings");
+        p->rings.x = (const double *)d;
+        if ((e = B.upload(&d, xdf)) != cudaSuccess) return bailc(e, "upload rings");
+        p->rings.xdf = (const float2 *)d;
+        if ((e = B.upload(&d, ls)) != cudaSuccess) return bailc(e, "upload rings");
+        p->rings.lsin2 = (const double *)d;
+        if ((e = B.upload(&d, lc)) != cudaSuccess) return bailc(e, "upload rings");
+        p->rings.lcos2 = (const double *)d;
+
+        Quad q(std::max(64, 4 * p->W + 40));
+        std::vector<double> w1(2 * lmax + 1), w2(p->ncol);
+        for (int k = 0; k <= lmax; ++k) {
+            const double v = 1.0 / psihat(q, 2 * kPi * k / p->N1, p->W, p->beta);
+            w1[lmax + k] = v;
+            w1[lmax - k] = v;
+        }
+        for (int c = 0; c < p->ncol; ++c) {
+            const int m = spin ? c - mmax : c;
+            w2[c] = 1.0 / (p->M * psihat(q, 2 * kPi * m / p->N2, p->W, p->beta));
+        }
+        if (prec == LENS_FP32) {
+            std::vector<float> f1(w1.begin(), w1.end()), f2(w2.begin(), w2.end());
+            if ((e = B.upload(&p->w1, f1)) != cudaSuccess) return bailc(e, "upload w1");
+            if ((e = B.upload(&p->w2, f2)) != cudaSuccess) return bailc(e, "upload w2");
+        } else {
+            if ((e = B.upload(&p->w1, w1)) != cudaSuccess) return bailc(e, "upload w1");
+            if ((e = B.upload(&p->w2, w2)) != cudaSuccess) return bailc(e, "upload w2");
+        }
+    }
+    if ((e = B.fft(p->fM, p->M)) != cudaSuccess) return bailc(e, "fft tables");
+    if ((e = B.fft(p->fN1, p->N1)) != cudaSuccess) return bailc(e, "fft tables");
+    if ((e = B.fft(p->fN2, p->N2)) != cudaSuccess) return bailc(e, "fft tables");
+
+    if ((e = launch_rec_tables(*p)) != cudaSuccess) return bailc(e, "recursion tables");
+    {
+        std::string err;
+        e = launch_prep_points(*p, theta_d, phi_d, spin ? chi_d : nullptr, p->stream, err);
+        if (e != cudaSuccess) {
+            if (!err.empty()) return bail(err.find("internal") == 0 ? LENS_ERR_CUDA : LENS_ERR_DOMAIN, err);
+            return bailc(e, "point preparation");
+        }
+    }
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return bailc(e, "plan sync");
+    *out = reinterpret_cast<lens_plan>(p);
+    return LENS_OK;
+}
+
+int lens_plan_create(lens_plan *out, int lmax, int mmax, int spin, int64_t npoints, const double *theta_d,
+                     const double *phi_d, const double *chi_d, double epsilon, int prec, unsigned flags, void *stream)
+{
+    return lens_plan_create_ex(out, lmax, mmax, spin, npoints, theta_d, phi_d, chi_d, epsilon, prec, flags, stream,
+                               nullptr);
+}
+
+int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
+{
+    if (!pl || !info) return fail(LENS_ERR_INVALID, "NULL argument");
+    const Plan *p = reinterpret_cast<const Plan *>(pl);
+    info->lmax = p->lmax; info->mmax = p->mmax; info->spin = p->spin; info->prec = p->prec;
+    info->npoints = p->npts; info->epsilon = p->eps;
+    info->ntheta = p->ntheta; info->ntheta_fft = p->M; info->n1 = p->N1; info->n2 = p->N2;
+    info->W = p->W; info->beta = p->beta; info->sigma = p->sigma;
+    info->rows_kept = p->R; info->row_pitch = p->pitch;
+    info->workspace_bytes = p->work_bytes; info->plan_bytes = p->plan_bytes;
+    return LENS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int forward_one(const Plan &p, const void *alm, void *map, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = launch_legendre_fwd(p, alm, p.ring, st)) != cudaSuccess) return cuda_fail(e, "legendre synthesis");
+    if ((e = launch_theta_fwd(p, p.ring, p.X, st)) != cudaSuccess) return cuda_fail(e, "theta transform");
+    if ((e = launch_phi_fwd(p, p.X, p.grid, st)) != cudaSuccess) return cuda_fail(e, "phi transform");
+    if ((e = launch_interp(p, p.grid, map, st)) != cudaSuccess) return cuda_fail(e, "interpolation");
+    return LENS_OK;
+}
+
+int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = launch_spread(p, map, p.grid, st)) != cudaSuccess) return cuda_fail(e, "spreading");
+    if ((e = launch_phi_adj(p, p.grid, p.X, st)) != cudaSuccess) return cuda_fail(e, "phi transform");
+    if ((e = launch_theta_adj(p, p.X, p.ring, st)) != cudaSuccess) return cuda_fail(e, "theta transform");
+    if ((e = launch_legendre_adj(p, p.ring, alm, st)) != cudaSuccess) return cuda_fail(e, "adjoint legendre");
+    return LENS_OK;
+}
+
+size_t alm_bytes(const Plan &p) { return (size_t)p.nalm * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 8 : 16); }
+size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 4 : 8); }
+
+}  // namespace
+
+extern "C" {
+
+int lens_synthesis(lens_plan pl, const void *alm_d, void *map_d, int nmaps, void *stream)
+{
+    if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
+    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    if (nmaps > 0 && (!alm_d || (!map_d && p.npts > 0))) return fail(LENS_ERR_INVALID, "NULL buffer");
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    for (int i = 0; i < nmaps; ++i) {
+        int r = forward_one(p, (const char *)alm_d + i * alm_bytes(p), (char *)map_d + i * map_bytes(p), st);
+        if (r != LENS_OK) return r;
+    }
+    return LENS_OK;
+}
+
+int lens_adjoint(lens_plan pl, const void *map_d, void *alm_d, int nmaps, void *stream)
+{
+    if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
+    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    if (nmaps > 0 && (!alm_d || (!map_d && p.npts > 0))) return fail(LENS_ERR_INVALID, "NULL buffer");
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    for (int i = 0; i < nmaps; ++i) {
+        int r = adjoint_one(p, (const char *)map_d + i * map_bytes(p), (char *)alm_d + i * alm_bytes(p), st);
+        if (r != LENS_OK) return r;
+    }
+    return LENS_OK;
+}
+
+static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, void *stream, bool fwd)
+{
+    if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
+    Plan &p = *reinterpret_cast<Plan *>(pl);
+    if (nmaps > 0 && (!in_h || !out_h)) return fail(LENS_ERR_INVALID, "NULL buffer");
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    const size_t ab = alm_bytes(p), mb = map_bytes(p);
+    void *d_in = nullptr, *d_out = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_in, fwd ? ab : mb)) != cudaSuccess) return cuda_fail(e, "staging alloc");
+    if ((e = cudaMalloc(&d_out, fwd ? mb : ab)) != cudaSuccess) { cudaFree(d_in); return cuda_fail(e, "staging alloc"); }
+    int rc = LENS_OK;
+    for (int i = 0; i < nmaps && rc == LENS_OK; ++i) {
+        const size_t ib = fwd ? ab : mb, ob = fwd ? mb : ab;
+        if ((e = cudaMemcpyAsync(d_in, (const char *)in_h + i * ib, ib, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "host to device copy");
+            break;
+        }
+        rc = fwd ? forward_one(p, d_in, d_out, st) : adjoint_one(p, d_in, d_out, st);
+        if (rc != LENS_OK) break;
+        if ((e = cudaMemcpyAsync((char *)out_h + i * ob, d_out, ob, cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "device to host copy");
+            break;
+        }
+    }
+    e = cudaStreamSynchronize(st);
+    if (rc == LENS_OK && e != cudaSuccess) rc = cuda_fail(e, "stream sync");
+    cudaFree(d_in);
+    cudaFree(d_out);
+    return rc;
+}
+
+int lens_synthesis_host(lens_plan p, const void *alm_h, void *map_h, int nmaps, void *stream)
+{
+    return host_call(p, alm_h, map_h, nmaps, stream, true);
+}
+
+int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream)
+{
+    return host_call(p, map_h, alm_h, nmaps, stream, false);
+}
+
+int lens_ring_synthesis(lens_plan pl, const void *alm_d, void *ring_d, void *stream)
+{
+    if (!pl || !alm_d || !ring_d) return fail(LENS_ERR_INVALID, "NULL argument");
+    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    cudaError_t e = launch_legendre_fwd(p, alm_d, ring_d, st);
+    return e == cudaSuccess ? LENS_OK : cuda_fail(e, "legendre synthesis");
+}
+
+int lens_ring_adjoint(lens_plan pl, const void *ring_d, void *alm_d, void *stream)
+{
+    if (!pl || !alm_d || !ring_d) return fail(LENS_ERR_INVALID, "NULL argument");
+    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    cudaError_t e = launch_legendre_adj(p, ring_d, alm_d, st);
+    return e == cudaSuccess ? LENS_OK : cuda_fail(e, "adjoint legendre");
+}
+
+int lens_pointing(int64_t n, const double *theta_d, const double *phi_d, const double *ath_d, const double *aph_d,
+                  double *theta_out_d, double *phi_out_d, double *chi_out_d, void *stream)
+{
+    if (n < 0) return fail(LENS_ERR_INVALID, "n < 0");
+    if (n > 0 && (!theta_d || !phi_d || !ath_d || !aph_d || !theta_out_d || !phi_out_d))
+        return fail(LENS_ERR_INVALID, "NULL argument");
+    cudaError_t e = launch_pointing(n, theta_d, phi_d, ath_d, aph_d, theta_out_d, phi_out_d, chi_out_d,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? LENS_OK : cuda_fail(e, "pointing");
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: the relative L2 error over all outputs (Sect. 4's eps_eff, also
+applied to a_lm for the adjoint) must not exceed the requested epsilon: 1e-5
+for FP32 plans, 1e-10 for FP64 plans.  The adjoint identity holds to 1e-12
+(FP64) with the real-field inner product.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2304_10431_gb300 import LensError, LensPlan, pointing
+from paper_2304_10431_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+PRECS = [("fp32", 1e-5), ("fp64", 1e-10)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_alm(L, spin, seed, ld=None, mmax=None):
+    nc = 1 if spin == 0 else 2
+    cl = W.cmb_cl(L, ld or max(0.8 * L, 2.0))
+    return np.stack([W.draw_alm(cl, L, seed + k, mmax=mmax, spin=spin) for k in range(nc)])
+
+
+def gpu_alm(plan, a):
+    return torch.as_tensor(a, dtype=plan.complex_dtype, device=DEV)
+
+
+def gpu_map(plan, m):
+    return torch.as_tensor(m, dtype=plan.real_dtype, device=DEV)
+
+
+# ---------------------------------------------------------------- Legendre step
+@pytest.mark.parametrize("spin", [0, 1, 2])
+@pytest.mark.parametrize("prec,eps", PRECS)
+def test_ring_synthesis_vs_oracle(spin, prec, eps):
+    L = 70
+    th, ph, chi = W.random_points(100, 3)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=eps, precision=prec, device=DEV)
+    a = make_alm(L, spin, 5)
+    ring = plan.ring_synthesis(gpu_alm(plan, a)).cpu().numpy()
+    nt = plan.info()["ntheta"]
+    ref = O.ring_coeffs(L, L, spin, np.arange(nt) * math.pi / (nt - 1), a).T
+    assert rel(ring, ref) < (1e-13 if prec == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+@pytest.mark.parametrize("prec,eps", PRECS)
+def test_ring_adjoint_is_transpose(spin, prec, eps):
+    L = 70
+    th, ph, chi = W.random_points(10, 3)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=eps, precision=prec, device=DEV)
+    a = make_alm(L, spin, 8)
+    F = plan.ring_synthesis(gpu_alm(plan, a)).cpu().numpy()
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(F.shape) + 1j * rng.standard_normal(F.shape)
+    if spin == 0:
+        r[0] = r[0].real
+    at = plan.ring_adjoint(torch.as_tensor(r, dtype=plan.complex_dtype, device=DEV)).cpu().numpy()
+    em = W.alm_m_of_index(L)
+    if spin == 0:  # stored columns are m >= 0 of a Hermitian set: weight 2 for m > 0 on both sides
+        wr = np.where(np.arange(F.shape[0]) == 0, 1.0, 2.0)[:, None]
+        lhs = np.sum(wr * (F * np.conj(r)).real)
+    else:
+        lhs = np.sum((F * np.conj(r)).real)
+    rhs = np.sum(np.where(em == 0, 1.0, 2.0) * (a * np.conj(at)).real)
+    assert abs(lhs - rhs) <= (1e-12 if prec == "fp64" else 1e-5) * np.linalg.norm(F) * np.linalg.norm(r)
+
+
+# ---------------------------------------------------------------- full operator
+CASES = [  # (lmax, npoints, spin)
+    (1, 37, 0), (2, 64, 2), (17, 999, 0), (17, 999, 1), (33, 3001, 2), (70, 4099, 0), (70, 4099, 2), (70, 2500, 3),
+]
+
+
+@pytest.mark.parametrize("L,n,spin", CASES)
+@pytest.mark.parametrize("prec,eps", PRECS)
+def test_forward_and_adjoint_vs_oracle(L, n, spin, prec, eps):
+    th, ph, chi = W.random_points(n, 100 + L + spin)
+    th[:4] = [0.0, math.pi, 0.5 * math.pi, 1e-9]
+    ph[:4] = [7.0, -1.0, 2 * math.pi, 0.0]
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=eps, precision=prec, device=DEV)
+    a = make_alm(L, spin, 11)
+    m = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+    ref = O.synthesis(L, L, spin, th, ph, a, chi)
+    assert rel(m, ref) <= eps
+    y = np.random.default_rng(L).standard_normal(ref.shape)
+    at = plan.adjoint(gpu_map(plan, y)).cpu().numpy()
+    aref = O.adjoint(L, L, spin, th, ph, y, chi)
+    assert rel(at, aref) <= eps
+    if spin == 0:
+        assert np.all(at[0, W.alm_m_of_index(L) == 0].imag == 0)
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_adjoint_identity_fp64(spin):
+    L, n = 96, 20000
+    th, ph, chi = W.random_points(n, 4)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-12, precision="fp64", device=DEV)
+    rng = np.random.default_rng(2)
+    nc = 1 if spin == 0 else 2
+    x = rng.standard_normal((nc, plan.nalm)) + 1j * rng.standard_normal((nc, plan.nalm))
+    em, ell = W.alm_m_of_index(L), W.alm_l_of_index(L)
+    x[:, em == 0] = x[:, em == 0].real
+    x[:, ell < spin] = 0
+    y = rng.standard_normal((nc, n))
+    ax = plan.synthesis(gpu_alm(plan, x)).cpu().numpy()
+    aty = plan.adjoint(gpu_map(plan, y)).cpu().numpy()
+    lhs = np.sum(ax * y)
+    rhs = np.sum(np.where(em == 0, 1.0, 2.0) * (x * np.conj(aty)).real)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(ax) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("prec,eps", PRECS)
+def test_config1_lensed_healpix(prec, eps):
+    """Spin-0 lensing, lmax 128, HEALPix Nside 64 (49,152 points) deflected by the
+    gradient of phi (phi lmax 128, 2.5 arcmin rms), both directions."""
+    L, nside = 128, 64
+    th0, ph0 = W.healpix_centres(nside)
+    phi_lm = W.draw_alm(W.phi_cl(L), L, 2000)
+    th, ph, chi = O.deflected_points(th0, ph0, phi_lm, L)
+    a = W.draw_alm(W.cmb_cl(L, 100.0), L, 1000)[None]
+    plan = LensPlan(L, th, ph, chi, spin=0, epsilon=eps, precision=prec, device=DEV)
+    m = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+    ref = O.synthesis(L, L, 0, th, ph, a)
+    assert rel(m, ref) <= eps
+    at = plan.adjoint(gpu_map(plan, ref)).cpu().numpy()
+    aref = O.adjoint(L, L, 0, th, ph, ref)
+    assert rel(at, aref) <= eps
+
+
+def test_spin2_lensed_healpix_with_phase():
+    """Spin-2 Q/U at deflected HEALPix points (Nside 32) with the lensing phase chi."""
+    L, nside = 80, 32
+    th0, ph0 = W.healpix_centres(nside)
+    th, ph, chi = O.deflected_points(th0, ph0, W.draw_alm(W.phi_cl(L), L, 2001), L)
+    a = make_alm(L, 2, 1001)
+    for prec, eps in PRECS:
+        plan = LensPlan(L, th, ph, chi, spin=2, epsilon=eps, precision=prec, device=DEV)
+        m = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+        ref = O.synthesis(L, L, 2, th, ph, a, chi)
+        assert rel(m, ref) <= eps
+
+
+# ---------------------------------------------------------------- edge cases
+def test_mmax_below_lmax():
+    L, mmax, n = 40, 17, 1500
+    th, ph, chi = W.random_points(n, 21)
+    for spin in (0, 2):
+        a = make_alm(L, spin, 3, mmax=mmax)
+        plan = LensPlan(L, th, ph, chi, spin=spin, mmax=mmax, epsilon=1e-10, precision="fp64", device=DEV)
+        m = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+        assert rel(m, O.synthesis(L, mmax, spin, th, ph, a, chi)) <= 1e-10
+        y = np.random.default_rng(0).standard_normal(m.shape)
+        at = plan.adjoint(gpu_map(plan, y)).cpu().numpy()
+        assert rel(at, O.adjoint(L, mmax, spin, th, ph, y, chi)) <= 1e-10
+
+
+def test_lmax_zero_and_empty_points():
+    th, ph, _ = W.random_points(50, 1)
+    plan = LensPlan(0, th, ph, spin=0, epsilon=1e-10, precision="fp64", device=DEV)
+    a = torch.tensor([[2.0 + 5.0j]], dtype=torch.complex128, device=DEV)
+    m = plan.synthesis(a).cpu().numpy()
+    assert np.allclose(m, 2.0 / math.sqrt(4 * math.pi), atol=1e-14, rtol=0)
+    e = LensPlan(8, np.zeros(0), np.zeros(0), spin=2, epsilon=1e-5, device=DEV)
+    out = e.synthesis(torch.zeros(2, e.nalm, dtype=torch.complex64, device=DEV))
+    assert out.shape == (2, 0)
+    at = e.adjoint(torch.zeros(2, 0, dtype=torch.float32, device=DEV)).cpu().numpy()
+    assert np.all(at == 0)
+
+
+def test_domain_errors():
+    with pytest.raises(LensError) as ex:
+        LensPlan(8, np.array([0.1, 3.5]), np.array([0.0, 0.0]), device=DEV)
+    assert ex.value.status == 2
+    with pytest.raises(LensError) as ex:
+        LensPlan(8, np.array([0.1, np.nan]), np.array([0.0, 0.0]), device=DEV)
+    assert ex.value.status == 2
+    with pytest.raises(LensError) as ex:
+        LensPlan(8, np.array([0.1]), np.array([np.inf]), device=DEV)
+    assert ex.value.status == 2
+    with pytest.raises(LensError) as ex:
+        LensPlan(8, np.array([0.1]), np.array([0.0]), epsilon=1e-7, precision="fp32", device=DEV)
+    assert ex.value.status == 3
+
+
+def test_batch_and_host_entry_points():
+    L, n = 40, 2000
+    th, ph, chi = W.random_points(n, 5)
+    plan = LensPlan(L, th, ph, chi, spin=2, epsilon=1e-10, precision="fp64", device=DEV)
+    a = np.stack([make_alm(L, 2, 40 + i) for i in range(3)])
+    mb = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+    for i in range(3):
+        mi = plan.synthesis(gpu_alm(plan, a[i])).cpu().numpy()
+        assert np.array_equal(mb[i], mi)
+    mh = plan.synthesis_host(torch.as_tensor(a)).numpy()
+    assert np.array_equal(mh, mb)
+    ab = plan.adjoint(gpu_map(plan, mb)).cpu().numpy()
+    ah = plan.adjoint_host(torch.as_tensor(mb)).numpy()
+    # spreading accumulates with atomics: equal up to the order of FP64 additions
+    assert rel(ah, ab) < 1e-14
+
+
+def test_repeated_calls_identical_forward():
+    L, n = 64, 5000
+    th, ph, chi = W.random_points(n, 6)
+    plan = LensPlan(L, th, ph, chi, spin=0, epsilon=1e-5, precision="fp32", device=DEV)
+    a = gpu_alm(plan, make_alm(L, 0, 9))
+    m1 = plan.synthesis(a).cpu().numpy()
+    m2 = plan.synthesis(a).cpu().numpy()
+    assert np.array_equal(m1, m2)  # the forward path has no atomics
+
+
+# ---------------------------------------------------------------- pointing / deflection
+def test_pointing_vs_oracle():
+    rng = np.random.default_rng(3)
+    th0, ph0 = W.healpix_centres(16)
+    at = rng.normal(size=th0.size) * 1e-3
+    ap = rng.normal(size=th0.size) * 1e-3
+    at[:5] = 0.0
+    ap[:5] = 0.0
+    t = [torch.as_tensor(x, device=DEV) for x in (th0, ph0, at, ap)]
+    t2, p2, c2 = (x.cpu().numpy() for x in pointing(*t))
+    r2 = O.pointing(th0, ph0, at, ap)
+    assert np.max(np.abs(t2 - r2[0])) < 1e-13
+    assert np.max(np.abs(np.angle(np.exp(1j * (p2 - r2[1]))))) < 1e-12
+    assert np.max(np.abs(c2 - r2[2])) < 1e-12
+
+
+def test_deflection_field_on_gpu():
+    """Eq. "deflect": spin-1 synthesis of sqrt(L(L+1)) phi_LM at undeflected points."""
+    L, nside = 64, 32
+    th0, ph0 = W.healpix_centres(nside)
+    phi_lm = W.draw_alm(W.phi_cl(L), L, 7)
+    ell = W.alm_l_of_index(L)
+    g = np.stack([phi_lm * np.sqrt(ell * (ell + 1.0)), 0 * phi_lm])
+    plan = LensPlan(L, th0, ph0, spin=1, epsilon=1e-10, precision="fp64", device=DEV)
+    a = plan.synthesis(gpu_alm(plan, g)).cpu().numpy()
+    ref = O.synthesis(L, L, 1, th0, ph0, g)
+    assert rel(a, ref) <= 1e-10
