@@ -1,0 +1,505 @@
+#!/usr/bin/env python
+"""Benchmark: lensed points/sec of the general-SHT lensing pair on GB300.
+
+Workload (headline): lmax 4096, HEALPix Nside 2048 (50,331,648 points)
+deflected along the gradient of a lensing potential (phi lmax 4096,
+C_L^phiphi ~ (L+1)^-4 rescaled to 2.5 arcmin rms), CMB a_lm drawn from
+C_l = (l+10)^-2 exp(-(l/2990)^2).  One step = the whole hot path on that
+geometry: spin-0 T synthesis + adjoint, spin-2 E/B -> Q/U synthesis + adjoint.
+value = points / step time (FP32 plans, epsilon 1e-5); the FP64 plans
+(epsilon 1e-10) are measured in the same run and reported under "fp64".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gslens|reference]
+
+Deflected coordinates are computed on the GPU with the library itself (spin-1
+synthesis of sqrt(L(L+1)) phi_LM at the HEALPix centres, then the pointing
+kernel) and, like plan creation, are outside the timed region, as in the
+paper's benchmarks.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_PEAK_FALLBACK = 6800.0
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+STAGES = ["legendre_synthesis", "theta_fwd", "phi_fwd", "interp", "spread", "phi_adj", "theta_adj",
+          "legendre_adjoint"]
+KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legendre.cu", "theta_fwd": "torus.cu",
+                "theta_adj": "torus.cu", "phi_fwd": "torus.cu", "phi_adj": "torus.cu", "interp": "nufft.cu",
+                "spread": "nufft.cu"}
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
+# source makes the entry stale and the bench reports traffic null.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gslens", choices=["gslens", "reference"])
+    ap.add_argument("--lmax", type=int, default=4096)
+    ap.add_argument("--nside", type=int, default=2048)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_PEAK_FALLBACK, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def src_hash(fname):
+    with open(os.path.join(ROOT, "paper_2304_10431_gb300", "csrc", fname), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def alm_inputs(lmax):
+    from paper_2304_10431_gb300 import workloads as W
+    ld = 0.73 * lmax
+    cl = W.cmb_cl(lmax, ld)
+    aT = W.draw_alm(cl, lmax, 1000)[None]
+    aEB = np.stack([W.draw_alm(cl, lmax, 1001, spin=2), W.draw_alm(cl, lmax, 1002, spin=2)])
+    return aT, aEB, ld
+
+
+def workload_arrays(lmax, nside):
+    from paper_2304_10431_gb300 import workloads as W
+    th0, ph0 = W.healpix_centres(nside)
+    phi_lm = W.draw_alm(W.phi_cl(lmax), lmax, 2000)
+    aT, aEB, ld = alm_inputs(lmax)
+    return th0, ph0, phi_lm, aT, aEB, ld
+
+
+def deflect_on_gpu(th0, ph0, phi_lm, lmax, dev):
+    """Lensed geometry with the library: Eq. "deflect" (spin-1 synthesis) + pointing."""
+    import torch
+    from paper_2304_10431_gb300 import LensPlan, pointing
+    from paper_2304_10431_gb300 import workloads as W
+    ell = W.alm_l_of_index(lmax)
+    g = np.stack([phi_lm * np.sqrt(ell * (ell + 1.0)), np.zeros_like(phi_lm)])
+    t0 = torch.as_tensor(th0, device=dev)
+    p0 = torch.as_tensor(ph0, device=dev)
+    plan = LensPlan(lmax, t0, p0, spin=1, epsilon=1e-10, precision="fp64", device=dev)
+    alpha = plan.synthesis(torch.as_tensor(g, dtype=torch.complex128, device=dev))
+    plan.close()
+    th, ph, chi = pointing(t0, p0, alpha[0], alpha[1])
+    del alpha
+    return th, ph, chi
+
+
+def legendre_triples(lmax, spin, nnorth):
+    tot = 0
+    for m in range(lmax + 1):
+        l0 = max(m, spin)
+        tot += max(lmax - l0 + 1, 0)
+    return tot * nnorth
+
+
+def stage_units(info, npts, spin, prec):
+    """Algorithmic work per launch of each stage (flops for Legendre, bytes otherwise)."""
+    esz = 8 if prec == "fp32" else 16  # complex element
+    rsz = esz // 2
+    L, nt, ncol = info["lmax"], info["ntheta"], (2 * info["mmax"] + 1 if spin else info["mmax"] + 1)
+    R, N2 = info["rows_kept"], info["n2"]
+    gsz = rsz * (2 if spin else 1)
+    nnorth = (nt + 1) // 2
+    leg_flops = 8 * (3 if spin else 1) * legendre_triples(L, spin, nnorth)
+    ring_b = ncol * nt * esz
+    x_b = R * ncol * esz
+    grid_b = R * N2 * gsz
+    pt_b = npts * (4 + esz + 4 + (esz if spin else 0) + rsz * (2 if spin else 1))
+    return {
+        "legendre_synthesis": ("alu", leg_flops, "TFLOP/s"),
+        "legendre_adjoint": ("alu", leg_flops, "TFLOP/s"),
+        "theta_fwd": ("hbm", ring_b + x_b, "GB/s"),
+        "theta_adj": ("hbm", ring_b + x_b, "GB/s"),
+        "phi_fwd": ("hbm", x_b + grid_b, "GB/s"),
+        "phi_adj": ("hbm", x_b + grid_b, "GB/s"),
+        "interp": ("hbm", grid_b + pt_b, "GB/s"),
+        "spread": ("hbm", 2 * grid_b + pt_b, "GB/s"),
+    }
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2304_10431_gb300 import LensPlan, _native, lib_path
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _native.load()
+    peaks, peak_src = load_peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    lmax, nside = args.lmax, args.nside
+    th0, ph0, phi_lm, aT, aEB, ld = workload_arrays(lmax, nside)
+    npts = th0.size
+    th, ph, chi = deflect_on_gpu(th0, ph0, phi_lm, lmax, dev)
+    del th0, ph0
+
+    def make(prec, eps):
+        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, device=dev)
+        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, device=dev)
+        ct = pT.complex_dtype
+        a_T = torch.as_tensor(aT, dtype=ct, device=dev)
+        a_P = torch.as_tensor(aEB, dtype=ct, device=dev)
+        mT = pT.synthesis(a_T)
+        mP = pP.synthesis(a_P)
+        bufs = dict(a_T=a_T, a_P=a_P, m_T=mT, m_P=mP, o_mT=torch.empty_like(mT), o_mP=torch.empty_like(mP),
+                    o_aT=torch.empty_like(a_T), o_aP=torch.empty_like(a_P))
+        return pT, pP, bufs
+
+    def step(pT, pP, b):
+        pT.synthesis(b["a_T"], out=b["o_mT"])
+        pT.adjoint(b["m_T"], out=b["o_aT"])
+        pP.synthesis(b["a_P"], out=b["o_mP"])
+        pP.adjoint(b["m_P"], out=b["o_aP"])
+
+    stream = torch.cuda.current_stream()
+
+    def timed(pT, pP, b, steps, warmup, profile):
+        for _ in range(warmup):
+            step(pT, pP, b)
+        barrier()
+        lib.lens_profile_reset()
+        if profile:
+            lib.lens_profile_enable(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(pT, pP, b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lib.lens_profile_enable(0)
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def per_transform(pT, pP, b, reps=3):
+        out = {}
+        for name, fn in (("T_synthesis", lambda: pT.synthesis(b["a_T"], out=b["o_mT"])),
+                         ("T_adjoint", lambda: pT.adjoint(b["m_T"], out=b["o_aT"])),
+                         ("EB_synthesis", lambda: pP.synthesis(b["a_P"], out=b["o_mP"])),
+                         ("EB_adjoint", lambda: pP.adjoint(b["m_P"], out=b["o_aP"]))):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = npts / (e0.elapsed_time(e1) / reps * 1e-3)
+        return out
+
+    # ---------------- FP32 headline
+    pT, pP, b = make("fp32", 1e-5)
+    info_T, info_P = pT.info(), pP.info()
+    clk = ClockSampler(local)
+    clk.start()
+    ms = timed(pT, pP, b, args.steps, max(args.warmup, 3), profile=True)
+    clocks = clk.stop()
+    prof_ms = np.zeros(32)
+    cnt = np.zeros(32, dtype=np.int64)
+    lib.lens_profile_read(prof_ms.ctypes.data, cnt.ctypes.data, 32)
+    gpu_launches = None
+    pt = per_transform(pT, pP, b)
+
+    # dominant kernel and its roofline
+    units = {0: stage_units(info_T, npts, 0, "fp32"), 1: stage_units(info_P, npts, 2, "fp32")}
+    stage_rows = []
+    for slot in range(16):
+        if cnt[slot] == 0:
+            continue
+        sp = slot // 8
+        name = STAGES[slot % 8]
+        avg = prof_ms[slot] / cnt[slot]
+        bound, work, unit = units[sp][name]
+        stage_rows.append((prof_ms[slot] / args.steps, name, sp, avg, bound, work, unit, int(cnt[slot])))
+    stage_rows.sort(reverse=True)
+    top = stage_rows[0]
+    _, name, sp, avg, bound, work, unit, nl = top
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if bound == "alu":
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+        achieved = work / (avg * 1e-3) / 1e12
+        peak_note = "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_mhz_max
+    else:
+        peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+        achieved = work / (avg * 1e-3) / 1e9
+        peak_note = "HBM copy bandwidth (%s)" % peak_src
+    key = ("%s/spin%d/fp32" % (name, 2 if sp else 0), src_hash(KERNEL_FILES[name]))
+    traffic = NCU_TRAFFIC.get(key)
+    roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "%s (spin %d, fp32)" % (name, 2 if sp else 0), "avg_launch_ms": round(avg, 4),
+                "peak_source": peak_note}
+    stages = [{"stage": r[1], "spin": 2 if r[2] else 0, "ms_per_step": round(r[0], 4), "avg_launch_ms": round(r[3], 4),
+               "bound": r[4], "achieved": round(r[5] / (r[3] * 1e-3) / (1e12 if r[4] == "alu" else 1e9), 2),
+               "unit": r[6]} for r in stage_rows]
+    # our kernel launches per step: Legendre 1, theta 1, phi 1, interp 1 (fwd); spread 1, phi 1, theta 1,
+    # Legendre 1 (adj) -> 8 per spin, 16 per step (memsets excluded)
+    gpu_launches = 16 * args.steps
+
+    # ---------------- e2e through the host-buffer entry points (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        hT = b["a_T"].cpu().pin_memory()
+        hP = b["a_P"].cpu().pin_memory()
+        hmT = b["m_T"].cpu().pin_memory()
+        hmP = b["m_P"].cpu().pin_memory()
+        o_mT, o_mP = _t.empty_like(hmT).pin_memory(), _t.empty_like(hmP).pin_memory()
+        o_aT, o_aP = _t.empty_like(hT).pin_memory(), _t.empty_like(hP).pin_memory()
+
+        def hstep():
+            pT.synthesis_host(hT, o_mT)
+            pT.adjoint_host(hmT, o_aT)
+            pP.synthesis_host(hP, o_mP)
+            pP.adjoint_host(hmP, o_aP)
+
+        for _ in range(2):
+            hstep()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        barrier()
+        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        h2d = sum(x.numel() * x.element_size() for x in (hT, hP, hmT, hmP))
+        e2e = {"value": round(world * npts / (ems * 1e-3), 1), "unit": "lensed points/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3)}
+
+    # ---------------- FP64 plans (epsilon 1e-10), same geometry
+    fp64 = None
+    if not args.no_fp64:
+        del b
+        pT.close(); pP.close()
+        torch.cuda.empty_cache()
+        qT, qP, c = make("fp64", 1e-10)
+        k64 = max(1, min(args.steps, 3))
+        ms64 = timed(qT, qP, c, k64, 1, profile=True)
+        p64 = np.zeros(32)
+        c64 = np.zeros(32, dtype=np.int64)
+        lib.lens_profile_read(p64.ctypes.data, c64.ctypes.data, 32)
+        u64 = {0: stage_units(qT.info(), npts, 0, "fp64"), 1: stage_units(qP.info(), npts, 2, "fp64")}
+        rows64 = []
+        for slot in range(16, 32):
+            if c64[slot] == 0:
+                continue
+            s2 = (slot - 16) // 8
+            nm = STAGES[slot % 8]
+            av = p64[slot] / c64[slot]
+            bd, wk, un = u64[s2][nm]
+            rows64.append({"stage": nm, "spin": 2 if s2 else 0, "ms_per_step": round(p64[slot] / k64, 3),
+                           "avg_launch_ms": round(av, 3), "bound": bd,
+                           "achieved": round(wk / (av * 1e-3) / (1e12 if bd == "alu" else 1e9), 3),
+                           "unit": "TFLOP/s (FP64 ALU work)" if bd == "alu" else un})
+        rows64.sort(key=lambda r: -r["ms_per_step"])
+        fp64 = {"value": round(world * npts / (ms64 * 1e-3), 1), "unit": "lensed points/s", "epsilon": 1e-10,
+                "ms_per_step": round(ms64, 3), "steps": k64, "per_transform": per_transform(qT, qP, c, reps=1),
+                "plan": {k: qT.info()[k] for k in ("n1", "W", "sigma")} | {"W_spin2": qP.info()["W"]},
+                "stages": rows64}
+        qT.close(); qP.close()
+
+    result = {
+        "metric": "lensed points/sec (synthesis and adjoint), lmax 4096, eps 1e-5 FP32 vs 1e-10 FP64",
+        "value": round(world * npts / (ms * 1e-3), 1),
+        "unit": "lensed points/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (df32 Legendre recursion)",
+        "data": "synthetic: seeded CMB/phi a_lm, HEALPix centres lensed on the GPU",
+        "config": {"workload": "T + E/B lensing, lmax 4096, HEALPix Nside %d (%d points), phi lmax %d, "
+                               "2.5 arcmin rms deflection, l_damp %.0f" % (nside, npts, lmax, ld),
+                   "lmax": lmax, "nside": nside, "points": npts, "epsilon": 1e-5,
+                   "step": "T synthesis + T adjoint + E/B synthesis + E/B adjoint",
+                   "plan_T": {k: info_T[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
+                   "plan_EB": {k: info_P[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
+                   "l2": "per-step inputs 0.8 GB > 129 MB L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "per_transform": {k: round(v, 1) for k, v in pt.items()},
+        "roofline": roofline,
+        "stages": stages,
+        "gpu_launches": gpu_launches,
+        "library": os.path.relpath(lib_path(), ROOT),
+        "clocks": clocks,
+        "e2e": e2e,
+        "fp64": fp64,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(lmax, nside, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(lmax, nside, k, seed=0):
+    """k points of the same lensed geometry, spread over rings near both poles and the equator."""
+    import oracle as O
+    from paper_2304_10431_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    n = 12 * nside * nside
+    idx = np.sort(np.concatenate([rng.integers(0, n // 50, k // 4), rng.integers(n - n // 50, n, k // 4),
+                                  rng.integers(n // 2 - n // 20, n // 2 + n // 20, k - 2 * (k // 4))]))
+    th0, ph0 = W.healpix_centres(nside)
+    th0, ph0 = th0[idx], ph0[idx]
+    phi_lm = W.draw_alm(W.phi_cl(lmax), lmax, 2000)
+    th, ph, chi = O.deflected_points(th0, ph0, phi_lm, lmax)
+    return th, ph, chi
+
+
+def oracle_step(lmax, th, ph, chi, aT, aEB):
+    import oracle as O
+    mT = O.synthesis(lmax, lmax, 0, th, ph, aT)
+    O.adjoint(lmax, lmax, 0, th, ph, mT)
+    mP = O.synthesis(lmax, lmax, 2, th, ph, aEB, chi)
+    O.adjoint(lmax, lmax, 2, th, ph, mP, chi)
+
+
+def cpu_baseline(lmax, nside, seconds, steps=1, warmup=0, return_times=False):
+    import oracle as O
+    aT, aEB, _ = alm_inputs(lmax)
+    # calibrate on 8 points, then size the sample to ~`seconds` per step
+    th, ph, chi = oracle_sample(lmax, nside, 8, seed=1)
+    t0 = time.perf_counter()
+    oracle_step(lmax, th, ph, chi, aT, aEB)
+    per_pt = (time.perf_counter() - t0) / 8
+    k = int(max(8, min(4096, seconds / per_pt)))
+    th, ph, chi = oracle_sample(lmax, nside, k, seed=2)
+    for _ in range(warmup):
+        oracle_step(lmax, th, ph, chi, aT, aEB)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle_step(lmax, th, ph, chi, aT, aEB)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    res = {"value": round(k / t, 3), "unit": "lensed points/s", "cores": O.num_threads(), "kind": "oracle",
+           "sample": "%d lensed HEALPix points (Nside %d, near both poles and the equator), lmax %d, "
+                     "T + E/B synthesis and adjoint by direct FP64 summation" % (k, nside, lmax),
+           "seconds_per_step": round(t, 3)}
+    return (res, t) if return_times else res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps, warmup = args.steps, max(args.warmup, 0)
+    per_step = max(2.0, 150.0 / max(steps + warmup, 1))
+    cb, t = cpu_baseline(args.lmax, args.nside, per_step, steps=steps, warmup=warmup, return_times=True)
+    out = {"metric": "lensed points/sec (synthesis and adjoint), lmax 4096, eps 1e-5 FP32 vs 1e-10 FP64",
+           "value": cb["value"], "unit": "lensed points/s", "n_gpus": args.gpus, "steps": steps,
+           "warmup": warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded CMB/phi a_lm, lensed HEALPix sample",
+           "config": {"workload": "T + E/B lensing, lmax %d, HEALPix Nside %d sample" % (args.lmax, args.nside),
+                      "lmax": args.lmax, "nside": args.nside},
+           "impl": "reference", "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "lensed points/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

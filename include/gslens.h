@@ -181,6 +181,25 @@ int lens_pointing(int64_t n, const double *theta_d, const double *phi_d,
                   const double *alpha_theta_d, const double *alpha_phi_d,
                   double *theta_out_d, double *phi_out_d, double *chi_out_d, void *stream);
 
+/*
+ * Stage timers.  While enabled, every transform records a CUDA event pair
+ * around each of its kernel stages on the stream it launches on; the pairs
+ * are resolved by lens_profile_read.  Slots (index = stage + 8 * (spin > 0)
+ * + 16 * (prec == LENS_FP64)), stage = 0 Legendre synthesis, 1 theta
+ * transform (forward), 2 phi transform (forward), 3 interpolation,
+ * 4 spreading, 5 phi transform (adjoint), 6 theta transform (adjoint),
+ * 7 adjoint Legendre.  Process-wide; not thread-safe with concurrent calls.
+ *   lens_profile_enable(1/0)  start / stop recording (recording keeps totals)
+ *   lens_profile_read(ms, counts, n)  synchronises the recorded events, adds
+ *       their durations into per-slot totals and copies slots [0, n) out
+ *       (ms: double[n] total milliseconds, counts: int64[n] launches; either
+ *       may be NULL); n <= 32.
+ *   lens_profile_reset()  clears totals and pending events.
+ */
+int lens_profile_enable(int on);
+int lens_profile_read(double *ms, int64_t *counts, int n);
+int lens_profile_reset(void);
+
 /* Number of a_lm for (lmax, mmax). */
 int64_t lens_nalm(int lmax, int mmax);
 

@@ -26,6 +26,9 @@ EXPORTS = {
     "lens_ring_synthesis": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_adjoint": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_pointing": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "lens_profile_enable": (_i32, [_i32]),
+    "lens_profile_read": (_i32, [_vp, _vp, _i32]),
+    "lens_profile_reset": (_i32, []),
     "lens_nalm": (_i64, [_i32, _i32]),
     "lens_status_string": (ctypes.c_char_p, [_i32]),
     "lens_get_last_error": (_i32, []),

@@ -75,6 +75,9 @@ struct Plan {
     void *grid = nullptr;      // [R][pitch] real (spin 0) or complex
     unsigned *flags = nullptr; // device status flags
 
+    // device staging for the host-buffer entry points (allocated on first use)
+    void *stage_in = nullptr, *stage_out = nullptr;
+
     size_t plan_bytes = 0, work_bytes = 0;
     void *allocs[64];
     int nallocs = 0;

@@ -468,6 +468,51 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
 
 namespace {
 
+// ------------------------------------------------------------ stage timers
+struct Profiler {
+    bool on = false;
+    double ms[32] = {0};
+    int64_t cnt[32] = {0};
+    struct Rec { int slot; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void drain()
+    {
+        for (auto &r : pending) {
+            float t = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+                ms[r.slot] += t;
+                cnt[r.slot] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+};
+Profiler g_prof;
+
+// Runs one stage launch, bracketed by events when the profiler is on.
+template <class F> cudaError_t staged(const Plan &p, int stage, cudaStream_t st, F &&launch)
+{
+    if (!g_prof.on) return launch();
+    const int slot = stage + 8 * (p.spin > 0) + 16 * (p.prec == LENS_FP64);
+    cudaEvent_t a = g_prof.get(), b = g_prof.get();
+    cudaEventRecord(a, st);
+    cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    g_prof.pending.push_back({slot, a, b});
+    if (g_prof.pending.size() > 4096) g_prof.drain();
+    return e;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -486,20 +531,28 @@ struct DeviceGuard {
 int forward_one(const Plan &p, const void *alm, void *map, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = launch_legendre_fwd(p, alm, p.ring, st)) != cudaSuccess) return cuda_fail(e, "legendre synthesis");
-    if ((e = launch_theta_fwd(p, p.ring, p.X, st)) != cudaSuccess) return cuda_fail(e, "theta transform");
-    if ((e = launch_phi_fwd(p, p.X, p.grid, st)) != cudaSuccess) return cuda_fail(e, "phi transform");
-    if ((e = launch_interp(p, p.grid, map, st)) != cudaSuccess) return cuda_fail(e, "interpolation");
+    if ((e = staged(p, 0, st, [&] { return launch_legendre_fwd(p, alm, p.ring, st); })) != cudaSuccess)
+        return cuda_fail(e, "legendre synthesis");
+    if ((e = staged(p, 1, st, [&] { return launch_theta_fwd(p, p.ring, p.X, st); })) != cudaSuccess)
+        return cuda_fail(e, "theta transform");
+    if ((e = staged(p, 2, st, [&] { return launch_phi_fwd(p, p.X, p.grid, st); })) != cudaSuccess)
+        return cuda_fail(e, "phi transform");
+    if ((e = staged(p, 3, st, [&] { return launch_interp(p, p.grid, map, st); })) != cudaSuccess)
+        return cuda_fail(e, "interpolation");
     return LENS_OK;
 }
 
 int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = launch_spread(p, map, p.grid, st)) != cudaSuccess) return cuda_fail(e, "spreading");
-    if ((e = launch_phi_adj(p, p.grid, p.X, st)) != cudaSuccess) return cuda_fail(e, "phi transform");
-    if ((e = launch_theta_adj(p, p.X, p.ring, st)) != cudaSuccess) return cuda_fail(e, "theta transform");
-    if ((e = launch_legendre_adj(p, p.ring, alm, st)) != cudaSuccess) return cuda_fail(e, "adjoint legendre");
+    if ((e = staged(p, 4, st, [&] { return launch_spread(p, map, p.grid, st); })) != cudaSuccess)
+        return cuda_fail(e, "spreading");
+    if ((e = staged(p, 5, st, [&] { return launch_phi_adj(p, p.grid, p.X, st); })) != cudaSuccess)
+        return cuda_fail(e, "phi transform");
+    if ((e = staged(p, 6, st, [&] { return launch_theta_adj(p, p.X, p.ring, st); })) != cudaSuccess)
+        return cuda_fail(e, "theta transform");
+    if ((e = staged(p, 7, st, [&] { return launch_legendre_adj(p, p.ring, alm, st); })) != cudaSuccess)
+        return cuda_fail(e, "adjoint legendre");
     return LENS_OK;
 }
 
@@ -546,10 +599,20 @@ static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, voi
     DeviceGuard g(p.device);
     cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
     const size_t ab = alm_bytes(p), mb = map_bytes(p);
-    void *d_in = nullptr, *d_out = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d_in, fwd ? ab : mb)) != cudaSuccess) return cuda_fail(e, "staging alloc");
-    if ((e = cudaMalloc(&d_out, fwd ? mb : ab)) != cudaSuccess) { cudaFree(d_in); return cuda_fail(e, "staging alloc"); }
+    if (!p.stage_in) {  // one alm-sized and one map-sized buffer, kept by the plan
+        const size_t big = std::max(ab, mb) > 0 ? std::max(ab, mb) : 16;
+        if ((e = cudaMalloc(&p.stage_in, big)) != cudaSuccess) { p.stage_in = nullptr; return cuda_fail(e, "staging alloc"); }
+        if ((e = cudaMalloc(&p.stage_out, big)) != cudaSuccess) {
+            cudaFree(p.stage_in);
+            p.stage_in = nullptr;
+            return cuda_fail(e, "staging alloc");
+        }
+        p.allocs[p.nallocs++] = p.stage_in;
+        p.allocs[p.nallocs++] = p.stage_out;
+        p.work_bytes += 2 * big;
+    }
+    void *d_in = p.stage_in, *d_out = p.stage_out;
     int rc = LENS_OK;
     for (int i = 0; i < nmaps && rc == LENS_OK; ++i) {
         const size_t ib = fwd ? ab : mb, ob = fwd ? mb : ab;
@@ -566,8 +629,6 @@ static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, voi
     }
     e = cudaStreamSynchronize(st);
     if (rc == LENS_OK && e != cudaSuccess) rc = cuda_fail(e, "stream sync");
-    cudaFree(d_in);
-    cudaFree(d_out);
     return rc;
 }
 
@@ -599,6 +660,30 @@ int lens_ring_adjoint(lens_plan pl, const void *ring_d, void *alm_d, void *strea
     cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
     cudaError_t e = launch_legendre_adj(p, ring_d, alm_d, st);
     return e == cudaSuccess ? LENS_OK : cuda_fail(e, "adjoint legendre");
+}
+
+int lens_profile_enable(int on)
+{
+    g_prof.on = on != 0;
+    return LENS_OK;
+}
+
+int lens_profile_read(double *ms, int64_t *counts, int n)
+{
+    if (n < 0 || n > 32) return fail(LENS_ERR_INVALID, "n must be in [0, 32]");
+    g_prof.drain();
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = g_prof.ms[i];
+        if (counts) counts[i] = g_prof.cnt[i];
+    }
+    return LENS_OK;
+}
+
+int lens_profile_reset(void)
+{
+    g_prof.drain();
+    for (int i = 0; i < 32; ++i) { g_prof.ms[i] = 0; g_prof.cnt[i] = 0; }
+    return LENS_OK;
 }
 
 int lens_pointing(int64_t n, const double *theta_d, const double *phi_d, const double *ath_d, const double *aph_d,
