@@ -68,6 +68,19 @@ __device__ __forceinline__ df32 df_sub(df32 a, df32 b)
     return {h, l};
 }
 
+// a - b without the final renormalisation: (s, e) with s = fl(a.h - b.h) and
+// e the exact two-sum error plus the low parts, so s + e carries the full
+// df32 accuracy and |e| is at most a few ulp of max(|a|, |b|).  df_mul accepts
+// such pairs; s alone is off from a - b by at most |e|.
+__device__ __forceinline__ df32 df_sub_u(df32 a, df32 b)
+{
+    float s = __fsub_rn(a.h, b.h);
+    float bb = __fsub_rn(s, a.h);
+    float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(-b.h, bb));
+    err = __fadd_rn(err, __fsub_rn(a.l, b.l));
+    return {s, err};
+}
+
 __device__ __forceinline__ df32 df_scale_pow2(df32 a, float p2) { return {a.h * p2, a.l * p2}; }
 
 // Status flags written by kernels (bitwise OR).  No kernel traps.

@@ -17,10 +17,15 @@
 // Values are carried as mantissa * 2^(60 E) so that sin^m theta cannot
 // underflow; contributions with E <= -2 are below 2^-60 and dropped.
 //
-// Mapping: one CTA per (m, ring chunk); each thread owns RPT north rings
-// (theta <= pi/2) and obtains the mirrored south ring from
+// Mapping: one CTA per (m, ring chunk); each thread owns RPT adjacent north
+// rings (theta <= pi/2) and obtains the mirrored south ring from
 //   s lambda_lm(pi - theta) = (-1)^{l+m} (-s)lambda_lm(theta).
+// Work proceeds in blocks of l; a warp vote picks one of three regimes per
+// block: every state at scale 0 (no checks), every state at scale <= -4
+// (contributions below 2^-180 for the whole block: recursion only), or mixed.
 // Recursion coefficients are read with warp-uniform addresses (L1 broadcast).
+// The adjoint reduces over rings inside each warp (transpose-reduce over a
+// block of l) and adds the warp's sums into a_lm with one atomic per lane.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -34,6 +39,7 @@ constexpr float kBigF = 0x1p60f;
 constexpr float kSmallF = 0x1p-60f;
 constexpr double kBigD = 0x1p60;
 constexpr double kSmallD = 0x1p-60;
+constexpr int kSkipE = -4;  // below 2^-240 before the block, < 2^-180 after 8 steps of growth <= 2^8.5
 
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
@@ -59,18 +65,31 @@ struct PolDF {  // df32 recursion, FP32 accumulation
         float2 v = __ldg(rt.xdf + j);
         return {v.x, v.y};
     }
-    static __device__ __forceinline__ X add(X a, X b) { return df_sub(a, {-b.h, -b.l}); }
-    static __device__ __forceinline__ X sub(X a, X b) { return df_sub(a, b); }
+    static __device__ __forceinline__ X add(X a, X b) { return df_sub_u(a, {-b.h, -b.l}); }
+    static __device__ __forceinline__ X sub(X a, X b) { return df_sub_u(a, b); }
     static __device__ __forceinline__ void step(St &s, X y, const Co &c)
     {
         df32 t = df_mul(y, s.cur);
         df32 v = df_mul(c.A, t);
         df32 w = df_mul(c.B, s.prev);
         s.prev = s.cur;
-        s.cur = df_sub(v, w);
+        s.cur = df_sub_u(v, w);
     }
-    static __device__ __forceinline__ R val(const St &s) { return s.cur.h; }
-    static __device__ __forceinline__ void maybe_rescale(St &s)
+    // The state is not renormalised after every step (the low word carries
+    // the compensation of the high-word recursion), so the value is h + l.
+    static __device__ __forceinline__ R val(const St &s) { return __fadd_rn(s.cur.h, s.cur.l); }
+    static __device__ __forceinline__ df32 norm(df32 a)  // two-sum: exact for any ordering of |h|, |l|
+    {
+        const float h = __fadd_rn(a.h, a.l);
+        const float bb = __fsub_rn(h, a.h);
+        return {h, __fadd_rn(__fsub_rn(a.h, __fsub_rn(h, bb)), __fsub_rn(a.l, bb))};
+    }
+    static __device__ __forceinline__ void renorm(St &s)
+    {
+        s.cur = norm(s.cur);
+        s.prev = norm(s.prev);
+    }
+    static __device__ __forceinline__ void rescale(St &s)
     {
         if (s.E < 0 && fabsf(s.cur.h) > kBigF) {
             s.cur = df_scale_pow2(s.cur, kSmallF);
@@ -91,6 +110,7 @@ struct PolDF {  // df32 recursion, FP32 accumulation
         s.cur = {sign < 0 ? -m : m, 0.f};
         s.E = (int)e;
     }
+    static __device__ __forceinline__ void zero(St &s) { s.cur = {0.f, 0.f}; s.prev = s.cur; s.E = 0; }
 };
 
 struct PolF64 {  // native FP64
@@ -115,7 +135,8 @@ struct PolF64 {  // native FP64
         s.cur = n;
     }
     static __device__ __forceinline__ R val(const St &s) { return s.cur; }
-    static __device__ __forceinline__ void maybe_rescale(St &s)
+    static __device__ __forceinline__ void renorm(St &) {}
+    static __device__ __forceinline__ void rescale(St &s)
     {
         if (s.E < 0 && fabs(s.cur) > kBigD) {
             s.cur *= kSmallD;
@@ -134,6 +155,7 @@ struct PolF64 {  // native FP64
         s.cur = sign < 0 ? -m : m;
         s.E = (int)e;
     }
+    static __device__ __forceinline__ void zero(St &s) { s.cur = 0.0; s.prev = 0.0; s.E = 0; }
 };
 
 // Start value of sigma lambda_{l0,m} at ring j (north half), sigma = +-s.
@@ -158,6 +180,55 @@ __device__ __forceinline__ void start_value(typename P::St &st, int m, int s, in
     P::start(st, L2, sign, zero);
 }
 
+// Regime of the next block of l for the whole warp: 0 all states at scale 0,
+// 1 all states negligible (scale <= kSkipE), 2 mixed.
+template <class P, int RPT, bool SPIN>
+__device__ __forceinline__ int warp_regime(typename P::St (&sp)[RPT], typename P::St (&sm)[RPT])
+{
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {  // keep the df32 low words small (once per block)
+        P::renorm(sp[k]);
+        if (SPIN) P::renorm(sm[k]);
+    }
+    bool all0 = true, allneg = true;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        all0 = all0 && sp[k].E == 0;
+        allneg = allneg && sp[k].E <= kSkipE;
+        if (SPIN) {
+            all0 = all0 && sm[k].E == 0;
+            allneg = allneg && sm[k].E <= kSkipE;
+        }
+    }
+    if (__all_sync(0xffffffffu, all0)) return 0;
+    if (__all_sync(0xffffffffu, allneg)) return 1;
+    return 2;
+}
+
+// One recursion step of all states owned by the thread to degree l.
+template <class P, int RPT, bool SPIN, bool CHECK>
+__device__ __forceinline__ void advance(typename P::St (&sp)[RPT], typename P::St (&sm)[RPT],
+                                        const typename P::X (&x)[RPT], const void *rec_ab, const void *rec_c,
+                                        int64_t idx)
+{
+    const typename P::Co co = P::load(rec_ab, idx);
+    if (!SPIN) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            P::step(sp[k], x[k], co);
+            if (CHECK) P::rescale(sp[k]);
+        }
+    } else {
+        const typename P::X t = P::load_t(rec_c, idx);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            P::step(sp[k], P::add(x[k], t), co);
+            P::step(sm[k], P::sub(x[k], t), co);
+            if (CHECK) { P::rescale(sp[k]); P::rescale(sm[k]); }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- forward
 template <class P, int RPT, bool SPIN>
 __global__ void __launch_bounds__(512) k_leg_fwd(const typename P::C *__restrict__ alm, const void *__restrict__ rec_ab,
@@ -169,116 +240,85 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const typename P::C *__restrict
     using Cx = typename P::C;
     using St = typename P::St;
     using X = typename P::X;
+    constexpr int BLK = 8;
     const int m = blockIdx.y;
-    const int nthr = blockDim.x;
-    const int per_chunk = nthr * RPT;
+    const int per_chunk = blockDim.x * RPT;
     const int64_t base = alm_base(lmax, m);
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
-    if (l0 > lmax) return;  // nothing to do: columns stay as written below? (zeroed by caller)
+    if (l0 > lmax) return;
 
     X x[RPT];
     St sp[RPT], sm[RPT];
     Cx pn[RPT], ps[RPT], qn[RPT], qs[RPT];
-    int rp[RPT];
+    const int rp0 = blockIdx.x * per_chunk + threadIdx.x * RPT;
     const double lnm = lognorm[m];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        rp[k] = blockIdx.x * per_chunk + k * nthr + threadIdx.x;
+        const int rp = rp0 + k;
         pn[k] = mkc(R(0), R(0)); ps[k] = pn[k]; qn[k] = pn[k]; qs[k] = pn[k];
-        if (rp[k] < nnorth) {
-            x[k] = P::ring_x(rt, rp[k]);
-            double ls = rt.lsin2[rp[k]], lc = rt.lcos2[rp[k]];
+        if (rp < nnorth) {
+            x[k] = P::ring_x(rt, rp);
+            const double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
             start_value<P>(sp[k], m, s, s, lnm, ls, lc);
             if (SPIN) start_value<P>(sm[k], m, s, -s, lnm, ls, lc);
         } else {
             x[k] = X{};
-            P::start(sp[k], 0.0, 1, true);
-            sp[k].E = 0;
-            if (SPIN) { P::start(sm[k], 0.0, 1, true); sm[k].E = 0; }
+            P::zero(sp[k]);
+            P::zero(sm[k]);
         }
     }
     const Cx *aG = alm;
     const Cx *aC = alm + nalm;
     const R sgs = (s & 1) ? R(-1) : R(1);
 
-    auto accumulate = [&](int l, bool fast) {
+    auto accumulate = [&](int l, bool scaled) {
         Cx g = __ldg(aG + base + l);
         if (m == 0) g.y = R(0);
-        const bool odd = ((l - m) & 1) != 0;
+        const R sg = ((l - m) & 1) ? R(-1) : R(1);
         if (!SPIN) {
-            Cx gs = odd ? mkc(-g.x, -g.y) : g;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 R v = P::val(sp[k]);
-                if (!fast) v *= P::fac(sp[k].E);
+                if (scaled) v *= P::fac(sp[k].E);
+                const R vs = sg * v;
                 pn[k].x += g.x * v; pn[k].y += g.y * v;
-                ps[k].x += gs.x * v; ps[k].y += gs.y * v;
+                ps[k].x += g.x * vs; ps[k].y += g.y * vs;
             }
         } else {
             Cx c = __ldg(aC + base + l);
             if (m == 0) c.y = R(0);
             // a = G + iC ; b = (-1)^s (conj G + i conj C)
-            Cx a = mkc(g.x - c.y, g.y + c.x);
-            Cx b = mkc(sgs * (g.x + c.y), sgs * (c.x - g.y));
-            Cx as = odd ? mkc(-a.x, -a.y) : a;
-            Cx bs = odd ? mkc(-b.x, -b.y) : b;
+            const Cx a = mkc(g.x - c.y, g.y + c.x);
+            const Cx b = mkc(sgs * (g.x + c.y), sgs * (c.x - g.y));
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 R vp = P::val(sp[k]), vm = P::val(sm[k]);
-                if (!fast) { vp *= P::fac(sp[k].E); vm *= P::fac(sm[k].E); }
+                if (scaled) { vp *= P::fac(sp[k].E); vm *= P::fac(sm[k].E); }
+                const R vps = sg * vp, vms = sg * vm;
                 pn[k].x += a.x * vp; pn[k].y += a.y * vp;     // north, column +m
-                ps[k].x += as.x * vm; ps[k].y += as.y * vm;   // south, column +m
+                ps[k].x += a.x * vms; ps[k].y += a.y * vms;   // south, column +m
                 qn[k].x += b.x * vm; qn[k].y += b.y * vm;     // north, column -m
-                qs[k].x += bs.x * vp; qs[k].y += bs.y * vp;   // south, column -m
+                qs[k].x += b.x * vps; qs[k].y += b.y * vps;   // south, column -m
             }
         }
     };
 
-    accumulate(l0, false);
-    int l = l0 + 1;
-    while (l <= lmax) {
-        const int lend = min(l + 16, lmax + 1);
-        bool all0 = true;
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            all0 = all0 && sp[k].E == 0;
-            if (SPIN) all0 = all0 && sm[k].E == 0;
-        }
-        const bool fast = __all_sync(0xffffffffu, all0);
-        if (fast) {
-            for (; l < lend; ++l) {
-                typename P::Co co = P::load(rec_ab, base + l);
-                if (!SPIN) {
-#pragma unroll
-                    for (int k = 0; k < RPT; ++k) P::step(sp[k], x[k], co);
-                } else {
-                    X t = P::load_t(rec_c, base + l);
-#pragma unroll
-                    for (int k = 0; k < RPT; ++k) {
-                        P::step(sp[k], P::add(x[k], t), co);
-                        P::step(sm[k], P::sub(x[k], t), co);
-                    }
-                }
-                accumulate(l, true);
-            }
-        } else {
-            for (; l < lend; ++l) {
-                typename P::Co co = P::load(rec_ab, base + l);
-                if (!SPIN) {
-#pragma unroll
-                    for (int k = 0; k < RPT; ++k) { P::step(sp[k], x[k], co); P::maybe_rescale(sp[k]); }
-                } else {
-                    X t = P::load_t(rec_c, base + l);
-#pragma unroll
-                    for (int k = 0; k < RPT; ++k) {
-                        P::step(sp[k], P::add(x[k], t), co);
-                        P::maybe_rescale(sp[k]);
-                        P::step(sm[k], P::sub(x[k], t), co);
-                        P::maybe_rescale(sm[k]);
-                    }
-                }
+    accumulate(l0, true);
+    for (int lb = l0 + 1; lb <= lmax; lb += BLK) {
+        const int lend = min(lb + BLK, lmax + 1);
+        const int regime = warp_regime<P, RPT, SPIN>(sp, sm);
+        if (regime == 0) {
+            for (int l = lb; l < lend; ++l) {
+                advance<P, RPT, SPIN, false>(sp, sm, x, rec_ab, rec_c, base + l);
                 accumulate(l, false);
+            }
+        } else if (regime == 1) {
+            for (int l = lb; l < lend; ++l) advance<P, RPT, SPIN, true>(sp, sm, x, rec_ab, rec_c, base + l);
+        } else {
+            for (int l = lb; l < lend; ++l) {
+                advance<P, RPT, SPIN, true>(sp, sm, x, rec_ab, rec_c, base + l);
+                accumulate(l, true);
             }
         }
     }
@@ -286,8 +326,9 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const typename P::C *__restrict
     // write: spin 0 column m; spin s columns mmax + m (P) and mmax - m (Q), with the minus sign
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        if (rp[k] >= nnorth) continue;
-        const int jn = rp[k], js = ntheta - 1 - jn;
+        const int jn = rp0 + k;
+        if (jn >= nnorth) continue;
+        const int js = ntheta - 1 - jn;
         if (!SPIN) {
             Cx *col = ring + (int64_t)m * ntheta;
             col[jn] = pn[k];
@@ -342,7 +383,7 @@ template <class P, int RPT, bool SPIN, int LCH>
 __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_ab,
                                                  const void *__restrict__ rec_c, const double *__restrict__ lognorm,
                                                  RingTab rt, typename P::C *__restrict__ alm, int lmax, int mmax,
-                                                 int spin, int ntheta, int nnorth, int64_t nalm, int atomic_out)
+                                                 int spin, int ntheta, int nnorth, int64_t nalm)
 {
     using R = typename P::R;
     using Cx = typename P::C;
@@ -350,15 +391,15 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     using X = typename P::X;
     constexpr int NCOMP = SPIN ? 4 : 2;  // reals per l: spin 0 (re, im); spin s U, V
     constexpr int NV = LCH * NCOMP;
-    __shared__ R red[2][16][NV];  // [buffer][warp][value]
+    constexpr int SH = (NV == 32 ? 0 : NV == 16 ? 1 : NV == 8 ? 2 : NV == 4 ? 3 : NV == 2 ? 4 : 5);
 
     const int m = blockIdx.y;
-    const int nthr = blockDim.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = nthr >> 5;
-    const int per_chunk = nthr * RPT;
+    const int lane = threadIdx.x & 31;
+    const int per_chunk = blockDim.x * RPT;
     const int64_t base = alm_base(lmax, m);
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
+    if (l0 > lmax) return;
     const R sgs = (s & 1) ? R(-1) : R(1);
 
     X x[RPT];
@@ -366,14 +407,15 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     // spin 0: hn/hs = ring values at north/south ring of column m.
     // spin s: hn/hs column +m, gn/gs column -m.
     Cx hn[RPT], hs[RPT], gn[RPT], gs[RPT];
+    const int rp0 = blockIdx.x * per_chunk + threadIdx.x * RPT;
     const double lnm = lognorm[m];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        const int rp = blockIdx.x * per_chunk + k * nthr + threadIdx.x;
+        const int rp = rp0 + k;
         hn[k] = mkc(R(0), R(0)); hs[k] = hn[k]; gn[k] = hn[k]; gs[k] = hn[k];
         if (rp < nnorth) {
             x[k] = P::ring_x(rt, rp);
-            double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
+            const double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
             start_value<P>(sp[k], m, s, s, lnm, ls, lc);
             if (SPIN) start_value<P>(sm[k], m, s, -s, lnm, ls, lc);
             const int js = ntheta - 1 - rp;
@@ -387,106 +429,85 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
             }
         } else {
             x[k] = X{};
-            P::start(sp[k], 0.0, 1, true);
-            sp[k].E = 0;
-            if (SPIN) { P::start(sm[k], 0.0, 1, true); sm[k].E = 0; }
+            P::zero(sp[k]);
+            P::zero(sm[k]);
+        }
+    }
+    // spin 0: p = H_N + H_S (even l+m) and q = H_N - H_S (odd l+m)
+    if (!SPIN) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const Cx a = hn[k], b = hs[k];
+            hn[k] = cadd(a, b);
+            hs[k] = csub(a, b);
         }
     }
 
-    int buf = 0;
     for (int lc0 = l0; lc0 <= lmax; lc0 += LCH) {
+        const int regime = warp_regime<P, RPT, SPIN>(sp, sm);
+        const bool scaled = regime != 0;
         R part[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) part[i] = R(0);
-        bool all0 = true;
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            all0 = all0 && sp[k].E == 0;
-            if (SPIN) all0 = all0 && sm[k].E == 0;
-        }
-        const bool fast = __all_sync(0xffffffffu, all0);
 #pragma unroll
         for (int i = 0; i < LCH; ++i) {
             const int l = lc0 + i;
             if (l <= lmax) {
                 if (l > l0) {
-                    typename P::Co co = P::load(rec_ab, base + l);
-                    if (!SPIN) {
-#pragma unroll
-                        for (int k = 0; k < RPT; ++k) {
-                            P::step(sp[k], x[k], co);
-                            if (!fast) P::maybe_rescale(sp[k]);
-                        }
-                    } else {
-                        X t = P::load_t(rec_c, base + l);
-#pragma unroll
-                        for (int k = 0; k < RPT; ++k) {
-                            P::step(sp[k], P::add(x[k], t), co);
-                            P::step(sm[k], P::sub(x[k], t), co);
-                            if (!fast) { P::maybe_rescale(sp[k]); P::maybe_rescale(sm[k]); }
-                        }
-                    }
+                    if (scaled) advance<P, RPT, SPIN, true>(sp, sm, x, rec_ab, rec_c, base + l);
+                    else advance<P, RPT, SPIN, false>(sp, sm, x, rec_ab, rec_c, base + l);
                 }
-                const bool odd = ((l - m) & 1) != 0;
+                if (regime != 1) {
+                    const bool odd = ((l - m) & 1) != 0;
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) {
-                    R vp = P::val(sp[k]);
-                    if (!fast) vp *= P::fac(sp[k].E);
-                    if (!SPIN) {
-                        // lambda (H_N + (-1)^{l+m} H_S)
-                        Cx h = odd ? csub(hn[k], hs[k]) : cadd(hn[k], hs[k]);
-                        part[i * 2 + 0] += vp * h.x;
-                        part[i * 2 + 1] += vp * h.y;
-                    } else {
-                        R vm = P::val(sm[k]);
-                        if (!fast) vm *= P::fac(sm[k].E);
-                        const R sg = odd ? R(-1) : R(1);
-                        // U += lam+ H_m(N) + sg lam- H_m(S) ; V += lam- H_-m(N) + sg lam+ H_-m(S)
-                        part[i * 4 + 0] += vp * hn[k].x + sg * vm * hs[k].x;
-                        part[i * 4 + 1] += vp * hn[k].y + sg * vm * hs[k].y;
-                        part[i * 4 + 2] += vm * gn[k].x + sg * vp * gs[k].x;
-                        part[i * 4 + 3] += vm * gn[k].y + sg * vp * gs[k].y;
+                    for (int k = 0; k < RPT; ++k) {
+                        R vp = P::val(sp[k]);
+                        if (scaled) vp *= P::fac(sp[k].E);
+                        if (!SPIN) {
+                            const Cx h = odd ? hs[k] : hn[k];
+                            part[i * 2 + 0] += vp * h.x;
+                            part[i * 2 + 1] += vp * h.y;
+                        } else {
+                            R vm = P::val(sm[k]);
+                            if (scaled) vm *= P::fac(sm[k].E);
+                            const R sg = odd ? R(-1) : R(1);
+                            const R vms = sg * vm, vps = sg * vp;
+                            // U += lam+ H_m(N) + sg lam- H_m(S) ; V += lam- H_-m(N) + sg lam+ H_-m(S)
+                            part[i * 4 + 0] += vp * hn[k].x + vms * hs[k].x;
+                            part[i * 4 + 1] += vp * hn[k].y + vms * hs[k].y;
+                            part[i * 4 + 2] += vm * gn[k].x + vps * gs[k].x;
+                            part[i * 4 + 3] += vm * gn[k].y + vps * gs[k].y;
+                        }
                     }
                 }
             }
         }
-        // warp reduction: lane t ends with value index t >> (5 - log2 NV)
+        if (regime == 1) continue;  // every contribution of this block is below 2^-180
+        // warp reduction: lane t ends with value index t >> SH
         R tot = warp_transpose_reduce<NV, R>(part);
-        constexpr int SH = (NV == 32 ? 0 : NV == 16 ? 1 : NV == 8 ? 2 : NV == 4 ? 3 : NV == 2 ? 4 : 5);
-        if ((lane & ((1 << SH) - 1)) == 0) red[buf][warp][lane >> SH] = tot;
-        __syncthreads();
-        if (threadIdx.x < LCH) {
-            const int i = threadIdx.x;
-            const int l = lc0 + i;
-            if (l <= lmax) {
-                R acc[NCOMP];
-#pragma unroll
-                for (int c = 0; c < NCOMP; ++c) acc[c] = R(0);
-                for (int w = 0; w < nwarp; ++w) {
-#pragma unroll
-                    for (int c = 0; c < NCOMP; ++c) acc[c] += red[buf][w][i * NCOMP + c];
-                }
-                if (!SPIN) {
-                    Cx o = mkc(acc[0], m == 0 ? R(0) : acc[1]);
-                    if (atomic_out) { atomicAdd(&alm[base + l].x, o.x); if (m) atomicAdd(&alm[base + l].y, o.y); }
-                    else alm[base + l] = o;
-                } else {
-                    // G = -(U + sgs conj V)/2 ; C = i (U - sgs conj V)/2
-                    const R ux = acc[0], uy = acc[1], vx = sgs * acc[2], vy = -sgs * acc[3];
-                    Cx G = mkc(R(-0.5) * (ux + vx), R(-0.5) * (uy + vy));
-                    Cx Cc = mkc(R(-0.5) * (uy - vy), R(0.5) * (ux - vx));
-                    if (m == 0) { G.y = R(0); Cc.y = R(0); }
-                    if (atomic_out) {
-                        atomicAdd(&alm[base + l].x, G.x); atomicAdd(&alm[base + l].y, G.y);
-                        atomicAdd(&alm[nalm + base + l].x, Cc.x); atomicAdd(&alm[nalm + base + l].y, Cc.y);
-                    } else {
-                        alm[base + l] = G;
-                        alm[nalm + base + l] = Cc;
-                    }
-                }
+        const int v = lane >> SH;
+        const int i = v / NCOMP, c = v % NCOMP;
+        const int l = lc0 + i;
+        R *out = reinterpret_cast<R *>(alm);
+        if (!SPIN) {
+            if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1))
+                atomicAdd(out + 2 * (base + l) + c, tot);
+        } else {
+            // lanes hold U.re, U.im, V.re, V.im of degree l at c = 0..3; the
+            // G/C split is linear, so each warp adds its share directly:
+            //   G.re = -(U.re + sgs V.re)/2   G.im = -(U.im - sgs V.im)/2
+            //   C.re = -(U.im + sgs V.im)/2   C.im =  (U.re - sgs V.re)/2
+            const R other = __shfl_xor_sync(0xffffffffu, tot, 2 << SH);  // U <-> V of the same l
+            if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax) {
+                R val;
+                int64_t dst;
+                if (c == 0) { val = R(-0.5) * (tot + sgs * other); dst = 2 * (base + l); }
+                else if (c == 1) { val = R(-0.5) * (tot - sgs * other); dst = 2 * (base + l) + 1; }
+                else if (c == 2) { val = R(0.5) * (other - sgs * tot); dst = 2 * (nalm + base + l) + 1; }
+                else { val = R(-0.5) * (other + sgs * tot); dst = 2 * (nalm + base + l); }
+                if (!(m == 0 && (c == 1 || c == 2))) atomicAdd(out + dst, val);
             }
         }
-        buf ^= 1;
     }
 }
 
@@ -538,14 +559,11 @@ cudaError_t adj_launch(const Plan &p, const void *ring, void *alm, cudaStream_t 
     dim3 grid(p.leg_chunks, p.mmax + 1);
     dim3 block(p.leg_warps * 32);
     const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * (SPIN ? 2 : 1);
-    const int atomic_out = p.leg_chunks > 1;
-    if (atomic_out) {
-        cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);
+    if (e != cudaSuccess) return e;
     k_leg_adj<P, RPT, SPIN, LCH><<<grid, block, 0, st>>>((const typename P::C *)ring, p.rec_ab, p.rec_c, p.lognorm,
                                                          p.rings, (typename P::C *)alm, p.lmax, p.mmax, p.spin,
-                                                         p.ntheta, p.nnorth, p.nalm, atomic_out);
+                                                         p.ntheta, p.nnorth, p.nalm);
     return cudaGetLastError();
 }
 
@@ -574,12 +592,6 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
 
 cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st)
 {
-    const size_t eb = p.prec == LENS_FP32 ? 8 : 16;
-    if (p.leg_chunks <= 1) {
-        // entries l < spin are not produced by the kernel
-        cudaError_t e = cudaMemsetAsync(alm, 0, eb * (size_t)p.nalm * (p.spin ? 2 : 1), st);
-        if (e != cudaSuccess) return e;
-    }
     if (p.prec == LENS_FP32)
         return p.spin ? adj_launch<PolDF, 2, true, 8>(p, ring, alm, st) : adj_launch<PolDF, 4, false, 16>(p, ring, alm, st);
     return p.spin ? adj_launch<PolF64, 1, true, 4>(p, ring, alm, st) : adj_launch<PolF64, 2, false, 8>(p, ring, alm, st);
