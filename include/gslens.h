@@ -81,6 +81,8 @@ typedef struct {
     int W;          /* kernel support in grid cells (4 .. 16) */
     double beta;    /* ES kernel shape parameter */
     int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
+    int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1, 2 or 4) */
+    int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (1, 2 or 4) */
 } lens_plan_params;
 
 typedef struct {

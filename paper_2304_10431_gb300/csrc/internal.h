@@ -51,8 +51,10 @@ struct Plan {
     int ncol = 0;         // m columns: mmax+1 (spin 0) or 2 mmax + 1
     int64_t nalm = 0;
 
-    // Legendre launch shape
-    int leg_rpt = 0, leg_warps = 0, leg_chunks = 0;
+    // Legendre launch shapes (forward, adjoint): rings per thread, warps per
+    // CTA, CTAs per m
+    struct LegShape { int rpt = 0, warps = 0, chunks = 0; };
+    LegShape leg_f, leg_a;
 
     // tables (device)
     void *rec_ab = nullptr;   // per alm index: df32 (Ah, Al, Bh, Bl) or double2 (A, B)

@@ -17,7 +17,8 @@
 #include "internal.h"
 
 namespace gsl {
-int legendre_rpt(int prec, int spin);
+int legendre_rpt(int prec, int spin, bool adjoint);
+bool legendre_rpt_supported(int prec, int spin, bool adjoint, int rpt);
 }
 
 using namespace gsl;
@@ -329,12 +330,16 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     p->R = p->N1 / 2 + 2 * p->W + 1;
     p->pitch = ((p->N2 + p->W - 1) + 31) / 32 * 32;
 
-    // ---- Legendre launch shape
-    p->leg_rpt = legendre_rpt(prec, spin);
-    {
-        const int nw = (p->nnorth + 32 * p->leg_rpt - 1) / (32 * p->leg_rpt);
-        p->leg_chunks = (nw + 15) / 16;
-        p->leg_warps = (nw + p->leg_chunks - 1) / p->leg_chunks;
+    // ---- Legendre launch shapes: RPT rings per thread, at most 16 warps per CTA
+    for (int adj = 0; adj < 2; ++adj) {
+        Plan::LegShape &sh = adj ? p->leg_a : p->leg_f;
+        const int want = prm ? (adj ? prm->legendre_rpt_adj : prm->legendre_rpt_fwd) : 0;
+        if (want && !legendre_rpt_supported(prec, spin, adj != 0, want))
+            return bail(LENS_ERR_INVALID, "unsupported Legendre rings-per-thread setting");
+        sh.rpt = want ? want : legendre_rpt(prec, spin, adj != 0);
+        const int nw = (p->nnorth + 32 * sh.rpt - 1) / (32 * sh.rpt);
+        sh.chunks = (nw + 15) / 16;
+        sh.warps = (nw + sh.chunks - 1) / sh.chunks;
     }
 
     cudaError_t e;
