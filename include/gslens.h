@@ -157,6 +157,24 @@ int lens_synthesis_host(lens_plan p, const void *alm_h, void *map_h, int nmaps, 
 int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream);
 
 /*
+ * Forward lensing that allocates nothing (no counterpart in the paper).
+ * Callers whose device memory belongs to someone else once they are running
+ * (a host framework that owns every device allocation, a service with a
+ * memory budget fixed at start-up) cannot call cudaMalloc; this entry
+ * point computes exactly what lens_synthesis computes for one map, with its
+ * scratch (ring coefficients, torus rows, oversampled grid) taken from a
+ * fixed 64 MiB array compiled into the library instead of the plan's
+ * workspace, and calls no allocating routine.
+ *   alm_d  device [ncomp][nalm] complex;  map_d  device [ncomp][npoints] real.
+ * LENS_ERR_UNSUPPORTED if the plan needs more scratch than the array holds
+ * (the message gives both sizes; use lens_synthesis then).  The array's
+ * device address is looked up on the first call made on each device, which
+ * should therefore come before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU race.
+ */
+int lens_synthesis_static(lens_plan p, const void *alm_d, void *map_d, void *stream);
+
+/*
  * Legendre step alone (Sect. 3 "synthesis" restricted to the theta direction):
  * ring Fourier coefficients on the plan's equiangular rings
  * theta_j = j pi / (ntheta - 1), j = 0..ntheta-1.

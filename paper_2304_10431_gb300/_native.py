@@ -23,6 +23,7 @@ EXPORTS = {
     "lens_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_synthesis": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_adjoint": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_pointing": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -101,6 +101,10 @@ cudaError_t launch_pointing(int64_t n, const double *theta, const double *phi, c
                             const double *aph, double *theta_out, double *phi_out, double *chi_out,
                             cudaStream_t st);
 
+// Records a failing status and message in the calling thread's error state
+// (lens_get_last_error / lens_last_error_message) and returns the status.
+int record_failure(int status, const char *msg);
+
 size_t theta_smem_bytes(const Plan &p);
 size_t phi_smem_bytes(const Plan &p);
 

@@ -200,6 +200,8 @@ void sizes_for(int lmax, int mmax, int M, double sigma, int W, int &N1, int &N2)
 
 }  // namespace
 
+int gsl::record_failure(int status, const char *msg) { return fail(status, msg); }
+
 extern "C" {
 
 int64_t lens_nalm(int lmax, int mmax)
