@@ -46,7 +46,9 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
 # source makes the entry stale and the bench reports traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("legendre_adjoint/spin2/fp32", "19d455e0b7ae"): 742806272,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
+}
 
 
 def parse():
@@ -243,7 +245,7 @@ def run_gpu(args):
 
     stream = torch.cuda.current_stream()
 
-    def timed(pT, pP, b, steps, warmup, profile):
+    def timed(pT, pP, b, steps, warmup, profile, nvtx_name):
         for _ in range(warmup):
             step(pT, pP, b)
         barrier()
@@ -251,11 +253,13 @@ def run_gpu(args):
         if profile:
             lib.lens_profile_enable(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(nvtx_name)
         e0.record(stream)
         for _ in range(steps):
             step(pT, pP, b)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         lib.lens_profile_enable(0)
         ms = e0.elapsed_time(e1) / steps
         if world > 1:
@@ -286,7 +290,7 @@ def run_gpu(args):
     info_T, info_P = pT.info(), pP.info()
     clk = ClockSampler(local)
     clk.start()
-    ms = timed(pT, pP, b, args.steps, max(args.warmup, 3), profile=True)
+    ms = timed(pT, pP, b, args.steps, max(args.warmup, 3), profile=True, nvtx_name="timed_fp32")
     clocks = clk.stop()
     prof_ms = np.zeros(32)
     cnt = np.zeros(32, dtype=np.int64)
@@ -367,7 +371,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         qT, qP, c = make("fp64", 1e-10)
         k64 = max(1, min(args.steps, 3))
-        ms64 = timed(qT, qP, c, k64, 1, profile=True)
+        ms64 = timed(qT, qP, c, k64, 1, profile=True, nvtx_name="timed_fp64")
         p64 = np.zeros(32)
         c64 = np.zeros(32, dtype=np.int64)
         lib.lens_profile_read(p64.ctypes.data, c64.ctypes.data, 32)
