@@ -70,6 +70,7 @@ struct Plan {
     void *frac = nullptr;      // float2 / double2 (u - i0, v - j0)
     int32_t *perm = nullptr;   // sorted -> user index
     void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
+    double *wts = nullptr;     // FP64 plans: [npts][2W] kernel weights (theta taps, then phi taps)
 
     // per-call workspace
     void *ring = nullptr;      // [ncol][ntheta] complex

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include <cub/cub.cuh>
 
 #include "common.cuh"
@@ -97,23 +99,52 @@ template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta
     return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
 }
 
-template <typename T, int W, bool SPIN>
+// FP64 plans: the 2W weights of every (sorted) point, computed once.
+__global__ void k_weights(const double2 *__restrict__ frac, int64_t n, int W, double beta, double *__restrict__ wts)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double2 f = frac[p];
+    const double twoW = 2.0 / W;
+    double *w = wts + p * 2 * W;
+    for (int a = 0; a < W; ++a) {
+        w[a] = es_kernel<double>(f.x - a, twoW, beta);
+        w[W + a] = es_kernel<double>(f.y - a, twoW, beta);
+    }
+}
+
+template <typename T, int W, bool PRE>
+__device__ __forceinline__ void tap_weights(T (&wa)[W], T (&wb)[W], const cplx<T> &f, const double *wts, int64_t p,
+                                            T beta)
+{
+    if (PRE) {
+        const double *w = wts + p * 2 * W;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            wa[a] = (T)__ldg(w + a);
+            wb[a] = (T)__ldg(w + W + a);
+        }
+    } else {
+        const T twoW = T(2) / T(W);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            wa[a] = es_kernel<T>(f.x - T(a), twoW, beta);
+            wb[a] = es_kernel<T>(f.y - T(a), twoW, beta);
+        }
+    }
+}
+
+template <typename T, int W, bool SPIN, bool PRE>
 __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                 const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
-                                                const cplx<T> *__restrict__ phase, T *__restrict__ map, int64_t n,
-                                                int pitch, T beta)
+                                                const cplx<T> *__restrict__ phase, const double *__restrict__ wts,
+                                                T *__restrict__ map, int64_t n, int pitch, T beta)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t c0 = cell[p];
-    const cplx<T> f = frac[p];
-    const T twoW = T(2) / T(W);
     T wa[W], wb[W];
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-        wa[a] = es_kernel<T>(f.x - T(a), twoW, beta);
-        wb[a] = es_kernel<T>(f.y - T(a), twoW, beta);
-    }
+    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
     const int32_t dst = perm[p];
     if (!SPIN) {
         const T *g = (const T *)grid + c0;
@@ -147,23 +178,17 @@ __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, c
     }
 }
 
-template <typename T, int W, bool SPIN>
+template <typename T, int W, bool SPIN, bool PRE>
 __global__ void __launch_bounds__(256) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                 const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
-                                                const cplx<T> *__restrict__ phase, const T *__restrict__ map,
-                                                int64_t n, int pitch, T beta)
+                                                const cplx<T> *__restrict__ phase, const double *__restrict__ wts,
+                                                const T *__restrict__ map, int64_t n, int pitch, T beta)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t c0 = cell[p];
-    const cplx<T> f = frac[p];
-    const T twoW = T(2) / T(W);
     T wa[W], wb[W];
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-        wa[a] = es_kernel<T>(f.x - T(a), twoW, beta);
-        wb[a] = es_kernel<T>(f.y - T(a), twoW, beta);
-    }
+    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
     const int32_t src = perm[p];
     if (!SPIN) {
         const T x = map[src];
@@ -199,9 +224,17 @@ cudaError_t interp_w(const Plan &p, const void *grid, void *map, cudaStream_t st
     const int thr = 256;
     const int64_t blocks = (p.npts + thr - 1) / thr;
     if (blocks == 0) return cudaSuccess;
-    k_interp<T, W, SPIN><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
-                                                           (const cplx<T> *)p.phase, (T *)map, p.npts, p.pitch,
-                                                           (T)p.beta);
+    if constexpr (std::is_same<T, double>::value) {
+        if (p.wts) {
+            k_interp<T, W, SPIN, true><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                                         (const cplx<T> *)p.phase, p.wts, (T *)map,
+                                                                         p.npts, p.pitch, (T)p.beta);
+            return cudaGetLastError();
+        }
+    }
+    k_interp<T, W, SPIN, false><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                                      (const cplx<T> *)p.phase, p.wts, (T *)map,
+                                                                      p.npts, p.pitch, (T)p.beta);
     return cudaGetLastError();
 }
 
@@ -211,9 +244,17 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
     const int thr = 256;
     const int64_t blocks = (p.npts + thr - 1) / thr;
     if (blocks == 0) return cudaSuccess;
-    k_spread<T, W, SPIN><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
-                                                           (const cplx<T> *)p.phase, (const T *)map, p.npts, p.pitch,
-                                                           (T)p.beta);
+    if constexpr (std::is_same<T, double>::value) {
+        if (p.wts) {
+            k_spread<T, W, SPIN, true><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                                         (const cplx<T> *)p.phase, p.wts,
+                                                                         (const T *)map, p.npts, p.pitch, (T)p.beta);
+            return cudaGetLastError();
+        }
+    }
+    k_spread<T, W, SPIN, false><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
+                                                                      (const cplx<T> *)p.phase, p.wts,
+                                                                      (const T *)map, p.npts, p.pitch, (T)p.beta);
     return cudaGetLastError();
 }
 
@@ -320,6 +361,10 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
     k_gather_points<<<blocks, thr, 0, st>>>(p.perm, n, cell_u, frac_u, phase_u, p.prec, p.spin, p.cell, p.frac,
                                             p.phase);
     GSL_TRY(cudaGetLastError());
+    if (p.wts) {
+        k_weights<<<blocks, thr, 0, st>>>((const double2 *)p.frac, n, p.W, p.beta, p.wts);
+        GSL_TRY(cudaGetLastError());
+    }
     unsigned hflags = 0;
     GSL_TRY(cudaMemcpyAsync(&hflags, p.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     GSL_TRY(cudaStreamSynchronize(st));

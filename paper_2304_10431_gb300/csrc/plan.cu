@@ -359,6 +359,11 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if ((e = B.alloc(&p->frac, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc frac");
         if ((e = B.alloc((void **)&p->perm, sizeof(int32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc perm");
         if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
+        // FP64 plans keep the 2W kernel weights of every point (GB300's FP64 pipe makes
+        // evaluating exp/sqrt per tap far dearer than reading 16 W bytes per point)
+        if (prec == LENS_FP64 &&
+            (e = B.alloc((void **)&p->wts, sizeof(double) * 2 * (size_t)p->W * npoints, false)) != cudaSuccess)
+            return bailc(e, "alloc weights");
     }
 
     // ---- host tables: start-value norms, rings, deconvolution factors
