@@ -81,8 +81,10 @@ typedef struct {
     int W;          /* kernel support in grid cells (4 .. 16) */
     double beta;    /* ES kernel shape parameter */
     int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
-    int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1, 2 or 4) */
-    int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (1, 2 or 4) */
+    int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1 or 2) */
+    int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (1 or 2) */
+    int legendre_df32_mmin; /* FP64 plans: orders m >= this value use the double-float Legendre
+                               recursion (0 = choose, -1 = never) */
 } lens_plan_params;
 
 typedef struct {

@@ -52,13 +52,18 @@ struct Plan {
     int64_t nalm = 0;
 
     // Legendre launch shapes (forward, adjoint): rings per thread, warps per
-    // CTA, CTAs per m
+    // CTA, CTAs per m.  FP64 plans may run orders m >= m_df with a df32
+    // recursion and df32 accumulation (shapes leg_fd, leg_ad); FP32 plans run
+    // every order in df32 (m_df = 0).
     struct LegShape { int rpt = 0, warps = 0, chunks = 0; };
-    LegShape leg_f, leg_a;
+    LegShape leg_f, leg_a, leg_fd, leg_ad;
+    int m_df = 0;
 
     // tables (device)
     void *rec_ab = nullptr;   // per alm index: df32 (Ah, Al, Bh, Bl) or double2 (A, B)
     void *rec_c = nullptr;    // spin s: per alm index: float2 (Ch, Cl) or double
+    void *rec_ab_df = nullptr, *rec_c_df = nullptr;  // FP64 plans with m_df <= mmax: df32 copies
+    void *coef_dd = nullptr;  // workspace: df32 coefficients of the forward (FP64 plans, m >= m_df)
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;
     void *w1 = nullptr;       // [2 lmax + 1]  1/psihat(2 pi k / N1), k = -lmax..lmax
@@ -85,6 +90,8 @@ struct Plan {
     void *allocs[64];
     int nallocs = 0;
 };
+
+Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);

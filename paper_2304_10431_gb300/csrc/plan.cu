@@ -18,6 +18,7 @@
 
 namespace gsl {
 int legendre_rpt(int prec, int spin, bool adjoint);
+int legendre_rpt_dd(int spin, bool adjoint);
 bool legendre_rpt_supported(int prec, int spin, bool adjoint, int rpt);
 }
 
@@ -332,16 +333,33 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     p->R = p->N1 / 2 + 2 * p->W + 1;
     p->pitch = ((p->N2 + p->W - 1) + 31) / 32 * 32;
 
-    // ---- Legendre launch shapes: RPT rings per thread, at most 16 warps per CTA
+    // ---- Legendre arithmetic: FP32 plans df32 for every m; FP64 plans native FP64
+    // for m < m_df and df32 recursion + df32 accumulation for m >= m_df.  df32
+    // loses ~2^-45 per operation and the recursion amplifies rounding most at
+    // low m near the poles.  Measured eps_eff of the whole forward at lmax 4096,
+    // HEALPix Nside 2048, eps 1e-10 (spin 0 / spin 2) against the oracle:
+    //   df32 from m = 1: 2.3e-10 / 1.7e-10;  m = 64: 6.1e-11 / 5.1e-11;
+    //   m = 128: 2.5e-11 / 2.3e-11;  m = 256: 8.3e-12 / 8.8e-12 (= all-FP64).
+    // Hence m_df = 64 for epsilon >= 1e-9, 256 for epsilon >= 5e-11, none below.
+    if (prec == LENS_FP32) {
+        p->m_df = 0;
+    } else {
+        const int want = prm ? prm->legendre_df32_mmin : 0;
+        if (want < 0) p->m_df = mmax + 1;
+        else if (want > 0) p->m_df = std::min(want, mmax + 1);
+        else if (epsilon >= 1e-9) p->m_df = std::min(64, mmax + 1);
+        else if (epsilon >= 5e-11) p->m_df = std::min(256, mmax + 1);
+        else p->m_df = mmax + 1;
+    }
+    // ---- Legendre launch shapes: RPT rings per thread; warps per CTA chosen
+    // for occupancy of the kernel variant (legendre_shape)
     for (int adj = 0; adj < 2; ++adj) {
-        Plan::LegShape &sh = adj ? p->leg_a : p->leg_f;
         const int want = prm ? (adj ? prm->legendre_rpt_adj : prm->legendre_rpt_fwd) : 0;
         if (want && !legendre_rpt_supported(prec, spin, adj != 0, want))
             return bail(LENS_ERR_INVALID, "unsupported Legendre rings-per-thread setting");
-        sh.rpt = want ? want : legendre_rpt(prec, spin, adj != 0);
-        const int nw = (p->nnorth + 32 * sh.rpt - 1) / (32 * sh.rpt);
-        sh.chunks = (nw + 15) / 16;
-        sh.warps = (nw + sh.chunks - 1) / sh.chunks;
+        (adj ? p->leg_a : p->leg_f) = legendre_shape(*p, adj != 0, false, want ? want : legendre_rpt(prec, spin, adj != 0));
+        if (prec == LENS_FP64)
+            (adj ? p->leg_ad : p->leg_fd) = legendre_shape(*p, adj != 0, true, legendre_rpt_dd(spin, adj != 0));
     }
 
     cudaError_t e;
@@ -350,6 +368,13 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if ((e = B.alloc(&p->rec_ab, (size_t)p->nalm * (prec == LENS_FP32 ? 16 : 16), false)) != cudaSuccess)
         return bailc(e, "alloc rec_ab");
     if (spin && (e = B.alloc(&p->rec_c, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_c");
+    if (prec == LENS_FP64 && p->m_df <= mmax) {
+        if ((e = B.alloc(&p->rec_ab_df, (size_t)p->nalm * 16, false)) != cudaSuccess) return bailc(e, "alloc rec_ab_df");
+        if (spin && (e = B.alloc(&p->rec_c_df, (size_t)p->nalm * 8, false)) != cudaSuccess)
+            return bailc(e, "alloc rec_c_df");
+        if ((e = B.alloc(&p->coef_dd, (size_t)p->nalm * 16 * (spin ? 2 : 1), true)) != cudaSuccess)
+            return bailc(e, "alloc coef_dd");
+    }
     if ((e = B.alloc(&p->ring, esz * (size_t)p->ncol * p->ntheta, true)) != cudaSuccess) return bailc(e, "alloc ring");
     if ((e = B.alloc(&p->X, esz * (size_t)p->R * p->ncol, true)) != cudaSuccess) return bailc(e, "alloc X");
     if ((e = B.alloc(&p->grid, (esz / 2) * ncomp * (size_t)p->R * p->pitch, true)) != cudaSuccess)

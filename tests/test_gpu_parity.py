@@ -150,6 +150,27 @@ def test_spin2_lensed_healpix_with_phase():
         assert rel(m, ref) <= eps
 
 
+@pytest.mark.parametrize("spin", [0, 1, 2])
+@pytest.mark.parametrize("mmin", [1, 57])
+def test_fp64_plan_df32_orders(spin, mmin):
+    """FP64 plans run orders m >= legendre_df32_mmin in double-float: same accuracy bar."""
+    L, n = 160, 4000
+    th, ph, chi = W.random_points(n, 31 + spin)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-10, precision="fp64", legendre_df32_mmin=mmin,
+                    device=DEV)
+    a = make_alm(L, spin, 17)
+    ring = plan.ring_synthesis(gpu_alm(plan, a)).cpu().numpy()
+    nt = plan.info()["ntheta"]
+    rref = O.ring_coeffs(L, L, spin, np.arange(nt) * math.pi / (nt - 1), a).T
+    assert rel(ring, rref) < 1e-11  # double-float recursion: ~2^-45 per step, amplified at low m
+    m = plan.synthesis(gpu_alm(plan, a)).cpu().numpy()
+    ref = O.synthesis(L, L, spin, th, ph, a, chi)
+    assert rel(m, ref) <= 1e-10
+    y = np.random.default_rng(spin).standard_normal(ref.shape)
+    at = plan.adjoint(gpu_map(plan, y)).cpu().numpy()
+    assert rel(at, O.adjoint(L, L, spin, th, ph, y, chi)) <= 1e-10
+
+
 # ---------------------------------------------------------------- edge cases
 def test_mmax_below_lmax():
     L, mmax, n = 40, 17, 1500
