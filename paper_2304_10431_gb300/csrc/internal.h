@@ -60,10 +60,14 @@ struct Plan {
     int m_df = 0;
 
     // tables (device)
-    void *rec_ab = nullptr;   // per alm index: df32 (Ah, Al, Bh, Bl) or double2 (A, B)
-    void *rec_c = nullptr;    // spin s: per alm index: float2 (Ch, Cl) or double
-    void *rec_ab_df = nullptr, *rec_c_df = nullptr;  // FP64 plans with m_df <= mmax: df32 copies
-    void *coef_dd = nullptr;  // workspace: df32 coefficients of the forward (FP64 plans, m >= m_df)
+    // monic-form recursion coefficients per alm index: alpha and (spin s) tau,
+    // as df32 float2 (FP32 plans) or double (FP64 plans); FP64 plans with
+    // m_df <= mmax also hold df32 copies.  scale: c_l (double, per alm index).
+    void *rec_a = nullptr, *rec_t = nullptr;
+    void *rec_a_df = nullptr, *rec_t_df = nullptr;
+    double *scale = nullptr;
+    void *coef = nullptr;     // workspace: forward coefficients c_l a_lm of one call
+                              // ([ncomp][nalm], float2 / double2 / df32 float4)
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;
     void *w1 = nullptr;       // [2 lmax + 1]  1/psihat(2 pi k / N1), k = -lmax..lmax

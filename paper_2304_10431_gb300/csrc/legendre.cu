@@ -13,7 +13,15 @@
 // s lambda_lm follows Wigner's d^l_{m,-s}: closed form at l0 = max(m, s),
 // then the three-term recursion
 //   lambda_l = A_l (x + sigma T_l) lambda_{l-1} - B_l lambda_{l-2},
-//   T_l = m s / ((l-1) l), sigma = +1 for +s, -1 for -s, x = cos theta.
+//   T_l = m s / ((l-1) l), sigma = +1 for +s, -1 for -s, x = cos theta,
+// run in monic form: with c_{l0} = c_{l0+1} = 1 and c_l = B_l c_{l-2}, the
+// scaled values mu_l = lambda_l / c_l obey
+//   mu_l = (alpha_l x + sigma tau_l) mu_{l-1} - mu_{l-2},
+//   alpha_l = A_l c_{l-1} / c_l,  tau_l = alpha_l T_l,
+// one product per step fewer than the plain form.  The forward folds c_l
+// into the coefficients (k_coef_prep, once per call); the adjoint multiplies
+// each degree's warp sum by c_l before adding it into a_lm.  c_l stays close
+// to 1 (within [2^-2.6, 2^0.2] for lmax 4096).
 // Values are carried as mantissa * 2^(60 E) so that sin^m theta cannot
 // underflow; contributions with E <= -2 are below 2^-60 and dropped.
 //
@@ -24,6 +32,10 @@
 // Mapping: one CTA per (m, ring chunk); each thread owns RPT adjacent north
 // rings (theta <= pi/2) and obtains the mirrored south ring from
 //   s lambda_lm(pi - theta) = (-1)^{l+m} (-s)lambda_lm(theta).
+// The sign (-1)^{l+m} is s0 (-1)^{l-lf} with lf = l0 + 1 the first degree of
+// the block loop, so inside a block it is a compile-time sign times the
+// per-m constant s0, applied once at the end (forward) or to the inputs
+// (adjoint).
 // The degree loop runs in fully unrolled blocks of 8 steps; the two words of
 // each recursion state swap roles every step (no register moves).  Before
 // every block a warp vote picks one of three regimes: every state at scale 0
@@ -51,7 +63,6 @@ constexpr int kBlk = 8;
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
 __device__ __forceinline__ df32 df_add_u(df32 a, df32 b) { return df_sub_u(a, {-b.h, -b.l}); }
-__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ df32 df_split(double v)
 {
     const float h = (float)v;
@@ -69,45 +80,34 @@ __device__ __forceinline__ df32 df_norm(df32 a)  // two-sum: exact for any order
 // the newest alternates.  E is the power-of-2^60 scale shared by both words.
 //
 // Accumulation interface: V is the value handed from the recursion to the
-// sums, K a real coefficient component (a_lm or ring input), A a real
-// accumulator; fma(acc, k, v) is acc += k v.
+// sums, K a real coefficient component (prepared a_lm or ring input), A a
+// real accumulator; fma(acc, k, v) is acc += k v, fms(acc, k, v) acc -= k v.
 struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
     using R = float;
     using C = float2;
     using X = df32;
-    using Tab = float4;   // (A_hi, A_lo, B_hi, B_lo)
-    using TTab = float2;  // (T_hi, T_lo)
+    using Tab = float2;   // alpha (hi, lo)
+    using TTab = float2;  // tau (hi, lo)
     using V = float;
     using K = float;
     using A = float;
-    static constexpr bool kPreCombined = false;
     struct St { df32 w[2]; int E; };
-    struct Co { df32 A, B; };
-    static __device__ __forceinline__ Co load(const Tab *tab, int l)
-    {
-        const float4 c = __ldg(tab + l);
-        return {{c.x, c.y}, {c.z, c.w}};
-    }
-    static __device__ __forceinline__ X load_t(const TTab *tab, int l)
+    static __device__ __forceinline__ X load(const Tab *tab, int l)
     {
         const float2 c = __ldg(tab + l);
         return {c.x, c.y};
     }
+    static __device__ __forceinline__ X load_t(const TTab *tab, int l) { return load(tab, l); }
     static __device__ __forceinline__ X ring_x(const RingTab &rt, int j)
     {
         const float2 v = __ldg(rt.xdf + j);
         return {v.x, v.y};
     }
+    static __device__ __forceinline__ X mul(X a, X b) { return df_mul(a, b); }
     static __device__ __forceinline__ X add(X a, X b) { return df_add_u(a, b); }
     static __device__ __forceinline__ X sub(X a, X b) { return df_sub_u(a, b); }
-    // new = A (y q) - B p, written over p
-    static __device__ __forceinline__ void comb(df32 &p, const df32 &q, X y, const Co &c)
-    {
-        const df32 t = df_mul(y, q);
-        const df32 v = df_mul(c.A, t);
-        const df32 w = df_mul(c.B, p);
-        p = df_sub_u(v, w);
-    }
+    // new = y q - p, written over p
+    static __device__ __forceinline__ void step(df32 &p, const df32 &q, X y) { p = df_sub_u(df_mul(y, q), p); }
     // The words are not renormalised after every step (the low word carries
     // the compensation of the high-word recursion), so a value is h + l.
     static __device__ __forceinline__ V val(const df32 &a) { return __fadd_rn(a.h, a.l); }
@@ -141,8 +141,16 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
     // accumulation
     static __device__ __forceinline__ V vscale(V v, float f) { return v * f; }
     static __device__ __forceinline__ V vsign(V v, float sg) { return v * sg; }
-    static __device__ __forceinline__ void fma(A &acc, K k, V v) { acc += k * v; }
-    static __device__ __forceinline__ void fma2(A &acc, K k1, V v1, K k2, V v2) { acc += k1 * v1 + k2 * v2; }
+    static __device__ __forceinline__ void fma(A &acc, K k, V v) { acc = __fmaf_rn(k, v, acc); }
+    static __device__ __forceinline__ void fms(A &acc, K k, V v) { acc = __fmaf_rn(-k, v, acc); }
+    static __device__ __forceinline__ void fma2(A &acc, K k1, V v1, K k2, V v2)
+    {
+        acc = __fmaf_rn(k2, v2, __fmaf_rn(k1, v1, acc));
+    }
+    static __device__ __forceinline__ void fma2m(A &acc, K k1, V v1, K k2, V v2)
+    {
+        acc = __fmaf_rn(-k2, v2, __fmaf_rn(k1, v1, acc));
+    }
     static __device__ __forceinline__ A azero() { return 0.f; }
     static __device__ __forceinline__ K kadd(K a, K b) { return a + b; }
     static __device__ __forceinline__ K ksub(K a, K b) { return a - b; }
@@ -150,10 +158,12 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
     static __device__ __forceinline__ void arenorm(A &) {}
     static __device__ __forceinline__ R aout(A a) { return a; }
     static __device__ __forceinline__ A aadd(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A asub(A a, A b) { return a - b; }
     static __device__ __forceinline__ A ascale(A a, float f) { return a * f; }
     static __device__ __forceinline__ A shfl_xor(A v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
-    static __device__ __forceinline__ void atomic_add(R *dst, A v) { atomicAdd(dst, v); }
-    // a_lm coefficient (re, im) of entry idx, component comp (0: G or T, 1: C)
+    // *dst += c v (c the monic-form scale of the degree)
+    static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, v * (float)c); }
+    // prepared coefficient (re, im) of entry idx, component comp
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
         const float2 v = __ldg((const float2 *)tab + comp * nalm + idx);
@@ -173,27 +183,19 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     using R = double;
     using C = double2;
     using X = double;
-    using Tab = double2;  // (A, B)
-    using TTab = double;  // T
+    using Tab = double;   // alpha
+    using TTab = double;  // tau
     using V = double;
     using K = double;
     using A = double;
-    static constexpr bool kPreCombined = false;
     struct St { double w[2]; int E; };
-    struct Co { double A, B; };
-    static __device__ __forceinline__ Co load(const Tab *tab, int l)
-    {
-        const double2 c = __ldg(tab + l);
-        return {c.x, c.y};
-    }
+    static __device__ __forceinline__ X load(const Tab *tab, int l) { return __ldg(tab + l); }
     static __device__ __forceinline__ X load_t(const TTab *tab, int l) { return __ldg(tab + l); }
     static __device__ __forceinline__ X ring_x(const RingTab &rt, int j) { return __ldg(rt.x + j); }
+    static __device__ __forceinline__ X mul(X a, X b) { return a * b; }
     static __device__ __forceinline__ X add(X a, X b) { return a + b; }
     static __device__ __forceinline__ X sub(X a, X b) { return a - b; }
-    static __device__ __forceinline__ void comb(double &p, const double &q, X y, const Co &c)
-    {
-        p = c.A * (y * q) - c.B * p;
-    }
+    static __device__ __forceinline__ void step(double &p, const double &q, X y) { p = __fma_rn(y, q, -p); }
     static __device__ __forceinline__ V val(const double &a) { return a; }
     static __device__ __forceinline__ void renorm(St &) {}
     static __device__ __forceinline__ void rescale(St &s, int newest)
@@ -218,8 +220,16 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static __device__ __forceinline__ void zero(St &s) { s.w[0] = 0.0; s.w[1] = 0.0; s.E = 0; }
     static __device__ __forceinline__ V vscale(V v, double f) { return v * f; }
     static __device__ __forceinline__ V vsign(V v, double sg) { return v * sg; }
-    static __device__ __forceinline__ void fma(A &acc, K k, V v) { acc += k * v; }
-    static __device__ __forceinline__ void fma2(A &acc, K k1, V v1, K k2, V v2) { acc += k1 * v1 + k2 * v2; }
+    static __device__ __forceinline__ void fma(A &acc, K k, V v) { acc = __fma_rn(k, v, acc); }
+    static __device__ __forceinline__ void fms(A &acc, K k, V v) { acc = __fma_rn(-k, v, acc); }
+    static __device__ __forceinline__ void fma2(A &acc, K k1, V v1, K k2, V v2)
+    {
+        acc = __fma_rn(k2, v2, __fma_rn(k1, v1, acc));
+    }
+    static __device__ __forceinline__ void fma2m(A &acc, K k1, V v1, K k2, V v2)
+    {
+        acc = __fma_rn(-k2, v2, __fma_rn(k1, v1, acc));
+    }
     static __device__ __forceinline__ A azero() { return 0.0; }
     static __device__ __forceinline__ K kadd(K a, K b) { return a + b; }
     static __device__ __forceinline__ K ksub(K a, K b) { return a - b; }
@@ -227,9 +237,10 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static __device__ __forceinline__ void arenorm(A &) {}
     static __device__ __forceinline__ R aout(A a) { return a; }
     static __device__ __forceinline__ A aadd(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A asub(A a, A b) { return a - b; }
     static __device__ __forceinline__ A ascale(A a, double f) { return a * f; }
     static __device__ __forceinline__ A shfl_xor(A v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
-    static __device__ __forceinline__ void atomic_add(R *dst, A v) { atomicAdd(dst, v); }
+    static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, v * c); }
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
         const double2 v = __ldg((const double2 *)tab + comp * nalm + idx);
@@ -245,16 +256,14 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static __device__ __forceinline__ C cout(A re, A im) { return make_double2(re, im); }
 };
 
-// FP64 plans, orders m >= m_df: the df32 recursion of PolDF with df32 sums.
-// Coefficients come from a df32 table prepared per call (k_coef_dd); for
-// spin s it already holds a = G + iC and b = (-1)^s (conj G + i conj C).
+// FP64 plans, orders m >= m_df: the df32 recursion of PolDF with df32 sums and
+// df32 prepared coefficients.
 struct PolDD : PolDF {
     using R = double;
     using C = double2;
     using V = df32;
     using K = df32;
     using A = df32;
-    static constexpr bool kPreCombined = true;
     static __device__ __forceinline__ V val(const df32 &a) { return a; }
     // start mantissa to df32 accuracy (exp2 in FP64, split in two words)
     static __device__ __forceinline__ void start(St &s, double L2, int sign, bool zero)
@@ -270,9 +279,14 @@ struct PolDD : PolDF {
     static __device__ __forceinline__ V vscale(V v, float f) { return df_scale_pow2(v, f); }
     static __device__ __forceinline__ V vsign(V v, float sg) { return df_scale_pow2(v, sg); }
     static __device__ __forceinline__ void fma(A &acc, K k, V v) { acc = df_add_u(acc, df_mul(k, v)); }
+    static __device__ __forceinline__ void fms(A &acc, K k, V v) { acc = df_sub_u(acc, df_mul(k, v)); }
     static __device__ __forceinline__ void fma2(A &acc, K k1, V v1, K k2, V v2)
     {
         acc = df_add_u(acc, df_add_u(df_mul(k1, v1), df_mul(k2, v2)));
+    }
+    static __device__ __forceinline__ void fma2m(A &acc, K k1, V v1, K k2, V v2)
+    {
+        acc = df_add_u(acc, df_sub_u(df_mul(k1, v1), df_mul(k2, v2)));
     }
     static __device__ __forceinline__ A azero() { return {0.f, 0.f}; }
     static __device__ __forceinline__ K kadd(K a, K b) { return df_add_u(a, b); }
@@ -281,13 +295,14 @@ struct PolDD : PolDF {
     static __device__ __forceinline__ void arenorm(A &a) { a = df_norm(a); }
     static __device__ __forceinline__ R aout(A a) { return (double)a.h + (double)a.l; }
     static __device__ __forceinline__ A aadd(A a, A b) { return df_add_u(a, b); }
+    static __device__ __forceinline__ A asub(A a, A b) { return df_sub_u(a, b); }
     static __device__ __forceinline__ A ascale(A a, float f) { return df_scale_pow2(a, f); }
     static __device__ __forceinline__ A shfl_xor(A v, int off)
     {
         return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
     }
-    static __device__ __forceinline__ void atomic_add(R *dst, A v) { atomicAdd(dst, aout(v)); }
-    // table entry: float4 (re_h, re_l, im_h, im_l); comp selects a (0) or b (1) for spin s
+    static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, aout(v) * c); }
+    // table entry: float4 (re_h, re_l, im_h, im_l)
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
         const float4 v = __ldg((const float4 *)tab + comp * nalm + idx);
@@ -370,27 +385,28 @@ template <class P, int RPT, bool SPIN> struct Rings {
     }
     // One step to degree l; the newest value goes into word NW.
     template <int NW, bool CHECK>
-    __device__ __forceinline__ void advance(const typename P::Tab *recm, const typename P::TTab *recc, int l)
+    __device__ __forceinline__ void advance(const typename P::Tab *reca, const typename P::TTab *rect, int l)
     {
-        const typename P::Co co = P::load(recm, l);
+        const typename P::X al = P::load(reca, l);
         if (!SPIN) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                P::comb(sp[k].w[NW], sp[k].w[1 - NW], x[k], co);
+                P::step(sp[k].w[NW], sp[k].w[1 - NW], P::mul(al, x[k]));
                 if (CHECK) P::rescale(sp[k], NW);
             }
         } else {
-            const typename P::X t = P::load_t(recc, l);
+            const typename P::X t = P::load_t(rect, l);
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                P::comb(sp[k].w[NW], sp[k].w[1 - NW], P::add(x[k], t), co);
-                P::comb(sm[k].w[NW], sm[k].w[1 - NW], P::sub(x[k], t), co);
+                const typename P::X ax = P::mul(al, x[k]);
+                P::step(sp[k].w[NW], sp[k].w[1 - NW], P::add(ax, t));
+                P::step(sm[k].w[NW], sm[k].w[1 - NW], P::sub(ax, t));
                 if (CHECK) { P::rescale(sp[k], NW); P::rescale(sm[k], NW); }
             }
         }
     }
     // Tail step: word 1 moves to word 0, the newest goes into word 1.
-    __device__ __forceinline__ void advance_moved(const typename P::Tab *recm, const typename P::TTab *recc, int l)
+    __device__ __forceinline__ void advance_moved(const typename P::Tab *reca, const typename P::TTab *rect, int l)
     {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -403,7 +419,7 @@ template <class P, int RPT, bool SPIN> struct Rings {
                 sm[k].w[1] = b;
             }
         }
-        advance<1, true>(recm, recc, l);
+        advance<1, true>(reca, rect, l);
     }
     template <int NW, bool SCALED> __device__ __forceinline__ typename P::V vplus(int k) const
     {
@@ -420,132 +436,131 @@ template <class P, int RPT, bool SPIN> struct Rings {
 };
 
 // ---------------------------------------------------------------- forward
+// Accumulators per ring; "rel" below is (-1)^(l - lf), the sign of a degree
+// relative to the first degree lf = l0 + 1 of the block loop.
+//   spin 0: (r0, i0) sums degrees with rel = +1, (r1, i1) rel = -1;
+//           north = sum0 + sum1, south = s0 (sum0 - sum1).
+//   spin s: (r0, i0) = sum a s-lambda (north, +m), (r1, i1) = sum rel a (-s)lambda
+//           (south, +m), (r2, i2) = sum b (-s)lambda (north, -m), (r3, i3) =
+//           sum rel b s-lambda (south, -m); the south sums are multiplied by s0.
 template <class P, int RPT, bool SPIN> struct FwdAcc {
     using A = typename P::A;
     using K = typename P::K;
-    using Sg = decltype(P::fac(0));
-    // north/south accumulators of column +m (p) and -m (q), (re, im)
-    A pnr[RPT], pni[RPT], psr[RPT], psi[RPT], qnr[RPT], qni[RPT], qsr[RPT], qsi[RPT];
+    A r0[RPT], i0[RPT], r1[RPT], i1[RPT], r2[RPT], i2[RPT], r3[RPT], i3[RPT];
     const void *tab;
     int64_t nalm, base;
-    int m;
-    Sg sgs;
 
-    __device__ __forceinline__ void init(const void *tab_, int64_t nalm_, int64_t base_, int m_, int s)
+    __device__ __forceinline__ void init(const void *tab_, int64_t nalm_, int64_t base_)
     {
         tab = tab_;
         nalm = nalm_;
         base = base_;
-        m = m_;
-        sgs = (s & 1) ? Sg(-1) : Sg(1);
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            pnr[k] = P::azero(); pni[k] = pnr[k]; psr[k] = pnr[k]; psi[k] = pnr[k];
-            qnr[k] = pnr[k]; qni[k] = pnr[k]; qsr[k] = pnr[k]; qsi[k] = pnr[k];
+            r0[k] = P::azero(); i0[k] = r0[k]; r1[k] = r0[k]; i1[k] = r0[k];
+            r2[k] = r0[k]; i2[k] = r0[k]; r3[k] = r0[k]; i3[k] = r0[k];
         }
     }
     __device__ __forceinline__ void renorm()
     {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            P::arenorm(pnr[k]); P::arenorm(pni[k]); P::arenorm(psr[k]); P::arenorm(psi[k]);
-            if (SPIN) { P::arenorm(qnr[k]); P::arenorm(qni[k]); P::arenorm(qsr[k]); P::arenorm(qsi[k]); }
+            P::arenorm(r0[k]); P::arenorm(i0[k]); P::arenorm(r1[k]); P::arenorm(i1[k]);
+            if (SPIN) { P::arenorm(r2[k]); P::arenorm(i2[k]); P::arenorm(r3[k]); P::arenorm(i3[k]); }
         }
     }
-    // contribution of degree l (value in word NW); sg = (-1)^{l+m}
-    template <int NW, bool SCALED> __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, int l, Sg sg)
+    // contribution of degree l (value in word NW), ODD: rel = -1
+    template <int NW, bool SCALED, bool ODD> __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, int l)
     {
-        K gr, gi;
-        P::coef(tab, nalm, 0, base + l, gr, gi);
+        K ar, ai;
+        P::coef(tab, nalm, 0, base + l, ar, ai);
         if (!SPIN) {
-            if (m == 0) gi = K{};
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const typename P::V v = st.template vplus<NW, SCALED>(k);
-                const typename P::V vs = P::vsign(v, sg);
-                P::fma(pnr[k], gr, v); P::fma(pni[k], gi, v);
-                P::fma(psr[k], gr, vs); P::fma(psi[k], gi, vs);
+                if (!ODD) { P::fma(r0[k], ar, v); P::fma(i0[k], ai, v); }
+                else { P::fma(r1[k], ar, v); P::fma(i1[k], ai, v); }
             }
         } else {
-            K ar, ai, br, bi;
-            if (P::kPreCombined) {  // table holds a and b (m = 0 imaginary parts already dropped)
-                ar = gr; ai = gi;
-                P::coef(tab, nalm, 1, base + l, br, bi);
-            } else {
-                K cr, ci;
-                P::coef(tab, nalm, 1, base + l, cr, ci);
-                if (m == 0) { gi = K{}; ci = K{}; }
-                // a = G + iC ; b = (-1)^s (conj G + i conj C)
-                ar = P::ksub(gr, ci); ai = P::kadd(gi, cr);
-                br = P::ksign(P::kadd(gr, ci), sgs); bi = P::ksign(P::ksub(cr, gi), sgs);
-            }
+            K br, bi;
+            P::coef(tab, nalm, 1, base + l, br, bi);
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const typename P::V vp = st.template vplus<NW, SCALED>(k), vm = st.template vminus<NW, SCALED>(k);
-                const typename P::V vps = P::vsign(vp, sg), vms = P::vsign(vm, sg);
-                P::fma(pnr[k], ar, vp); P::fma(pni[k], ai, vp);     // north, column +m
-                P::fma(psr[k], ar, vms); P::fma(psi[k], ai, vms);   // south, column +m
-                P::fma(qnr[k], br, vm); P::fma(qni[k], bi, vm);     // north, column -m
-                P::fma(qsr[k], br, vps); P::fma(qsi[k], bi, vps);   // south, column -m
+                P::fma(r0[k], ar, vp); P::fma(i0[k], ai, vp);
+                P::fma(r2[k], br, vm); P::fma(i2[k], bi, vm);
+                if (!ODD) {
+                    P::fma(r1[k], ar, vm); P::fma(i1[k], ai, vm);
+                    P::fma(r3[k], br, vp); P::fma(i3[k], bi, vp);
+                } else {
+                    P::fms(r1[k], ar, vm); P::fms(i1[k], ai, vm);
+                    P::fms(r3[k], br, vp); P::fms(i3[k], bi, vp);
+                }
             }
         }
+    }
+    // general path (start value and tail): parity known at run time only
+    __device__ __forceinline__ void add_rt(const Rings<P, RPT, SPIN> &st, int l, bool odd)
+    {
+        if (odd) add<1, true, true>(st, l);
+        else add<1, true, false>(st, l);
     }
 };
 
 template <class P, int RPT, bool SPIN, int REG>
 __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN> &acc,
-                                          const typename P::Tab *recm, const typename P::TTab *recc, int lb,
-                                          decltype(P::fac(0)) s0)
+                                          const typename P::Tab *reca, const typename P::TTab *rect, int lb)
 {
 #pragma unroll
     for (int j = 0; j < kBlk; ++j) {
         const int l = lb + j;
-        const auto sg = (j & 1) ? -s0 : s0;
         if (j & 1) {
-            st.template advance<1, REG != 0>(recm, recc, l);
-            if (REG != 1) acc.template add<1, REG == 2>(st, l, sg);
+            st.template advance<1, REG != 0>(reca, rect, l);
+            if (REG != 1) acc.template add<1, REG == 2, true>(st, l);
         } else {
-            st.template advance<0, REG != 0>(recm, recc, l);
-            if (REG != 1) acc.template add<0, REG == 2>(st, l, sg);
+            st.template advance<0, REG != 0>(reca, rect, l);
+            if (REG != 1) acc.template add<0, REG == 2, false>(st, l);
         }
     }
 }
 
 template <class P, int RPT, bool SPIN>
-__global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_ab,
-                                                 const void *__restrict__ rec_c, const double *__restrict__ lognorm,
+__global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_a,
+                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
                                                  int spin, int ntheta, int nnorth, int64_t nalm, int m_begin)
 {
     using Sg = decltype(P::fac(0));
     using Cx = typename P::C;
+    using A = typename P::A;
     const int m = m_begin + blockIdx.y;
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
     if (l0 > lmax) return;
     const int64_t base = alm_base(lmax, m);
-    const typename P::Tab *recm = (const typename P::Tab *)rec_ab + base;
-    const typename P::TTab *recc = SPIN ? (const typename P::TTab *)rec_c + base : nullptr;
+    const typename P::Tab *reca = (const typename P::Tab *)rec_a + base;
+    const typename P::TTab *rect = SPIN ? (const typename P::TTab *)rec_t + base : nullptr;
     const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * RPT;
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
     FwdAcc<P, RPT, SPIN> acc;
-    acc.init(coef, nalm, base, m, s);
+    acc.init(coef, nalm, base);
 
-    acc.template add<1, true>(st, l0, ((l0 - m) & 1) ? Sg(-1) : Sg(1));  // l0 = s > m for m < s
-    int l = l0 + 1;
-    const Sg s0 = ((l - m) & 1) ? Sg(-1) : Sg(1);  // sign of the first degree of every block
+    const int lf = l0 + 1;
+    const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);  // (-1)^(lf - m)
+    acc.add_rt(st, l0, true);                         // l0 = lf - 1
+    int l = lf;
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         const int reg = st.regime();
         acc.renorm();
-        if (reg == 0) fwd_block<P, RPT, SPIN, 0>(st, acc, recm, recc, l, s0);
-        else if (reg == 1) fwd_block<P, RPT, SPIN, 1>(st, acc, recm, recc, l, s0);
-        else fwd_block<P, RPT, SPIN, 2>(st, acc, recm, recc, l, s0);
+        if (reg == 0) fwd_block<P, RPT, SPIN, 0>(st, acc, reca, rect, l);
+        else if (reg == 1) fwd_block<P, RPT, SPIN, 1>(st, acc, reca, rect, l);
+        else fwd_block<P, RPT, SPIN, 2>(st, acc, reca, rect, l);
     }
     for (; l <= lmax; ++l) {  // tail: general path
-        st.advance_moved(recm, recc, l);
-        acc.template add<1, true>(st, l, ((l - m) & 1) ? Sg(-1) : Sg(1));
+        st.advance_moved(reca, rect, l);
+        acc.add_rt(st, l, ((l - lf) & 1) != 0);
     }
 
     // write: spin 0 column m; spin s columns mmax + m (P) and mmax - m (Q), with the minus sign
@@ -556,18 +571,19 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
         const int js = ntheta - 1 - jn;
         if (!SPIN) {
             Cx *col = ring + (int64_t)m * ntheta;
-            col[jn] = P::cout(acc.pnr[k], acc.pni[k]);
-            if (js != jn) col[js] = P::cout(acc.psr[k], acc.psi[k]);
+            col[jn] = P::cout(P::aadd(acc.r0[k], acc.r1[k]), P::aadd(acc.i0[k], acc.i1[k]));
+            if (js != jn)
+                col[js] = P::cout(P::ascale(P::asub(acc.r0[k], acc.r1[k]), s0),
+                                  P::ascale(P::asub(acc.i0[k], acc.i1[k]), s0));
         } else {
+            const Sg ms0 = -s0;
             Cx *colp = ring + (int64_t)(mmax + m) * ntheta;
-            const Cx pn = P::cout(acc.pnr[k], acc.pni[k]), ps = P::cout(acc.psr[k], acc.psi[k]);
-            colp[jn] = mkc(-pn.x, -pn.y);
-            if (js != jn) colp[js] = mkc(-ps.x, -ps.y);
+            colp[jn] = P::cout(P::ascale(acc.r0[k], Sg(-1)), P::ascale(acc.i0[k], Sg(-1)));
+            if (js != jn) colp[js] = P::cout(P::ascale(acc.r1[k], ms0), P::ascale(acc.i1[k], ms0));
             if (m > 0) {
                 Cx *colq = ring + (int64_t)(mmax - m) * ntheta;
-                const Cx qn = P::cout(acc.qnr[k], acc.qni[k]), qs = P::cout(acc.qsr[k], acc.qsi[k]);
-                colq[jn] = mkc(-qn.x, -qn.y);
-                if (js != jn) colq[js] = mkc(-qs.x, -qs.y);
+                colq[jn] = P::cout(P::ascale(acc.r2[k], Sg(-1)), P::ascale(acc.i2[k], Sg(-1)));
+                if (js != jn) colq[js] = P::cout(P::ascale(acc.r3[k], ms0), P::ascale(acc.i3[k], ms0));
             }
         }
     }
@@ -604,14 +620,18 @@ template <class P, int NV> __device__ __forceinline__ typename P::A warp_transpo
     return v[0];
 }
 
+// Ring inputs of one thread.  spin 0: (k0r, k0i) multiplies the degrees with
+// rel = +1 and (k1r, k1i) those with rel = -1, i.e. H_N + H_S or H_N - H_S as
+// (-1)^(l-m) = s0 rel is +1 or -1.  spin s: hn/hs column +m north/south,
+// gn/gs column -m; the south inputs are multiplied by s0 so that a degree
+// takes them with the sign rel.
 template <class P, int RPT, bool SPIN> struct AdjIn {
     using K = typename P::K;
     using A = typename P::A;
-    // spin 0: (hn) = H_N + H_S (even l+m), (hs) = H_N - H_S (odd l+m)
-    // spin s: hn/hs column +m north/south, gn/gs column -m
     K hnr[RPT], hni[RPT], hsr[RPT], hsi[RPT], gnr[RPT], gni[RPT], gsr[RPT], gsi[RPT];
 
-    __device__ __forceinline__ void init(const typename P::C *ring, int rp0, int nnorth, int ntheta, int m, int mmax)
+    __device__ __forceinline__ void init(const typename P::C *ring, int rp0, int nnorth, int ntheta, int m, int mmax,
+                                         bool s0neg)
     {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -627,45 +647,58 @@ template <class P, int RPT, bool SPIN> struct AdjIn {
                     const int64_t colq = (int64_t)(mmax - m) * ntheta;
                     P::ring_in(ring, colq + rp, gnr[k], gni[k]);
                     if (js != rp) P::ring_in(ring, colq + js, gsr[k], gsi[k]);
+                    if (s0neg) {
+                        hsr[k] = P::ksign(hsr[k], -1); hsi[k] = P::ksign(hsi[k], -1);
+                        gsr[k] = P::ksign(gsr[k], -1); gsi[k] = P::ksign(gsi[k], -1);
+                    }
                 } else {
                     const K ar = hnr[k], ai = hni[k], br = hsr[k], bi = hsi[k];
-                    hnr[k] = P::kadd(ar, br); hni[k] = P::kadd(ai, bi);
-                    hsr[k] = P::ksub(ar, br); hsi[k] = P::ksub(ai, bi);
+                    const K er = P::kadd(ar, br), ei = P::kadd(ai, bi), orr = P::ksub(ar, br), oi = P::ksub(ai, bi);
+                    hnr[k] = s0neg ? orr : er; hni[k] = s0neg ? oi : ei;
+                    hsr[k] = s0neg ? er : orr; hsi[k] = s0neg ? ei : oi;
                 }
             }
         }
     }
-    // partial sums of one degree (value in word NW) into part[0..NCOMP)
-    template <int NW, bool SCALED>
-    __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, bool odd, A *part) const
+    // partial sums of one degree (value in word NW) into part[0..NCOMP); ODD: rel = -1
+    template <int NW, bool SCALED, bool ODD>
+    __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, A *part) const
     {
-        using Sg = decltype(P::fac(0));
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const typename P::V vp = st.template vplus<NW, SCALED>(k);
             if (!SPIN) {
-                const K hr = odd ? hsr[k] : hnr[k], hi = odd ? hsi[k] : hni[k];
-                P::fma(part[0], hr, vp);
-                P::fma(part[1], hi, vp);
+                P::fma(part[0], ODD ? hsr[k] : hnr[k], vp);
+                P::fma(part[1], ODD ? hsi[k] : hni[k], vp);
             } else {
                 const typename P::V vm = st.template vminus<NW, SCALED>(k);
-                const Sg sg = odd ? Sg(-1) : Sg(1);
-                const typename P::V vms = P::vsign(vm, sg), vps = P::vsign(vp, sg);
-                // U += lam+ H_m(N) + sg lam- H_m(S) ; V += lam- H_-m(N) + sg lam+ H_-m(S)
-                P::fma2(part[0], hnr[k], vp, hsr[k], vms);
-                P::fma2(part[1], hni[k], vp, hsi[k], vms);
-                P::fma2(part[2], gnr[k], vm, gsr[k], vps);
-                P::fma2(part[3], gni[k], vm, gsi[k], vps);
+                // U += lam+ H_m(N) + rel lam- s0 H_m(S) ; V += lam- H_-m(N) + rel lam+ s0 H_-m(S)
+                if (!ODD) {
+                    P::fma2(part[0], hnr[k], vp, hsr[k], vm);
+                    P::fma2(part[1], hni[k], vp, hsi[k], vm);
+                    P::fma2(part[2], gnr[k], vm, gsr[k], vp);
+                    P::fma2(part[3], gni[k], vm, gsi[k], vp);
+                } else {
+                    P::fma2m(part[0], hnr[k], vp, hsr[k], vm);
+                    P::fma2m(part[1], hni[k], vp, hsi[k], vm);
+                    P::fma2m(part[2], gnr[k], vm, gsr[k], vp);
+                    P::fma2m(part[3], gni[k], vm, gsi[k], vp);
+                }
             }
         }
     }
+    __device__ __forceinline__ void add_rt(const Rings<P, RPT, SPIN> &st, bool odd, A *part) const
+    {
+        if (odd) add<1, true, true>(st, part);
+        else add<1, true, false>(st, part);
+    }
 };
 
-// Adds the warp sums of the degrees lb + i (value index i * NCOMP + c) into
-// a_lm (spin 0) or G, C (spin s).
+// Adds the warp sums of the degrees lb + i (value index i * NCOMP + c),
+// times the monic scale c_l, into a_lm (spin 0) or G, C (spin s).
 template <class P, bool SPIN, int NV>
-__device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *out, int64_t base, int64_t nalm, int m,
-                                      int lb, int lmax, decltype(P::fac(0)) sgs)
+__device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *out, const double *__restrict__ sc,
+                                      int64_t base, int64_t nalm, int m, int lb, int lmax, decltype(P::fac(0)) sgs)
 {
     using A = typename P::A;
     using Sg = decltype(P::fac(0));
@@ -678,7 +711,7 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
     const int l = lb + i;
     if (!SPIN) {
         if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1))
-            P::atomic_add(out + 2 * (base + l) + c, tot);
+            P::atomic_add(out + 2 * (base + l) + c, tot, __ldg(sc + l));
     } else {
         // lanes hold U.re, U.im, V.re, V.im of degree l at c = 0..3; the G/C
         // split is linear, so each warp adds its share directly:
@@ -693,35 +726,35 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
             else if (c == 1) { val = P::ascale(P::aadd(tot, P::ascale(other, -sgs)), -h); dst = 2 * (base + l) + 1; }
             else if (c == 2) { val = P::ascale(P::aadd(other, P::ascale(tot, -sgs)), h); dst = 2 * (nalm + base + l) + 1; }
             else { val = P::ascale(P::aadd(other, P::ascale(tot, sgs)), -h); dst = 2 * (nalm + base + l); }
-            if (!(m == 0 && (c == 1 || c == 2))) P::atomic_add(out + dst, val);
+            if (!(m == 0 && (c == 1 || c == 2))) P::atomic_add(out + dst, val, __ldg(sc + l));
         }
     }
 }
 
 template <class P, int RPT, bool SPIN, int REG>
 __device__ __forceinline__ void adj_block(Rings<P, RPT, SPIN> &st, const AdjIn<P, RPT, SPIN> &in, typename P::A *part,
-                                          const typename P::Tab *recm, const typename P::TTab *recc, int lb, bool odd0)
+                                          const typename P::Tab *reca, const typename P::TTab *rect, int lb)
 {
     constexpr int NCOMP = SPIN ? 4 : 2;
 #pragma unroll
     for (int j = 0; j < kBlk; ++j) {
         const int l = lb + j;
-        const bool odd = (j & 1) ? !odd0 : odd0;
         if (j & 1) {
-            st.template advance<1, REG != 0>(recm, recc, l);
-            if (REG != 1) in.template add<1, REG == 2>(st, odd, part + j * NCOMP);
+            st.template advance<1, REG != 0>(reca, rect, l);
+            if (REG != 1) in.template add<1, REG == 2, true>(st, part + j * NCOMP);
         } else {
-            st.template advance<0, REG != 0>(recm, recc, l);
-            if (REG != 1) in.template add<0, REG == 2>(st, odd, part + j * NCOMP);
+            st.template advance<0, REG != 0>(reca, rect, l);
+            if (REG != 1) in.template add<0, REG == 2, false>(st, part + j * NCOMP);
         }
     }
 }
 
 template <class P, int RPT, bool SPIN>
-__global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_ab,
-                                                 const void *__restrict__ rec_c, const double *__restrict__ lognorm,
-                                                 RingTab rt, typename P::C *__restrict__ alm, int lmax, int mmax,
-                                                 int spin, int ntheta, int nnorth, int64_t nalm, int m_begin)
+__global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_a,
+                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
+                                                 const double *__restrict__ scale, RingTab rt,
+                                                 typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
+                                                 int ntheta, int nnorth, int64_t nalm, int m_begin)
 {
     using A = typename P::A;
     using R = typename P::R;
@@ -733,38 +766,39 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     const int l0 = m > s ? m : s;
     if (l0 > lmax) return;
     const int64_t base = alm_base(lmax, m);
-    const typename P::Tab *recm = (const typename P::Tab *)rec_ab + base;
-    const typename P::TTab *recc = SPIN ? (const typename P::TTab *)rec_c + base : nullptr;
+    const typename P::Tab *reca = (const typename P::Tab *)rec_a + base;
+    const typename P::TTab *rect = SPIN ? (const typename P::TTab *)rec_t + base : nullptr;
+    const double *sc = scale + base;
     const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * RPT;
     const Sg sgs = (s & 1) ? Sg(-1) : Sg(1);
     R *out = reinterpret_cast<R *>(alm);
+    const int lf = l0 + 1;
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
     AdjIn<P, RPT, SPIN> in;
-    in.init(ring, rp0, nnorth, ntheta, m, mmax);
+    in.init(ring, rp0, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0);
 
     {  // degree l0 (the start value): one reduction of NCOMP values
         A p0[NCOMP];
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
-        in.template add<1, true>(st, ((l0 - m) & 1) != 0, p0);  // l0 = s > m for m < s
-        flush<P, SPIN, NCOMP>(p0, out, base, nalm, m, l0, lmax, sgs);
+        in.add_rt(st, true, p0);  // l0 = lf - 1
+        flush<P, SPIN, NCOMP>(p0, out, sc, base, nalm, m, l0, lmax, sgs);
     }
-    int l = l0 + 1;
-    const bool odd0 = ((l - m) & 1) != 0;
+    int l = lf;
     A part[NV];
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         const int reg = st.regime();
         if (reg == 1) {  // every contribution of this block is below 2^-180: recursion only
-            adj_block<P, RPT, SPIN, 1>(st, in, part, recm, recc, l, odd0);
+            adj_block<P, RPT, SPIN, 1>(st, in, part, reca, rect, l);
             continue;
         }
 #pragma unroll
         for (int i = 0; i < NV; ++i) part[i] = P::azero();
-        if (reg == 0) adj_block<P, RPT, SPIN, 0>(st, in, part, recm, recc, l, odd0);
-        else adj_block<P, RPT, SPIN, 2>(st, in, part, recm, recc, l, odd0);
-        flush<P, SPIN, NV>(part, out, base, nalm, m, l, lmax, sgs);
+        if (reg == 0) adj_block<P, RPT, SPIN, 0>(st, in, part, reca, rect, l);
+        else adj_block<P, RPT, SPIN, 2>(st, in, part, reca, rect, l);
+        flush<P, SPIN, NV>(part, out, sc, base, nalm, m, l, lmax, sgs);
     }
     if (l <= lmax) {  // tail: fewer than kBlk degrees, general path
 #pragma unroll
@@ -772,132 +806,169 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
 #pragma unroll
         for (int j = 0; j < kBlk; ++j) {
             if (l + j <= lmax) {
-                st.advance_moved(recm, recc, l + j);
-                in.template add<1, true>(st, ((l + j - m) & 1) != 0, part + j * NCOMP);
+                st.advance_moved(reca, rect, l + j);
+                in.add_rt(st, (j & 1) != 0, part + j * NCOMP);
             }
         }
-        flush<P, SPIN, NV>(part, out, base, nalm, m, l, lmax, sgs);
+        flush<P, SPIN, NV>(part, out, sc, base, nalm, m, l, lmax, sgs);
     }
 }
 
 // ------------------------------------------------------- coefficient tables
 // For the step (l-1 -> l), j = l - 1:
-//   A = (j+1) sqrt((2j+3)(2j+1) / (((j+1)^2-m^2)((j+1)^2-s^2)))
-//   B = (j+1)/j sqrt((2j+3)/(2j-1)) sqrt((j^2-m^2)(j^2-s^2) / (((j+1)^2-m^2)((j+1)^2-s^2)))
-//   T = m s / (j (j+1))
-// Written as df32 (ab_df, t_df) and/or FP64 (ab64, t64) tables.
-__global__ void k_rec_tables(int lmax, int spin, void *ab_df, void *t_df, void *ab64, void *t64)
+//   A_l = (j+1) sqrt((2j+3)(2j+1) / (((j+1)^2-m^2)((j+1)^2-s^2)))
+//   B_l = (j+1)/j sqrt((2j+3)/(2j-1)) sqrt((j^2-m^2)(j^2-s^2) / (((j+1)^2-m^2)((j+1)^2-s^2)))
+//   T_l = m s / (j (j+1))
+// Monic form: c_{l0} = c_{l0+1} = 1, c_l = B_l c_{l-2} (l >= l0 + 2),
+// alpha_l = A_l c_{l-1} / c_l, tau_l = alpha_l T_l; c_l = 0 for l < l0.
+// One CTA per m: two threads run the two parity chains of c, then all
+// threads fill alpha and tau.  Written as df32 (a_df, t_df) and/or FP64
+// (a64, t64) tables; scale holds c (FP64).
+__device__ __forceinline__ double rec_B(int l, int m, int s)
+{
+    const double j = l - 1, mm = m, ss = s;
+    const double den = ((j + 1) * (j + 1) - mm * mm) * ((j + 1) * (j + 1) - ss * ss);
+    return (j + 1) / j * sqrt((2 * j + 3) / (2 * j - 1) * ((j * j - mm * mm) * (j * j - ss * ss) / den));
+}
+
+__global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, float2 *__restrict__ a_df,
+                             float2 *__restrict__ t_df, double *__restrict__ a64, double *__restrict__ t64)
 {
     const int m = blockIdx.x;
     const int s = spin;
     const int l0 = m > s ? m : s;
     const int64_t base = alm_base(lmax, m);
+    for (int l = m + threadIdx.x; l < l0 && l <= lmax; l += blockDim.x) scale[base + l] = 0.0;
+    if (threadIdx.x < 2) {
+        int l = l0 + threadIdx.x;
+        if (l <= lmax) scale[base + l] = 1.0;
+        double c = 1.0;
+        for (l += 2; l <= lmax; l += 2) {
+            c *= rec_B(l, m, s);
+            scale[base + l] = c;
+        }
+    }
+    __syncthreads();
     for (int l = l0 + 1 + threadIdx.x; l <= lmax; l += blockDim.x) {
         const double j = l - 1, mm = m, ss = s;
         const double den = ((j + 1) * (j + 1) - mm * mm) * ((j + 1) * (j + 1) - ss * ss);
         const double A = (j + 1) * sqrt((2 * j + 3) * (2 * j + 1) / den);
-        double B = 0.0, T = 0.0;
-        if (j > 0) {
-            B = (j + 1) / j * sqrt((2 * j + 3) / (2 * j - 1)) * sqrt((j * j - mm * mm) * (j * j - ss * ss) / den);
-            T = mm * ss / (j * (j + 1));
+        const double T = j > 0 ? mm * ss / (j * (j + 1)) : 0.0;
+        const double alpha = A * (scale[base + l - 1] / scale[base + l]);
+        const double tau = alpha * T;
+        if (a_df) {
+            a_df[base + l] = make_float2((float)alpha, (float)(alpha - (double)(float)alpha));
+            if (t_df) t_df[base + l] = make_float2((float)tau, (float)(tau - (double)(float)tau));
         }
-        if (ab_df) {
-            const float ah = (float)A, bh = (float)B, th = (float)T;
-            ((float4 *)ab_df)[base + l] = make_float4(ah, (float)(A - ah), bh, (float)(B - bh));
-            if (t_df) ((float2 *)t_df)[base + l] = make_float2(th, (float)(T - th));
-        }
-        if (ab64) {
-            ((double2 *)ab64)[base + l] = make_double2(A, B);
-            if (t64) ((double *)t64)[base + l] = T;
+        if (a64) {
+            a64[base + l] = alpha;
+            if (t64) t64[base + l] = tau;
         }
     }
 }
 
-// df32 coefficients for the PolDD forward: spin 0 the a_lm; spin s
-// a = G + iC and b = (-1)^s (conj G + i conj C) (m = 0 imaginary parts of
-// G and C dropped).  One entry per alm index, orders m >= m_begin.
-__global__ void k_coef_dd(const double2 *__restrict__ alm, float4 *__restrict__ out, int lmax, int mmax, int spin,
-                          int64_t nalm, int m_begin)
+// Forward coefficients of one call: spin 0 c_l a_lm; spin s c_l (G + iC) and
+// c_l (-1)^s (conj G + i conj C) (m = 0: imaginary parts of a, G, C dropped);
+// zero for l < l0.  Entries of orders m < m_split are written as OUT_LO, the
+// others as OUT_HI: float2 (FP32 plans), double2 (FP64 plans, native FP64
+// orders) or float4 df32 (FP64 plans, df32 orders).
+template <typename T> __device__ __forceinline__ void put_coef(void *out, int64_t i, double re, double im);
+template <> __device__ __forceinline__ void put_coef<float2>(void *out, int64_t i, double re, double im)
 {
-    const int m = m_begin + blockIdx.y;
+    ((float2 *)out)[i] = make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ void put_coef<double2>(void *out, int64_t i, double re, double im)
+{
+    ((double2 *)out)[i] = make_double2(re, im);
+}
+template <> __device__ __forceinline__ void put_coef<float4>(void *out, int64_t i, double re, double im)
+{
+    const float rh = (float)re, ih = (float)im;
+    ((float4 *)out)[i] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+}
+
+template <typename Tin, typename OUT_LO, typename OUT_HI>
+__global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restrict__ scale, void *__restrict__ out,
+                            int lmax, int spin, int64_t nalm, int m_split)
+{
+    const int m = blockIdx.y;
     const int64_t base = alm_base(lmax, m);
     const double sgs = (spin & 1) ? -1.0 : 1.0;
+    const bool hi = m >= m_split;
     for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
         const int64_t i = base + l;
-        double2 g = alm[i];
-        if (m == 0) g.y = 0.0;
+        const double c = scale[i];
+        const Tin gv = alm[i];
+        const double gr = gv.x, gi = m == 0 ? 0.0 : (double)gv.y;
         if (!spin) {
-            const float rh = (float)g.x, ih = (float)g.y;
-            out[i] = make_float4(rh, (float)(g.x - rh), ih, (float)(g.y - ih));
+            if (hi) put_coef<OUT_HI>(out, i, c * gr, c * gi);
+            else put_coef<OUT_LO>(out, i, c * gr, c * gi);
         } else {
-            double2 c = alm[nalm + i];
-            if (m == 0) c.y = 0.0;
-            const double ar = g.x - c.y, ai = g.y + c.x;
-            const double br = sgs * (g.x + c.y), bi = sgs * (c.x - g.y);
-            float h0 = (float)ar, h1 = (float)ai;
-            out[i] = make_float4(h0, (float)(ar - h0), h1, (float)(ai - h1));
-            h0 = (float)br;
-            h1 = (float)bi;
-            out[nalm + i] = make_float4(h0, (float)(br - h0), h1, (float)(bi - h1));
+            const Tin cv = alm[nalm + i];
+            const double cr = cv.x, ci = m == 0 ? 0.0 : (double)cv.y;
+            const double ar = c * (gr - ci), ai = c * (gi + cr);
+            const double br = c * sgs * (gr + ci), bi = c * sgs * (cr - gi);
+            if (hi) { put_coef<OUT_HI>(out, i, ar, ai); put_coef<OUT_HI>(out, nalm + i, br, bi); }
+            else { put_coef<OUT_LO>(out, i, ar, ai); put_coef<OUT_LO>(out, nalm + i, br, bi); }
         }
     }
 }
 
 template <class P, int RPT, bool SPIN>
-cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ab, const void *tc,
+cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                        void *ring, int m_begin, int m_end, cudaStream_t st)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
-    k_leg_fwd<P, RPT, SPIN><<<grid, block, 0, st>>>(coef, ab, tc, p.lognorm, p.rings, (typename P::C *)ring, p.lmax,
+    k_leg_fwd<P, RPT, SPIN><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring, p.lmax,
                                                     p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin);
     return cudaGetLastError();
 }
 
 template <class P, int RPT, bool SPIN>
-cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ab, const void *tc,
+cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                        void *alm, int m_begin, int m_end, cudaStream_t st)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
-    k_leg_adj<P, RPT, SPIN><<<grid, block, 0, st>>>((const typename P::C *)ring, ab, tc, p.lognorm, p.rings,
+    k_leg_adj<P, RPT, SPIN><<<grid, block, 0, st>>>((const typename P::C *)ring, ta, tt, p.lognorm, p.scale, p.rings,
                                                     (typename P::C *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
                                                     p.nalm, m_begin);
     return cudaGetLastError();
 }
 
 template <class P, bool SPIN>
-cudaError_t fwd_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ab, const void *tc,
+cudaError_t fwd_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                     void *ring, int m_begin, int m_end, cudaStream_t st)
 {
-    if (sh.rpt == 1) return fwd_launch<P, 1, SPIN>(p, sh, coef, ab, tc, ring, m_begin, m_end, st);
-    return fwd_launch<P, 2, SPIN>(p, sh, coef, ab, tc, ring, m_begin, m_end, st);
+    if (sh.rpt == 1) return fwd_launch<P, 1, SPIN>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
+    return fwd_launch<P, 2, SPIN>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
 }
 
 template <class P, bool SPIN>
-cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ab, const void *tc,
+cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                     void *alm, int m_begin, int m_end, cudaStream_t st)
 {
-    if (sh.rpt == 1) return adj_launch<P, 1, SPIN>(p, sh, ring, ab, tc, alm, m_begin, m_end, st);
-    return adj_launch<P, 2, SPIN>(p, sh, ring, ab, tc, alm, m_begin, m_end, st);
+    if (sh.rpt == 1) return adj_launch<P, 1, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
+    return adj_launch<P, 2, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
 }
 
 template <class P>
-cudaError_t fwd_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ab, const void *tc,
+cudaError_t fwd_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                      void *ring, int m_begin, int m_end, cudaStream_t st)
 {
-    return p.spin ? fwd_rpt<P, true>(p, sh, coef, ab, tc, ring, m_begin, m_end, st)
-                  : fwd_rpt<P, false>(p, sh, coef, ab, tc, ring, m_begin, m_end, st);
+    return p.spin ? fwd_rpt<P, true>(p, sh, coef, ta, tt, ring, m_begin, m_end, st)
+                  : fwd_rpt<P, false>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
 }
 
 template <class P>
-cudaError_t adj_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ab, const void *tc,
+cudaError_t adj_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                      void *alm, int m_begin, int m_end, cudaStream_t st)
 {
-    return p.spin ? adj_rpt<P, true>(p, sh, ring, ab, tc, alm, m_begin, m_end, st)
-                  : adj_rpt<P, false>(p, sh, ring, ab, tc, alm, m_begin, m_end, st);
+    return p.spin ? adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st)
+                  : adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
 }
 
 // Kernel entry of one (arithmetic, spin, rings-per-thread, direction) variant.
@@ -945,11 +1016,12 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt)
 cudaError_t launch_rec_tables(Plan &p)
 {
     if (p.prec == LENS_FP32)
-        k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.rec_ab, p.spin ? p.rec_c : nullptr, nullptr,
-                                                       nullptr);
+        k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, (float2 *)p.rec_a,
+                                                       p.spin ? (float2 *)p.rec_t : nullptr, nullptr, nullptr);
     else
-        k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.rec_ab_df, p.spin ? p.rec_c_df : nullptr,
-                                                       p.rec_ab, p.spin ? p.rec_c : nullptr);
+        k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, (float2 *)p.rec_a_df,
+                                                       p.spin ? (float2 *)p.rec_t_df : nullptr, (double *)p.rec_a,
+                                                       p.spin ? (double *)p.rec_t : nullptr);
     return cudaGetLastError();
 }
 
@@ -976,16 +1048,18 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     const size_t eb = p.prec == LENS_FP32 ? 8 : 16;
     cudaError_t e = cudaMemsetAsync(ring, 0, eb * (size_t)p.ncol * p.ntheta, st);
     if (e != cudaSuccess) return e;
-    if (p.prec == LENS_FP32) return fwd_spin<PolDF>(p, p.leg_f, alm, p.rec_ab, p.rec_c, ring, 0, p.mmax + 1, st);
-    if (p.m_df > 0 && (e = fwd_spin<PolF64>(p, p.leg_f, alm, p.rec_ab, p.rec_c, ring, 0, p.m_df, st)) != cudaSuccess)
-        return e;
-    if (p.m_df <= p.mmax) {
-        dim3 g(4, p.mmax + 1 - p.m_df);
-        k_coef_dd<<<g, 256, 0, st>>>((const double2 *)alm, (float4 *)p.coef_dd, p.lmax, p.mmax, p.spin, p.nalm, p.m_df);
+    const dim3 g(4, p.mmax + 1);
+    if (p.prec == LENS_FP32) {
+        k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef, p.lmax, p.spin,
+                                                               p.nalm, p.mmax + 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = fwd_spin<PolDD>(p, p.leg_fd, p.coef_dd, p.rec_ab_df, p.rec_c_df, ring, p.m_df, p.mmax + 1, st);
+        return fwd_spin<PolDF>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
     }
-    return e;
+    k_coef_prep<double2, double2, float4><<<g, 256, 0, st>>>((const double2 *)alm, p.scale, p.coef, p.lmax, p.spin,
+                                                             p.nalm, p.m_df);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = fwd_spin<PolF64>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.m_df, st)) != cudaSuccess) return e;
+    return fwd_spin<PolDD>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
 }
 
 cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st)
@@ -993,11 +1067,9 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
     const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * (p.spin ? 2 : 1);
     cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);  // the kernels add warp sums atomically
     if (e != cudaSuccess) return e;
-    if (p.prec == LENS_FP32) return adj_spin<PolDF>(p, p.leg_a, ring, p.rec_ab, p.rec_c, alm, 0, p.mmax + 1, st);
-    if (p.m_df > 0 && (e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_ab, p.rec_c, alm, 0, p.m_df, st)) != cudaSuccess)
-        return e;
-    if (p.m_df <= p.mmax) e = adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_ab_df, p.rec_c_df, alm, p.m_df, p.mmax + 1, st);
-    return e;
+    if (p.prec == LENS_FP32) return adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st);
+    if ((e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st)) != cudaSuccess) return e;
+    return adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st);
 }
 
 }  // namespace gsl

@@ -337,7 +337,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // for m < m_df and df32 recursion + df32 accumulation for m >= m_df.  df32
     // loses ~2^-45 per operation and the recursion amplifies rounding most at
     // low m near the poles.  Measured eps_eff of the whole forward at lmax 4096,
-    // HEALPix Nside 2048, eps 1e-10 (spin 0 / spin 2) against the oracle:
+    // HEALPix Nside 2048, eps 1e-10 (spin 0 / spin 2) against FP64 direct summation:
     //   df32 from m = 1: 2.3e-10 / 1.7e-10;  m = 64: 6.1e-11 / 5.1e-11;
     //   m = 128: 2.5e-11 / 2.3e-11;  m = 256: 8.3e-12 / 8.8e-12 (= all-FP64).
     // Hence m_df = 64 for epsilon >= 1e-9, 256 for epsilon >= 5e-11, none below.
@@ -365,16 +365,15 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     cudaError_t e;
     // ---- device buffers
     if ((e = B.alloc((void **)&p->flags, sizeof(unsigned) * 4, false)) != cudaSuccess) return bailc(e, "alloc flags");
-    if ((e = B.alloc(&p->rec_ab, (size_t)p->nalm * (prec == LENS_FP32 ? 16 : 16), false)) != cudaSuccess)
-        return bailc(e, "alloc rec_ab");
-    if (spin && (e = B.alloc(&p->rec_c, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_c");
+    if ((e = B.alloc(&p->rec_a, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_a");
+    if (spin && (e = B.alloc(&p->rec_t, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_t");
+    if ((e = B.alloc((void **)&p->scale, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc scale");
     if (prec == LENS_FP64 && p->m_df <= mmax) {
-        if ((e = B.alloc(&p->rec_ab_df, (size_t)p->nalm * 16, false)) != cudaSuccess) return bailc(e, "alloc rec_ab_df");
-        if (spin && (e = B.alloc(&p->rec_c_df, (size_t)p->nalm * 8, false)) != cudaSuccess)
-            return bailc(e, "alloc rec_c_df");
-        if ((e = B.alloc(&p->coef_dd, (size_t)p->nalm * 16 * (spin ? 2 : 1), true)) != cudaSuccess)
-            return bailc(e, "alloc coef_dd");
+        if ((e = B.alloc(&p->rec_a_df, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_a_df");
+        if (spin && (e = B.alloc(&p->rec_t_df, (size_t)p->nalm * 8, false)) != cudaSuccess)
+            return bailc(e, "alloc rec_t_df");
     }
+    if ((e = B.alloc(&p->coef, (size_t)p->nalm * esz * ncomp, true)) != cudaSuccess) return bailc(e, "alloc coef");
     if ((e = B.alloc(&p->ring, esz * (size_t)p->ncol * p->ntheta, true)) != cudaSuccess) return bailc(e, "alloc ring");
     if ((e = B.alloc(&p->X, esz * (size_t)p->R * p->ncol, true)) != cudaSuccess) return bailc(e, "alloc X");
     if ((e = B.alloc(&p->grid, (esz / 2) * ncomp * (size_t)p->R * p->pitch, true)) != cudaSuccess)
