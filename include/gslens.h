@@ -112,7 +112,8 @@ typedef struct {
  *   theta_d, phi_d   device double[npoints] deflected coordinates.
  *   chi_d      device double[npoints] spin phase, or NULL (ignored for spin 0).
  *   epsilon    target relative accuracy (Sect. 4, eps_eff); FP32 plans accept
- *              epsilon >= 1e-6, FP64 plans epsilon >= 1e-13.
+ *              epsilon >= 2e-6 (FP32 rounding alone leaves ~1.2e-6 at lmax
+ *              4096), FP64 plans epsilon >= 1e-13.
  *   prec       LENS_FP32 or LENS_FP64.
  *   flags      reserved, must be 0.
  *   stream     cudaStream_t (NULL = legacy default stream).

@@ -211,6 +211,10 @@ def test_domain_errors():
     with pytest.raises(LensError) as ex:
         LensPlan(8, np.array([0.1]), np.array([0.0]), epsilon=1e-7, precision="fp32", device=DEV)
     assert ex.value.status == 3
+    with pytest.raises(LensError) as ex:  # FP32 floor: measured eps_eff 1.2e-6 at lmax 4096
+        LensPlan(8, np.array([0.1]), np.array([0.0]), epsilon=1.5e-6, precision="fp32", device=DEV)
+    assert ex.value.status == 3
+    LensPlan(8, np.array([0.1]), np.array([0.0]), epsilon=2e-6, precision="fp32", device=DEV).close()
 
 
 def test_batch_and_host_entry_points():
