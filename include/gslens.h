@@ -152,6 +152,24 @@ int lens_synthesis(lens_plan p, const void *alm_d, void *map_d, int nmaps, void 
 int lens_adjoint(lens_plan p, const void *map_d, void *alm_d, int nmaps, void *stream);
 
 /*
+ * Gradients for reverse-mode differentiation (no counterpart in the paper;
+ * they follow from the exact adjoint of Sect. 2).  For a real loss L and
+ * complex a_lm, gradients are written dL/dRe + i dL/dIm.  lens_synthesis
+ * counts each m > 0 coefficient for both +m and -m (real fields), so with the
+ * order weight w_0 = 1, w_m = 2 (m > 0):
+ *   lens_synthesis_vjp: grad_map_d [nmaps][ncomp][npoints] real = dL/dmap of
+ *       lens_synthesis's output; writes grad_alm_d [nmaps][ncomp][nalm]
+ *       complex = dL/da_lm = w_m * lens_adjoint(grad_map).
+ *   lens_adjoint_vjp: grad_alm_d = dL/da_lm of lens_adjoint's output; writes
+ *       grad_map_d = dL/dmap = lens_synthesis(grad_alm / w_m).
+ * Imaginary parts at m = 0 receive zero gradient (lens_synthesis ignores
+ * them and lens_adjoint returns them as zero).  Same layouts, stream
+ * semantics and errors as lens_synthesis / lens_adjoint.
+ */
+int lens_synthesis_vjp(lens_plan p, const void *grad_map_d, void *grad_alm_d, int nmaps, void *stream);
+int lens_adjoint_vjp(lens_plan p, const void *grad_alm_d, void *grad_map_d, int nmaps, void *stream);
+
+/*
  * The same two operations on host buffers: the inputs are copied to the
  * device, the transform runs, the outputs are copied back; returns after the
  * stream has finished.  Pinned host memory gives full copy bandwidth.

@@ -7,6 +7,7 @@ into raw device pointers and sizes.  PyTorch provides device memory and streams.
     plan = LensPlan(lmax, theta, phi, chi=None, spin=0, epsilon=1e-5, precision="fp32")
     m = plan.synthesis(alm)    # forward lensing (Eq. "forward" / "forwardpol")
     a = plan.adjoint(m)        # adjoint (Eq. "adjoint" and its spin-s form)
+    m = synthesis(plan, alm)   # the same, differentiable (torch.autograd; backward = exact adjoint)
 
 a_lm layout: complex tensor [ncomp, nalm] (or [nmaps, ncomp, nalm]) with
 index(l, m) = m (2 lmax + 1 - m)/2 + l; ncomp = 1 (spin 0) or 2 (G, C).
@@ -22,7 +23,7 @@ import torch
 from . import _native
 from ._native import LensError, PlanInfo, PlanParams
 
-__all__ = ["LensPlan", "LensError", "pointing", "nalm", "lib_path"]
+__all__ = ["LensPlan", "LensError", "synthesis", "adjoint", "pointing", "nalm", "lib_path"]
 
 _PREC = {"fp32": 0, "fp64": 1}
 
@@ -151,6 +152,26 @@ class LensPlan:
                                                   _stream_handle(stream)))
         return out
 
+    def synthesis_vjp(self, grad_map: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """dL/da_lm for a real loss L of synthesis's output, given dL/dmap (lens_synthesis_vjp)."""
+        g, nmaps = self._map_arg(grad_map)
+        lead = g.shape[:-2] if g.dim() > 2 else ()
+        if out is None:
+            out = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+        _native.check(_native.load().lens_synthesis_vjp(self._h, g.data_ptr(), out.data_ptr(), nmaps,
+                                                        _stream_handle(stream)))
+        return out
+
+    def adjoint_vjp(self, grad_alm: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """dL/dmap for a real loss L of adjoint's output, given dL/da_lm (lens_adjoint_vjp)."""
+        g, nmaps = self._alm_arg(grad_alm)
+        lead = g.shape[:-2] if g.dim() > 2 else ()
+        if out is None:
+            out = torch.empty(*lead, self.ncomp, self.npoints, dtype=self.real_dtype, device=self.device)
+        _native.check(_native.load().lens_adjoint_vjp(self._h, g.data_ptr(), out.data_ptr(), nmaps,
+                                                      _stream_handle(stream)))
+        return out
+
     def synthesis_host(self, alm_h, out_h=None, stream=None):
         """Forward on host (CPU) tensors: copies in, transform, copies out (synchronous)."""
         alm_h = torch.as_tensor(alm_h).to(self.complex_dtype).contiguous()
@@ -188,6 +209,38 @@ class LensPlan:
         _native.check(_native.load().lens_ring_adjoint(self._h, ring.data_ptr(), out.data_ptr(),
                                                        _stream_handle(stream)))
         return out
+
+
+class _Synthesis(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, alm, plan):
+        ctx.plan = plan
+        return plan.synthesis(alm)
+
+    @staticmethod
+    def backward(ctx, grad_map):
+        return ctx.plan.synthesis_vjp(grad_map), None
+
+
+class _Adjoint(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, m, plan):
+        ctx.plan = plan
+        return plan.adjoint(m)
+
+    @staticmethod
+    def backward(ctx, grad_alm):
+        return ctx.plan.adjoint_vjp(grad_alm), None
+
+
+def synthesis(plan: LensPlan, alm: torch.Tensor) -> torch.Tensor:
+    """Differentiable forward lensing: plan.synthesis with backward = lens_synthesis_vjp."""
+    return _Synthesis.apply(alm, plan)
+
+
+def adjoint(plan: LensPlan, m: torch.Tensor) -> torch.Tensor:
+    """Differentiable adjoint lensing: plan.adjoint with backward = lens_adjoint_vjp."""
+    return _Adjoint.apply(m, plan)
 
 
 def pointing(theta: torch.Tensor, phi: torch.Tensor, alpha_theta: torch.Tensor, alpha_phi: torch.Tensor,

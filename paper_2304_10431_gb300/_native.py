@@ -21,6 +21,8 @@ EXPORTS = {
     "lens_plan_info": (_i32, [_vp, _vp]),
     "lens_synthesis": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_synthesis_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_adjoint_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),

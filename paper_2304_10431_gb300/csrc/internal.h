@@ -12,6 +12,7 @@ namespace gsl {
 
 constexpr int kMaxFftStages = 24;
 constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
+constexpr int kTileR = 16, kTileC = 32;  // grid tile of the point sort (rows x columns)
 
 // One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
 // and the digit-reversal table (input element i is stored at position perm[i]).
@@ -78,6 +79,8 @@ struct Plan {
     uint32_t *cell = nullptr;  // row * pitch + col of the first tap
     void *frac = nullptr;      // float2 / double2 (u - i0, v - j0)
     int32_t *perm = nullptr;   // sorted -> user index
+    uint32_t *tile_start = nullptr;  // [ntiles + 1] first sorted point of each 16 x 32 grid tile
+    int ntile_c = 0, ntiles = 0;     // tiles per grid row band, total tiles
     void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
     double *wts = nullptr;     // FP64 plans: [npts][2W] kernel weights (theta taps, then phi taps)
 
@@ -99,8 +102,10 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);
-cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st);
-cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st);
+// wpos multiplies the orders m > 0 (1 for the transforms themselves; the
+// gradient entry points use 1/2 forward and 2 adjoint)
+cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st, double wpos = 1.0);
+cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st, double wpos = 1.0);
 cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st);
 cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st);
 cudaError_t launch_phi_fwd(const Plan &p, const void *X, void *grid, cudaStream_t st);

@@ -695,10 +695,12 @@ template <class P, int RPT, bool SPIN> struct AdjIn {
 };
 
 // Adds the warp sums of the degrees lb + i (value index i * NCOMP + c),
-// times the monic scale c_l, into a_lm (spin 0) or G, C (spin s).
+// times the monic scale c_l and the order weight wm, into a_lm (spin 0) or
+// G, C (spin s).
 template <class P, bool SPIN, int NV>
 __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *out, const double *__restrict__ sc,
-                                      int64_t base, int64_t nalm, int m, int lb, int lmax, decltype(P::fac(0)) sgs)
+                                      double wm, int64_t base, int64_t nalm, int m, int lb, int lmax,
+                                      decltype(P::fac(0)) sgs)
 {
     using A = typename P::A;
     using Sg = decltype(P::fac(0));
@@ -711,7 +713,7 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
     const int l = lb + i;
     if (!SPIN) {
         if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1))
-            P::atomic_add(out + 2 * (base + l) + c, tot, __ldg(sc + l));
+            P::atomic_add(out + 2 * (base + l) + c, tot, __ldg(sc + l) * wm);
     } else {
         // lanes hold U.re, U.im, V.re, V.im of degree l at c = 0..3; the G/C
         // split is linear, so each warp adds its share directly:
@@ -726,7 +728,7 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
             else if (c == 1) { val = P::ascale(P::aadd(tot, P::ascale(other, -sgs)), -h); dst = 2 * (base + l) + 1; }
             else if (c == 2) { val = P::ascale(P::aadd(other, P::ascale(tot, -sgs)), h); dst = 2 * (nalm + base + l) + 1; }
             else { val = P::ascale(P::aadd(other, P::ascale(tot, sgs)), -h); dst = 2 * (nalm + base + l); }
-            if (!(m == 0 && (c == 1 || c == 2))) P::atomic_add(out + dst, val, __ldg(sc + l));
+            if (!(m == 0 && (c == 1 || c == 2))) P::atomic_add(out + dst, val, __ldg(sc + l) * wm);
         }
     }
 }
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  const double *__restrict__ scale, RingTab rt,
                                                  typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
-                                                 int ntheta, int nnorth, int64_t nalm, int m_begin)
+                                                 int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos)
 {
     using A = typename P::A;
     using R = typename P::R;
@@ -773,6 +775,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     const Sg sgs = (s & 1) ? Sg(-1) : Sg(1);
     R *out = reinterpret_cast<R *>(alm);
     const int lf = l0 + 1;
+    const double wm = m > 0 ? wpos : 1.0;
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
         in.add_rt(st, true, p0);  // l0 = lf - 1
-        flush<P, SPIN, NCOMP>(p0, out, sc, base, nalm, m, l0, lmax, sgs);
+        flush<P, SPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs);
     }
     int l = lf;
     A part[NV];
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
         for (int i = 0; i < NV; ++i) part[i] = P::azero();
         if (reg == 0) adj_block<P, RPT, SPIN, 0>(st, in, part, reca, rect, l);
         else adj_block<P, RPT, SPIN, 2>(st, in, part, reca, rect, l);
-        flush<P, SPIN, NV>(part, out, sc, base, nalm, m, l, lmax, sgs);
+        flush<P, SPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
     }
     if (l <= lmax) {  // tail: fewer than kBlk degrees, general path
 #pragma unroll
@@ -810,7 +813,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                 in.add_rt(st, (j & 1) != 0, part + j * NCOMP);
             }
         }
-        flush<P, SPIN, NV>(part, out, sc, base, nalm, m, l, lmax, sgs);
+        flush<P, SPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
     }
 }
 
@@ -868,7 +871,8 @@ __global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, flo
 }
 
 // Forward coefficients of one call: spin 0 c_l a_lm; spin s c_l (G + iC) and
-// c_l (-1)^s (conj G + i conj C) (m = 0: imaginary parts of a, G, C dropped);
+// c_l (-1)^s (conj G + i conj C) (m = 0: imaginary parts of a, G, C dropped),
+// all multiplied by wpos for m > 0;
 // zero for l < l0.  Entries of orders m < m_split are written as OUT_LO, the
 // others as OUT_HI: float2 (FP32 plans), double2 (FP64 plans, native FP64
 // orders) or float4 df32 (FP64 plans, df32 orders).
@@ -889,15 +893,16 @@ template <> __device__ __forceinline__ void put_coef<float4>(void *out, int64_t 
 
 template <typename Tin, typename OUT_LO, typename OUT_HI>
 __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restrict__ scale, void *__restrict__ out,
-                            int lmax, int spin, int64_t nalm, int m_split)
+                            int lmax, int spin, int64_t nalm, int m_split, double wpos)
 {
     const int m = blockIdx.y;
     const int64_t base = alm_base(lmax, m);
+    const double wm = m > 0 ? wpos : 1.0;
     const double sgs = (spin & 1) ? -1.0 : 1.0;
     const bool hi = m >= m_split;
     for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
         const int64_t i = base + l;
-        const double c = scale[i];
+        const double c = scale[i] * wm;
         const Tin gv = alm[i];
         const double gr = gv.x, gi = m == 0 ? 0.0 : (double)gv.y;
         if (!spin) {
@@ -928,14 +933,14 @@ cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef
 
 template <class P, int RPT, bool SPIN>
 cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                       void *alm, int m_begin, int m_end, cudaStream_t st)
+                       void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
     k_leg_adj<P, RPT, SPIN><<<grid, block, 0, st>>>((const typename P::C *)ring, ta, tt, p.lognorm, p.scale, p.rings,
                                                     (typename P::C *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
-                                                    p.nalm, m_begin);
+                                                    p.nalm, m_begin, wpos);
     return cudaGetLastError();
 }
 
@@ -949,10 +954,10 @@ cudaError_t fwd_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, c
 
 template <class P, bool SPIN>
 cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                    void *alm, int m_begin, int m_end, cudaStream_t st)
+                    void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
-    if (sh.rpt == 1) return adj_launch<P, 1, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
-    return adj_launch<P, 2, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
+    if (sh.rpt == 1) return adj_launch<P, 1, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    return adj_launch<P, 2, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
 }
 
 template <class P>
@@ -965,10 +970,10 @@ cudaError_t fwd_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, 
 
 template <class P>
 cudaError_t adj_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                     void *alm, int m_begin, int m_end, cudaStream_t st)
+                     void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
-    return p.spin ? adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st)
-                  : adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st);
+    return p.spin ? adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos)
+                  : adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
 }
 
 // Kernel entry of one (arithmetic, spin, rings-per-thread, direction) variant.
@@ -1041,7 +1046,7 @@ int legendre_rpt_dd(int spin, bool adjoint) { return (spin || adjoint) ? 1 : 2; 
 
 bool legendre_rpt_supported(int, int, bool, int rpt) { return rpt == 1 || rpt == 2; }
 
-cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st)
+cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st, double wpos)
 {
     // entries with l < spin / columns without rings are never written by the
     // kernel: start from zero
@@ -1051,25 +1056,26 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     const dim3 g(4, p.mmax + 1);
     if (p.prec == LENS_FP32) {
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef, p.lmax, p.spin,
-                                                               p.nalm, p.mmax + 1);
+                                                               p.nalm, p.mmax + 1, wpos);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return fwd_spin<PolDF>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
     }
     k_coef_prep<double2, double2, float4><<<g, 256, 0, st>>>((const double2 *)alm, p.scale, p.coef, p.lmax, p.spin,
-                                                             p.nalm, p.m_df);
+                                                             p.nalm, p.m_df, wpos);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fwd_spin<PolF64>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.m_df, st)) != cudaSuccess) return e;
     return fwd_spin<PolDD>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
 }
 
-cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st)
+cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st, double wpos)
 {
     const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * (p.spin ? 2 : 1);
     cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);  // the kernels add warp sums atomically
     if (e != cudaSuccess) return e;
-    if (p.prec == LENS_FP32) return adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st);
-    if ((e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st)) != cudaSuccess) return e;
-    return adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st);
+    if (p.prec == LENS_FP32)
+        return adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos);
+    if ((e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos)) != cudaSuccess) return e;
+    return adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos);
 }
 
 }  // namespace gsl

@@ -384,6 +384,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if ((e = B.alloc((void **)&p->cell, sizeof(uint32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc cell");
         if ((e = B.alloc(&p->frac, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc frac");
         if ((e = B.alloc((void **)&p->perm, sizeof(int32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc perm");
+        p->ntile_c = (p->N2 + kTileC - 1) / kTileC;
+        p->ntiles = (p->R + kTileR - 1) / kTileR * p->ntile_c;
+        if ((e = B.alloc((void **)&p->tile_start, sizeof(uint32_t) * ((size_t)p->ntiles + 1), false)) != cudaSuccess)
+            return bailc(e, "alloc tile table");
         if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
         // FP64 plans keep the 2W kernel weights of every point (GB300's FP64 pipe makes
         // evaluating exp/sqrt per tap far dearer than reading 16 W bytes per point)
@@ -566,10 +570,10 @@ struct DeviceGuard {
     }
 };
 
-int forward_one(const Plan &p, const void *alm, void *map, cudaStream_t st)
+int forward_one(const Plan &p, const void *alm, void *map, cudaStream_t st, double wpos = 1.0)
 {
     cudaError_t e;
-    if ((e = staged(p, 0, st, [&] { return launch_legendre_fwd(p, alm, p.ring, st); })) != cudaSuccess)
+    if ((e = staged(p, 0, st, [&] { return launch_legendre_fwd(p, alm, p.ring, st, wpos); })) != cudaSuccess)
         return cuda_fail(e, "legendre synthesis");
     if ((e = staged(p, 1, st, [&] { return launch_theta_fwd(p, p.ring, p.X, st); })) != cudaSuccess)
         return cuda_fail(e, "theta transform");
@@ -580,7 +584,7 @@ int forward_one(const Plan &p, const void *alm, void *map, cudaStream_t st)
     return LENS_OK;
 }
 
-int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st)
+int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st, double wpos = 1.0)
 {
     cudaError_t e;
     if ((e = staged(p, 4, st, [&] { return launch_spread(p, map, p.grid, st); })) != cudaSuccess)
@@ -589,7 +593,7 @@ int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st)
         return cuda_fail(e, "phi transform");
     if ((e = staged(p, 6, st, [&] { return launch_theta_adj(p, p.X, p.ring, st); })) != cudaSuccess)
         return cuda_fail(e, "theta transform");
-    if ((e = staged(p, 7, st, [&] { return launch_legendre_adj(p, p.ring, alm, st); })) != cudaSuccess)
+    if ((e = staged(p, 7, st, [&] { return launch_legendre_adj(p, p.ring, alm, st, wpos); })) != cudaSuccess)
         return cuda_fail(e, "adjoint legendre");
     return LENS_OK;
 }
@@ -601,32 +605,45 @@ size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.
 
 extern "C" {
 
-int lens_synthesis(lens_plan pl, const void *alm_d, void *map_d, int nmaps, void *stream)
+static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, void *stream, bool fwd, double wpos)
 {
     if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
     const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    const void *alm_d = fwd ? in_d : out_d, *map_d = fwd ? out_d : in_d;
     if (nmaps > 0 && (!alm_d || (!map_d && p.npts > 0))) return fail(LENS_ERR_INVALID, "NULL buffer");
     DeviceGuard g(p.device);
     cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    const size_t ib = fwd ? alm_bytes(p) : map_bytes(p), ob = fwd ? map_bytes(p) : alm_bytes(p);
     for (int i = 0; i < nmaps; ++i) {
-        int r = forward_one(p, (const char *)alm_d + i * alm_bytes(p), (char *)map_d + i * map_bytes(p), st);
+        const void *in = (const char *)in_d + i * ib;
+        void *out = (char *)out_d + i * ob;
+        int r = fwd ? forward_one(p, in, out, st, wpos) : adjoint_one(p, in, out, st, wpos);
         if (r != LENS_OK) return r;
     }
     return LENS_OK;
 }
 
+int lens_synthesis(lens_plan pl, const void *alm_d, void *map_d, int nmaps, void *stream)
+{
+    return device_call(pl, alm_d, map_d, nmaps, stream, true, 1.0);
+}
+
 int lens_adjoint(lens_plan pl, const void *map_d, void *alm_d, int nmaps, void *stream)
 {
-    if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
-    const Plan &p = *reinterpret_cast<const Plan *>(pl);
-    if (nmaps > 0 && (!alm_d || (!map_d && p.npts > 0))) return fail(LENS_ERR_INVALID, "NULL buffer");
-    DeviceGuard g(p.device);
-    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
-    for (int i = 0; i < nmaps; ++i) {
-        int r = adjoint_one(p, (const char *)map_d + i * map_bytes(p), (char *)alm_d + i * alm_bytes(p), st);
-        if (r != LENS_OK) return r;
-    }
-    return LENS_OK;
+    return device_call(pl, map_d, alm_d, nmaps, stream, false, 1.0);
+}
+
+// Gradients: lens_synthesis counts every m > 0 coefficient for +m and -m, so
+// with respect to the weighted a_lm product the adjoint is exact and the
+// gradients carry the weight 2 (or 1/2) on m > 0.
+int lens_synthesis_vjp(lens_plan pl, const void *grad_map_d, void *grad_alm_d, int nmaps, void *stream)
+{
+    return device_call(pl, grad_map_d, grad_alm_d, nmaps, stream, false, 2.0);
+}
+
+int lens_adjoint_vjp(lens_plan pl, const void *grad_alm_d, void *grad_map_d, int nmaps, void *stream)
+{
+    return device_call(pl, grad_alm_d, grad_map_d, nmaps, stream, true, 0.5);
 }
 
 static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, void *stream, bool fwd)
