@@ -109,14 +109,17 @@ def synthesis(lmax: int, mmax: int, spin: int, theta, phi, alm, chi=None) -> np.
     """Forward lensing operator by direct summation.
 
     alm: [ncomp, nalm] complex (spin 0: [1, nalm] or [nalm]); returns [ncomp, npts]
-    (spin 0: T; spin s: Q, U).
+    (spin 0: T; spin s: Q, U).  Imaginary parts of the m = 0 entries are ignored.
     """
     theta, phi = _f64(theta), _f64(phi)
     chi = None if chi is None else _f64(chi)
     ncomp = 1 if spin == 0 else 2
-    alm = _c128(alm).reshape(ncomp, -1)
+    alm = _c128(alm).reshape(ncomp, -1).copy()
     if alm.shape[1] != nalm(lmax, mmax):
         raise ValueError("alm has the wrong size")
+    # real fields (a_{l,-m} = (-1)^m conj a_lm) have real m = 0 coefficients; an
+    # imaginary part there is outside the domain and ignored, as by the library
+    alm[:, :lmax + 1] = alm[:, :lmax + 1].real
     out = np.zeros((ncomp, theta.size))
     rc = _load().oracle_synthesis(lmax, mmax, spin, theta.size, _ptr(theta), _ptr(phi), _ptr(chi),
                                   _ptr(alm), _ptr(out))
@@ -164,3 +167,103 @@ def deflected_points(theta, phi, phi_lm, lmax_phi: int):
     alm = np.stack([g, np.zeros_like(g)])
     a = synthesis(lmax_phi, lmax_phi, 1, theta, phi, alm)
     return pointing(theta, phi, a[0], a[1])
+
+
+# ---------------------------------------------------------------- differentiation
+# Gradient of a real loss L(d) of the lensed map d = A(phi) x with respect to
+# the lensing potential phi_LM.  The paper gives the forward model (Sect. 2
+# Eqs. "forward" / "forwardpol", Eq. "deflect", the pointing formula of
+# Sect. 3 and chi of Fig. 1) but not its derivative; the chain rule below is
+# written out step by step and pinned by central finite differences of that
+# forward model (tests/test_oracle_pins.py).
+#
+# With P = Q + iU = e^{i s chi} sf(n') (sf = -sum (G + iC) sY, or sum a Y for
+# s = 0) and a tangent perturbation dalpha of the deflection at n, in the
+# frame of n parallel-transported along the geodesic:
+#   dP = -1/2 [conj(v) A + v B] + i s c dalpha_perp P,
+#   v = J dalpha,  J = ah ah^T + (sin a / a)(1 - ah ah^T)   (exponential map),
+#   A = e^{i(s+1)chi} (eth sf)(n'),  B = e^{i(s-1)chi} (ethbar sf)(n')
+#   (spin 0: B = conj(A)),  c = (1 - cos a) / a  (holonomy of the transport),
+# a = |alpha|, ah = alpha / a, dalpha_perp the component of dalpha along i ah.
+# Hence, for g = dL/dQ + i dL/dU (real dL/dd for s = 0):
+#   dL/dalpha = J Y + K i ah,  Y = -1/2 [conj(g) A + g conj(B)],
+#   K = -s c Im(conj(g) P),
+# and dL/dphi_LM = sqrt(L(L+1)) w_m [adjoint_1(dL/dalpha)]_G at the undeflected
+# points (w_0 = 1, w_m = 2: real-field coefficients appear for +m and -m).
+
+def _ell(lmax: int) -> np.ndarray:
+    return np.concatenate([np.arange(m, lmax + 1) for m in range(lmax + 1)]).astype(np.float64)
+
+
+def _mweight(lmax: int) -> np.ndarray:
+    return np.concatenate([np.full(lmax + 1 - m, 1.0 if m == 0 else 2.0) for m in range(lmax + 1)])
+
+
+def eth_coeffs(lmax: int, spin: int, alm, lower: bool = False) -> np.ndarray:
+    """Coefficients [G, C] of eth sf (spin s+1) or, lower=True, ethbar sf (spin s-1 >= 1).
+
+    eth sY_lm = sqrt((l-s)(l+s+1)) s+1Y_lm, ethbar sY_lm = -sqrt((l+s)(l-s+1)) s-1Y_lm, and
+    sf = -sum (G + iC) sY (s > 0) or sum a Y (s = 0).
+    """
+    ell = _ell(lmax)
+    alm = _c128(alm).reshape(1 if spin == 0 else 2, -1)
+    if spin == 0:
+        if lower:
+            raise ValueError("ethbar of a spin-0 field has spin -1")
+        return np.stack([-np.sqrt(ell * (ell + 1.0)) * alm[0], np.zeros_like(alm[0])])
+    if lower:
+        if spin < 2:
+            raise ValueError("ethbar of a spin-1 field has spin 0")
+        f = -np.sqrt(np.maximum((ell + spin) * (ell - spin + 1.0), 0.0))
+    else:
+        f = np.sqrt(np.maximum((ell - spin) * (ell + spin + 1.0), 0.0))
+    return alm * f[None, :]
+
+
+def lensed_forward(lmax: int, spin: int, theta0, phi0, phi_lm, lmax_phi: int, x) -> np.ndarray:
+    """d = A(phi) x: deflect the points (Eq. "deflect", pointing) and synthesise x there."""
+    th, ph, chi = deflected_points(theta0, phi0, phi_lm, lmax_phi)
+    return synthesis(lmax, lmax, spin, th, ph, x, chi if spin else None)
+
+
+def deflection_vjp(spin: int, alpha_theta, alpha_phi, g, p, a_up, b_down=None):
+    """dL/dalpha (complex, theta + i phi) per point from the formula above."""
+    at, ap = _f64(alpha_theta), _f64(alpha_phi)
+    a = np.hypot(at, ap)
+    safe = np.where(a > 0, a, 1.0)
+    ah = np.where(a > 0, (at + 1j * ap) / safe, 1.0 + 0j)
+    k = np.where(a > 0, np.sin(a) / safe, 1.0)
+    c = np.where(a > 0, 2.0 * np.sin(0.5 * a) ** 2 / safe, 0.0)
+    A = a_up[0] + 1j * a_up[1]
+    if spin == 0:
+        gc = _f64(g).reshape(-1) + 0j
+        B = np.conj(A)
+        P = _f64(p).reshape(-1) + 0j
+    else:
+        gc = g[0] + 1j * g[1]
+        B = b_down[0] + 1j * b_down[1]
+        P = p[0] + 1j * p[1]
+    Y = -0.5 * (np.conj(gc) * A + gc * np.conj(B))
+    par = (np.conj(ah) * Y).real
+    JY = par * ah + k * (Y - par * ah)
+    K = -spin * c * (np.conj(gc) * P).imag
+    return JY + K * 1j * ah
+
+
+def phi_gradient(lmax: int, spin: int, theta0, phi0, phi_lm, lmax_phi: int, x, g) -> np.ndarray:
+    """dL/dphi_LM (dL/dRe + i dL/dIm) for L = sum_i g_i . (A(phi) x)_i."""
+    theta0, phi0 = _f64(theta0), _f64(phi0)
+    ellp = _ell(lmax_phi)
+    gphi = _c128(phi_lm) * np.sqrt(ellp * (ellp + 1.0))
+    alpha = synthesis(lmax_phi, lmax_phi, 1, theta0, phi0, np.stack([gphi, np.zeros_like(gphi)]))
+    th, ph, chi = pointing(theta0, phi0, alpha[0], alpha[1])
+    x = _c128(x).reshape(1 if spin == 0 else 2, -1)
+    p = synthesis(lmax, lmax, spin, th, ph, x, chi if spin else None)
+    a_up = synthesis(lmax, lmax, spin + 1, th, ph, eth_coeffs(lmax, spin, x), chi)
+    b_down = None
+    if spin >= 2:
+        b_down = synthesis(lmax, lmax, spin - 1, th, ph, eth_coeffs(lmax, spin, x, lower=True), chi)
+    g = _f64(g).reshape(p.shape)
+    da = deflection_vjp(spin, alpha[0], alpha[1], g, p, a_up, b_down)
+    adj = adjoint(lmax_phi, lmax_phi, 1, theta0, phi0, np.stack([da.real, da.imag]))
+    return np.sqrt(ellp * (ellp + 1.0)) * _mweight(lmax_phi) * adj[0]

@@ -365,3 +365,64 @@ def test_pointing_special_cases():
     # along the equator: stays on it, no rotation
     t2, p2, chi = O.pointing(np.array([math.pi / 2]), np.array([1.0]), np.zeros(1), np.array([0.2]))
     assert abs(t2[0] - math.pi / 2) < 1e-14 and abs(p2[0] - 1.2) < 1e-14 and abs(chi[0]) < 1e-14
+
+
+def _phi_scaled(L, seed, rms):
+    """phi_LM with rms deflection `rms` radians (large, so that the exponential-map
+    Jacobian and the transport holonomy contribute visibly)."""
+    phi = W.draw_alm(W.phi_cl(L), L, seed)
+    ell = W.alm_l_of_index(L).astype(float)
+    w = np.where(W.alm_m_of_index(L) > 0, 2.0, 1.0)
+    return phi * rms / np.sqrt(np.sum(w * ell * (ell + 1) * np.abs(phi) ** 2) / (4 * math.pi))
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_phi_gradient_matches_finite_differences(spin):
+    """d/dphi of L = sum g . A(phi) x (Eq. "deflect", pointing, Eq. "forward"/"forwardpol"):
+    the oracle's chain rule against Richardson-extrapolated central differences of the
+    oracle's own forward model, 0.3 rad rms deflection, complex directions (including
+    imaginary parts at m = 0, which must get zero gradient)."""
+    L = 12
+    th0, ph0, _ = W.random_points(300, 4)
+    phi = _phi_scaled(L, 9, 0.3)
+    nc = 1 if spin == 0 else 2
+    x = np.stack([W.draw_alm(W.cmb_cl(L, 8.0), L, 30 + k, spin=spin) for k in range(nc)])
+    g = np.random.default_rng(1).standard_normal((nc, th0.size))
+    grad = O.phi_gradient(L, spin, th0, ph0, phi, L, x, g)
+    assert np.all(grad[W.alm_m_of_index(L) == 0].imag == 0)
+
+    def loss(p):
+        return float(np.sum(g * O.lensed_forward(L, spin, th0, ph0, p, L, x)))
+
+    for k in range(3):
+        rng = np.random.default_rng(100 + k)
+        d = rng.standard_normal(phi.size) + 1j * rng.standard_normal(phi.size)
+        t = 1e-5
+        fd1 = (loss(phi + t * d) - loss(phi - t * d)) / (2 * t)
+        fd2 = (loss(phi + 0.5 * t * d) - loss(phi - 0.5 * t * d)) / t
+        fd = (4 * fd2 - fd1) / 3
+        an = float(np.sum(grad.real * d.real + grad.imag * d.imag))
+        assert abs(an - fd) <= 1e-8 * abs(fd), (k, an, fd)
+
+
+def test_eth_coefficients_against_derivatives():
+    """eth / ethbar coefficient maps of a spin-2 field: with eth = -(D_theta + i D_phi)
+    and ethbar = -(D_theta - i D_phi) (covariant derivatives; D_theta is the plain
+    theta derivative along a meridian), the spin-3 and spin-1 syntheses of
+    eth_coeffs must give d_theta P = -(eth P + ethbar P) / 2, checked against a
+    fourth-order central difference in theta."""
+    L = 10
+    th = np.array([0.4, 1.1, 1.9, 2.6])
+    ph = np.array([0.2, 2.0, 4.0, 5.5])
+    x = np.stack([W.draw_alm(W.cmb_cl(L, 6.0), L, 40 + k, spin=2) for k in range(2)])
+    up = O.synthesis(L, L, 3, th, ph, O.eth_coeffs(L, 2, x))
+    dn = O.synthesis(L, L, 1, th, ph, O.eth_coeffs(L, 2, x, lower=True))
+    h = 1e-5
+
+    def P(t):
+        q = O.synthesis(L, L, 2, t, ph, x)
+        return q[0] + 1j * q[1]
+
+    dth = (8 * (P(th + h) - P(th - h)) - (P(th + 2 * h) - P(th - 2 * h))) / (12 * h)
+    got = -0.5 * ((up[0] + 1j * up[1]) + (dn[0] + 1j * dn[1]))
+    assert np.max(np.abs(got - dth)) <= 1e-8 * np.max(np.abs(dth))
