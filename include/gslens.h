@@ -170,6 +170,59 @@ int lens_synthesis_vjp(lens_plan p, const void *grad_map_d, void *grad_alm_d, in
 int lens_adjoint_vjp(lens_plan p, const void *grad_alm_d, void *grad_map_d, int nmaps, void *stream);
 
 /*
+ * Deflection field (Sect. 3 Eq. "deflect"): alpha_theta + i alpha_phi =
+ * spin-1 forward operator of G_LM = sqrt(L(L+1)) phi_LM, C_LM = 0, i.e. the
+ * gradient of phi, at the plan's points.
+ *   defl      an FP64 spin-1 plan on the undeflected points (chi NULL).
+ *   phi_lm_d  device complex double [nalm] (real-field layout of a_lm).
+ *   alpha_d   device double [2][npoints]: alpha_theta then alpha_phi; feed
+ *             them to lens_pointing for theta', phi', chi.
+ * LENS_ERR_INVALID unless defl is FP64 spin 1.
+ */
+int lens_deflection(lens_plan defl, const void *phi_lm_d, double *alpha_d, void *stream);
+
+/*
+ * Coefficients of eth f (lower = 0) or ethbar f (lower = 1) of a spin-s field
+ * f, as a spin s+1 (s-1) field in the convention of Eq. "forwardpol",
+ * sf = -sum (G + iC) sY (spin 0: f = sum a Y), with eth sY_lm =
+ * sqrt((l-s)(l+s+1)) s+1Y_lm and ethbar sY_lm = -sqrt((l+s)(l-s+1)) s-1Y_lm
+ * (no counterpart in the paper; used for gradients at deflected points).
+ *   alm_in_d   device complex [ncomp][nalm(lmax, mmax)] (ncomp 1 for s = 0).
+ *   alm_out_d  device complex [2][nalm] (G', C').  prec: LENS_FP32 / LENS_FP64.
+ * ethbar needs s >= 2 (LENS_ERR_UNSUPPORTED otherwise).
+ */
+int lens_alm_eth(int lmax, int mmax, int spin, int lower, int prec, const void *alm_in_d, void *alm_out_d,
+                 void *stream);
+
+/*
+ * Gradient of a real loss L(d) of the lensed map d = A(phi) x with respect to
+ * the lensing potential phi_LM (no counterpart in the paper; the chain rule
+ * through Eq. "deflect", the pointing formula and chi).  Per point, with
+ * g = dL/dQ + i dL/dU (dL/dT for spin 0), P the lensed field, a = |alpha|:
+ *   dL/dalpha = J Y + K i alpha/a,  Y = -1/2 [conj(g) A + g conj(B)],
+ *   K = -s (1 - cos a)/a Im(conj(g) P),
+ * J the derivative of the exponential map, A and B the lensed syntheses of
+ * eth x and ethbar x (spin 0: B = conj A); then dL/dphi_LM =
+ * sqrt(L(L+1)) * w_m * (G part of the spin-1 adjoint of dL/dalpha), w_0 = 1,
+ * w_m = 2 (real-field coefficients).
+ *   lensed       plan of spin s (0 or >= 2) on the deflected points, with chi.
+ *   lensed_up    plan of spin s+1, same points, chi, band limit, precision.
+ *   lensed_down  plan of spin s-1 for s >= 2 (NULL for s = 0).
+ *   defl         FP64 spin-1 plan on the undeflected points, band limit of phi.
+ *   alpha_d      device double [2][npoints], the deflection the points came from.
+ *   x_alm_d      device complex [ncomp][nalm], lensed's precision.
+ *   map_d        lensed map A(phi) x, [ncomp][npoints], or NULL (recomputed).
+ *   grad_map_d   dL/dd, [ncomp][npoints], lensed's precision.
+ *   grad_phi_d   device complex double [nalm of defl] (written).
+ * Scratch comes from the stream-ordered allocator and is released before
+ * return (stream order).  LENS_ERR_INVALID if the plans do not match,
+ * LENS_ERR_UNSUPPORTED for spin 1.
+ */
+int lens_phi_gradient(lens_plan lensed, lens_plan lensed_up, lens_plan lensed_down, lens_plan defl,
+                      const double *alpha_d, const void *x_alm_d, const void *map_d, const void *grad_map_d,
+                      void *grad_phi_d, void *stream);
+
+/*
  * The same two operations on host buffers: the inputs are copied to the
  * device, the transform runs, the outputs are copied back; returns after the
  * stream has finished.  Pinned host memory gives full copy bandwidth.

@@ -23,7 +23,8 @@ import torch
 from . import _native
 from ._native import LensError, PlanInfo, PlanParams
 
-__all__ = ["LensPlan", "LensError", "synthesis", "adjoint", "pointing", "nalm", "lib_path"]
+__all__ = ["LensPlan", "LensingModel", "LensError", "synthesis", "adjoint", "lensed", "pointing", "nalm",
+           "lib_path"]
 
 _PREC = {"fp32": 0, "fp64": 1}
 
@@ -241,6 +242,115 @@ def synthesis(plan: LensPlan, alm: torch.Tensor) -> torch.Tensor:
 def adjoint(plan: LensPlan, m: torch.Tensor) -> torch.Tensor:
     """Differentiable adjoint lensing: plan.adjoint with backward = lens_adjoint_vjp."""
     return _Adjoint.apply(m, plan)
+
+
+class LensingModel:
+    """d = A(phi) x: lensing of a spin-s field x by a potential phi, with gradients.
+
+    The undeflected points (theta0, phi0) are fixed.  set_phi(phi_lm) computes
+    the deflection (Eq. "deflect", lens_deflection) and the deflected geometry
+    (lens_pointing) on the GPU and builds the lensed plan; forward(x),
+    grad_x(g) (lens_synthesis_vjp) and grad_phi(x, g) (lens_phi_gradient) run
+    on it.  The spin s+1 / s-1 plans that the phi gradient needs are built on
+    first use.  phi_lm: complex128 [nalm(lmax_phi)] on the device.
+    """
+
+    def __init__(self, lmax: int, theta0, phi0, spin: int = 0, lmax_phi: int | None = None,
+                 epsilon: float = 1e-5, precision: str = "fp32", epsilon_deflection: float = 1e-10,
+                 device=None, **plan_kw):
+        if spin == 1:
+            raise ValueError("spin-1 fields are not supported by the phi gradient")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.lmax, self.spin = int(lmax), int(spin)
+        self.lmax_phi = int(lmax if lmax_phi is None else lmax_phi)
+        self.epsilon, self.precision, self.plan_kw = float(epsilon), precision, plan_kw
+        self.theta0 = _dev_f64(theta0, self.device)
+        self.phi0 = _dev_f64(phi0, self.device)
+        self.npoints = int(self.theta0.numel())
+        self.defl = LensPlan(self.lmax_phi, self.theta0, self.phi0, spin=1, epsilon=epsilon_deflection,
+                             precision="fp64", device=self.device)
+        self.alpha = torch.empty(2, self.npoints, dtype=torch.float64, device=self.device)
+        self.phi_lm = None
+        self.lensed = self._up = self._down = None
+        self.geometry = None
+
+    def _plan(self, spin):
+        t2, p2, chi = self.geometry
+        return LensPlan(self.lmax, t2, p2, chi, spin=spin, epsilon=self.epsilon, precision=self.precision,
+                        device=self.device, **self.plan_kw)
+
+    def _close_lensed(self):
+        for pl in (self.lensed, self._up, self._down):
+            if pl is not None:
+                pl.close()
+        self.lensed = self._up = self._down = None
+
+    def set_phi(self, phi_lm: torch.Tensor, stream=None):
+        """Deflect the points by the gradient of phi and rebuild the lensed plan."""
+        phi_lm = phi_lm.detach().to(device=self.device, dtype=torch.complex128).contiguous()
+        if phi_lm.numel() != self.defl.nalm:
+            raise ValueError("phi_lm must have %d entries" % self.defl.nalm)
+        _native.check(_native.load().lens_deflection(self.defl.handle, phi_lm.data_ptr(), self.alpha.data_ptr(),
+                                                     _stream_handle(stream)))
+        self.geometry = pointing(self.theta0, self.phi0, self.alpha[0], self.alpha[1], stream=stream)
+        self._close_lensed()
+        self.lensed = self._plan(self.spin)
+        self.phi_lm = phi_lm.clone()
+
+    def forward(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        return self.lensed.synthesis(x, stream=stream)
+
+    def grad_x(self, grad_map: torch.Tensor, stream=None) -> torch.Tensor:
+        return self.lensed.synthesis_vjp(grad_map, stream=stream)
+
+    def grad_phi(self, x: torch.Tensor, grad_map: torch.Tensor, d: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+        """dL/dphi_LM (complex128 [nalm(lmax_phi)]) given dL/dd of d = A(phi) x."""
+        if self._up is None:
+            self._up = self._plan(self.spin + 1)
+            if self.spin >= 2:
+                self._down = self._plan(self.spin - 1)
+        x, _ = self.lensed._alm_arg(x)
+        g, _ = self.lensed._map_arg(grad_map)
+        if d is not None:
+            d, _ = self.lensed._map_arg(d)
+        out = torch.empty(self.defl.nalm, dtype=torch.complex128, device=self.device)
+        _native.check(_native.load().lens_phi_gradient(
+            self.lensed.handle, self._up.handle, self._down.handle if self._down is not None else None,
+            self.defl.handle, self.alpha.data_ptr(), x.data_ptr(), d.data_ptr() if d is not None else None,
+            g.data_ptr(), out.data_ptr(), _stream_handle(stream)))
+        return out
+
+    def close(self):
+        self._close_lensed()
+        self.defl.close()
+
+
+class _Lensed(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, phi_lm, model):
+        if model.phi_lm is None or not torch.equal(phi_lm.detach(), model.phi_lm):
+            model.set_phi(phi_lm)
+        d = model.forward(x.detach())
+        ctx.model = model
+        ctx.save_for_backward(x.detach(), phi_lm.detach(), d)
+        return d
+
+    @staticmethod
+    def backward(ctx, grad_map):
+        x, phi_lm, d = ctx.saved_tensors
+        model = ctx.model
+        if not torch.equal(phi_lm, model.phi_lm):
+            model.set_phi(phi_lm)
+            d = None
+        gx = model.grad_x(grad_map) if ctx.needs_input_grad[0] else None
+        gp = model.grad_phi(x, grad_map, d) if ctx.needs_input_grad[1] else None
+        return gx, gp, None
+
+
+def lensed(model: LensingModel, x: torch.Tensor, phi_lm: torch.Tensor) -> torch.Tensor:
+    """Differentiable d = A(phi) x in both x (lens_synthesis_vjp) and phi (lens_phi_gradient)."""
+    return _Lensed.apply(x, phi_lm, model)
 
 
 def pointing(theta: torch.Tensor, phi: torch.Tensor, alpha_theta: torch.Tensor, alpha_phi: torch.Tensor,

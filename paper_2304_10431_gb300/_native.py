@@ -23,6 +23,9 @@ EXPORTS = {
     "lens_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_deflection": (_i32, [_vp, _vp, _vp, _vp]),
+    "lens_alm_eth": (_i32, [_i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "lens_phi_gradient": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),

@@ -118,6 +118,13 @@ cudaError_t launch_pointing(int64_t n, const double *theta, const double *phi, c
                             const double *aph, double *theta_out, double *phi_out, double *chi_out,
                             cudaStream_t st);
 
+// One map through the whole forward (Legendre synthesis .. interpolation) or
+// adjoint chain on stream st, with the order weight wpos (1 for the
+// transforms; 2 / 0.5 for the gradient entry points).  Returns a lens_status
+// and records failures.
+int run_forward(const Plan &p, const void *alm, void *map, cudaStream_t st, double wpos);
+int run_adjoint(const Plan &p, const void *map, void *alm, cudaStream_t st, double wpos);
+
 // Records a failing status and message in the calling thread's error state
 // (lens_get_last_error / lens_last_error_message) and returns the status.
 int record_failure(int status, const char *msg);

@@ -603,6 +603,16 @@ size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.
 
 }  // namespace
 
+int gsl::run_forward(const Plan &p, const void *alm, void *map, cudaStream_t st, double wpos)
+{
+    return forward_one(p, alm, map, st, wpos);
+}
+
+int gsl::run_adjoint(const Plan &p, const void *map, void *alm, cudaStream_t st, double wpos)
+{
+    return adjoint_one(p, map, alm, st, wpos);
+}
+
 extern "C" {
 
 static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, void *stream, bool fwd, double wpos)
