@@ -223,6 +223,52 @@ int lens_phi_gradient(lens_plan lensed, lens_plan lensed_up, lens_plan lensed_do
                       void *grad_phi_d, void *stream);
 
 /*
+ * Batched execution (no counterpart in the paper): a list of transforms over
+ * any mix of plans, recorded once as a CUDA graph and replayed with one
+ * launch.  Items of one plan share its workspace and run in the order they
+ * were added, on one branch; plans are spread over up to nbranches concurrent
+ * branches, largest estimated cost first, so that small transforms run side by
+ * side.
+ *   lens_batch_create(&b, device)
+ *   lens_batch_add(b, plan, op, in_d, out_d, nmaps)   op 0: lens_synthesis
+ *       (in = a_lm, out = map), op 1: lens_adjoint (in = map, out = a_lm);
+ *       layouts as for those calls.  The pointers are recorded, not copied:
+ *       every launch reads and writes the same buffers.
+ *   lens_batch_instantiate(b, nbranches)  records the graph (1 <= nbranches
+ *       <= 64); no item may be added afterwards.
+ *   lens_batch_launch(b, stream)  one cudaGraphLaunch on stream.
+ *   lens_batch_info(b, &nitems, &nbranches, &max_branch_seconds)  the
+ *       balancing estimate (any pointer may be NULL).
+ *   lens_batch_destroy(b)  the plans stay owned by the caller and must
+ *       outlive every launch.
+ */
+typedef struct lens_batch_s *lens_batch;
+int lens_batch_create(lens_batch *out, int device);
+int lens_batch_add(lens_batch b, lens_plan p, int op, const void *in_d, void *out_d, int nmaps);
+int lens_batch_instantiate(lens_batch b, int nbranches);
+int lens_batch_launch(lens_batch b, void *stream);
+int lens_batch_info(lens_batch b, int *nitems, int *nbranches, double *max_branch_seconds);
+int lens_batch_destroy(lens_batch b);
+
+/*
+ * Autotuner (no counterpart in the paper, which picks its kernel parameters
+ * with a heuristic): builds candidate plans for the given points and times
+ * them on the GPU.  Candidates: oversampling sigma in {1.25, 1.5, 1.75, 2.0,
+ * 2.25, 2.5} (W follows from epsilon; candidates outside this build's size
+ * limits are skipped), then the Legendre rings per thread (forward, adjoint)
+ * in {1, 2}^2 at the best sigma.  Each candidate is timed as reps forward +
+ * adjoint pairs after one warm-up pair, with CUDA events on stream.
+ * Arguments as for lens_plan_create, plus
+ *   reps      timed pairs per candidate (>= 1),
+ *   best      receives the fastest parameters (pass to lens_plan_create_ex),
+ *   best_ms   milliseconds of one forward + adjoint pair with them (or NULL).
+ * Allocates one a_lm and one map buffer for the duration of the call.
+ */
+int lens_autotune(int lmax, int mmax, int spin, int64_t npoints, const double *theta_d, const double *phi_d,
+                  const double *chi_d, double epsilon, int prec, void *stream, int reps, lens_plan_params *best,
+                  double *best_ms);
+
+/*
  * The same two operations on host buffers: the inputs are copied to the
  * device, the transform runs, the outputs are copied back; returns after the
  * stream has finished.  Pinned host memory gives full copy bandwidth.

@@ -23,8 +23,8 @@ import torch
 from . import _native
 from ._native import LensError, PlanInfo, PlanParams
 
-__all__ = ["LensPlan", "LensingModel", "LensError", "synthesis", "adjoint", "lensed", "pointing", "nalm",
-           "lib_path"]
+__all__ = ["LensPlan", "LensingModel", "LensBatch", "LensError", "synthesis", "adjoint", "lensed", "autotune",
+           "pointing", "nalm", "lib_path"]
 
 _PREC = {"fp32": 0, "fp64": 1}
 
@@ -351,6 +351,84 @@ class _Lensed(torch.autograd.Function):
 def lensed(model: LensingModel, x: torch.Tensor, phi_lm: torch.Tensor) -> torch.Tensor:
     """Differentiable d = A(phi) x in both x (lens_synthesis_vjp) and phi (lens_phi_gradient)."""
     return _Lensed.apply(x, phi_lm, model)
+
+
+class LensBatch:
+    """Many transforms recorded once as a CUDA graph and replayed with one launch (lens_batch_*).
+
+    add(plan, "synthesis" | "adjoint", inp, out) records an item (the tensors are kept
+    alive and reused by every launch); instantiate(nbranches) captures the graph; launch()
+    replays it on the current stream.
+    """
+
+    def __init__(self, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _native.check(_native.load().lens_batch_create(ctypes.byref(h), self.device.index or 0))
+        self._h = h
+        self._keep = []
+
+    def add(self, plan: LensPlan, op: str, inp: torch.Tensor, out: torch.Tensor):
+        if op == "synthesis":
+            inp, nmaps = plan._alm_arg(inp)
+            out_ok, _ = plan._map_arg(out)
+            code = 0
+        elif op == "adjoint":
+            inp, nmaps = plan._map_arg(inp)
+            out_ok, _ = plan._alm_arg(out)
+            code = 1
+        else:
+            raise ValueError("op must be 'synthesis' or 'adjoint'")
+        if out_ok.data_ptr() != out.data_ptr():
+            raise ValueError("out must be contiguous")
+        self._keep += [plan, inp, out]
+        _native.check(_native.load().lens_batch_add(self._h, plan.handle, code, inp.data_ptr(), out.data_ptr(),
+                                                    nmaps))
+
+    def instantiate(self, nbranches: int = 8):
+        _native.check(_native.load().lens_batch_instantiate(self._h, int(nbranches)))
+
+    def launch(self, stream=None):
+        _native.check(_native.load().lens_batch_launch(self._h, _stream_handle(stream)))
+
+    def info(self) -> dict:
+        n, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _native.check(_native.load().lens_batch_info(self._h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(c)))
+        return {"items": n.value, "branches": b.value, "max_branch_seconds": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _native.load().lens_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(lmax: int, theta, phi, chi=None, spin: int = 0, mmax: int | None = None, epsilon: float = 1e-5,
+             precision: str = "fp32", reps: int = 2, device=None, stream=None) -> dict:
+    """Measured plan parameters for these points (lens_autotune): LensPlan keyword
+    arguments (sigma, legendre_rpt) plus "ms", one forward + adjoint pair."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        th, ph = _dev_f64(theta, dev), _dev_f64(phi, dev)
+        ch = _dev_f64(chi, dev) if (chi is not None and spin) else None
+        best = PlanParams()
+        ms = ctypes.c_double()
+        _native.check(_native.load().lens_autotune(int(lmax), int(lmax if mmax is None else mmax), int(spin),
+                                                   int(th.numel()), th.data_ptr() if th.numel() else None,
+                                                   ph.data_ptr() if ph.numel() else None,
+                                                   ch.data_ptr() if ch is not None else None, float(epsilon),
+                                                   _PREC[precision], _stream_handle(stream), int(reps),
+                                                   ctypes.byref(best), ctypes.byref(ms)))
+    out = {"sigma": best.sigma, "ms": ms.value}
+    if best.legendre_rpt_fwd or best.legendre_rpt_adj:
+        out["legendre_rpt"] = (best.legendre_rpt_fwd, best.legendre_rpt_adj)
+    return out
 
 
 def pointing(theta: torch.Tensor, phi: torch.Tensor, alpha_theta: torch.Tensor, alpha_phi: torch.Tensor,

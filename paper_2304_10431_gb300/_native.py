@@ -26,6 +26,13 @@ EXPORTS = {
     "lens_deflection": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_alm_eth": (_i32, [_i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
     "lens_phi_gradient": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "lens_batch_create": (_i32, [ctypes.POINTER(_vp), _i32]),
+    "lens_batch_add": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32]),
+    "lens_batch_instantiate": (_i32, [_vp, _i32]),
+    "lens_batch_launch": (_i32, [_vp, _vp]),
+    "lens_batch_info": (_i32, [_vp, _vp, _vp, _vp]),
+    "lens_batch_destroy": (_i32, [_vp]),
+    "lens_autotune": (_i32, [_i32, _i32, _i32, _i64, _vp, _vp, _vp, _f64, _i32, _vp, _i32, _vp, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),

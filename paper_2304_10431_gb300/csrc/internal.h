@@ -125,6 +125,14 @@ cudaError_t launch_pointing(int64_t n, const double *theta, const double *phi, c
 int run_forward(const Plan &p, const void *alm, void *map, cudaStream_t st, double wpos);
 int run_adjoint(const Plan &p, const void *map, void *alm, cudaStream_t st, double wpos);
 
+// Sets the stage-timer switch, returning its previous state (stream capture
+// runs with the timers off).
+bool profile_swap(bool on);
+
+// Bytes of one map's a_lm / point values for a plan.
+inline size_t plan_alm_bytes(const Plan &p) { return (size_t)p.nalm * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 8 : 16); }
+inline size_t plan_map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 4 : 8); }
+
 // Records a failing status and message in the calling thread's error state
 // (lens_get_last_error / lens_last_error_message) and returns the status.
 int record_failure(int status, const char *msg);

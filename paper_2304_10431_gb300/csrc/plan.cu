@@ -603,6 +603,13 @@ size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.
 
 }  // namespace
 
+bool gsl::profile_swap(bool on)
+{
+    const bool was = g_prof.on;
+    g_prof.on = on;
+    return was;
+}
+
 int gsl::run_forward(const Plan &p, const void *alm, void *map, cudaStream_t st, double wpos)
 {
     return forward_one(p, alm, map, st, wpos);

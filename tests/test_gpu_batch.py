@@ -1,0 +1,138 @@
+"""Batched execution and the autotuner.
+
+LensBatch records many transforms (mixed plans, spins, precisions and band
+limits) as one CUDA graph; a launch must give what the individual calls give.
+The batched-lensing workload: 64 independent spin-0 / spin-2 instances, lmax
+drawn from {256, 512, 1024, 2048, 3072}, HEALPix points of Nside = lmax / 2
+displaced by 2.5 arcmin, epsilon 1e-5 (FP32) or 1e-9 (FP64), seed = instance,
+with plan parameters from the autotuner.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2304_10431_gb300 import LensBatch, LensPlan, autotune
+from paper_2304_10431_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def _instance(k, lmax, spin, prec, eps, th, ph, chi, **kw):
+    plan = LensPlan(lmax, th, ph, chi if spin else None, spin=spin, epsilon=eps, precision=prec, device=DEV, **kw)
+    nc = plan.ncomp
+    a = np.stack([W.draw_alm(W.cmb_cl(lmax, 0.73 * lmax), lmax, 5000 + 10 * k + c, spin=spin) for c in range(nc)])
+    alm = torch.as_tensor(a, dtype=plan.complex_dtype, device=DEV)
+    rng = np.random.default_rng(6000 + k)
+    x = torch.as_tensor(rng.standard_normal((nc, plan.npoints)), dtype=plan.real_dtype, device=DEV)
+    return plan, alm, x, a
+
+
+def test_batch_matches_individual_calls():
+    items = []
+    for k, (lmax, spin, prec, eps, n) in enumerate([(64, 0, "fp32", 1e-5, 5000), (128, 2, "fp32", 1e-5, 20000),
+                                                    (256, 0, "fp64", 1e-9, 40000), (96, 2, "fp64", 1e-9, 12000),
+                                                    (200, 2, "fp32", 1e-5, 30000), (32, 0, "fp64", 1e-9, 3000)]):
+        th, ph, chi = W.random_points(n, 700 + k)
+        plan, alm, x, _ = _instance(k, lmax, spin, prec, eps, th, ph, chi)
+        items.append((plan, alm, x))
+    batch = LensBatch(device=DEV)
+    outs = []
+    for plan, alm, x in items:
+        m = torch.empty(plan.ncomp, plan.npoints, dtype=plan.real_dtype, device=DEV)
+        a = torch.empty(plan.ncomp, plan.nalm, dtype=plan.complex_dtype, device=DEV)
+        batch.add(plan, "synthesis", alm, m)
+        batch.add(plan, "adjoint", x, a)
+        outs.append((m, a))
+    batch.instantiate(nbranches=3)
+    assert batch.info()["items"] == 12 and batch.info()["branches"] == 3
+    for rep in range(2):  # replays reuse the recorded buffers
+        for m, a in outs:
+            m.fill_(float("nan"))
+            a.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        for (plan, alm, x), (m, a) in zip(items, outs):
+            tol = 1e-6 if plan.precision == "fp32" else 1e-13
+            assert rel(m, plan.synthesis(alm)) <= tol
+            assert rel(a, plan.adjoint(x)) <= tol
+    batch.close()
+    for plan, *_ in items:
+        plan.close()
+
+
+def test_autotune_returns_a_working_plan():
+    th, ph, chi = W.random_points(200000, 71)
+    best = autotune(256, th, ph, chi, spin=2, epsilon=1e-5, precision="fp32", reps=2, device=DEV)
+    assert best["ms"] > 0 and 1.2 <= best["sigma"] <= 2.5
+    kw = {k: v for k, v in best.items() if k != "ms"}
+    plan = LensPlan(256, th, ph, chi, spin=2, epsilon=1e-5, precision="fp32", device=DEV, **kw)
+    a = np.stack([W.draw_alm(W.cmb_cl(256, 180.0), 256, 80 + c, spin=2) for c in range(2)])
+    s = np.arange(0, th.size, 997)
+    got = plan.synthesis(torch.as_tensor(a, dtype=torch.complex64, device=DEV))[:, torch.as_tensor(s, device=DEV)]
+    ref = O.synthesis(256, 256, 2, th[s], ph[s], a, chi[s])
+    assert np.linalg.norm(got.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    plan.close()
+
+
+def test_batched_lensing_64_instances():
+    rng = np.random.default_rng(2024)
+    lmaxes = rng.choice([256, 512, 1024, 2048, 3072], size=64)
+    spins = rng.choice([0, 2], size=64)
+    precs = rng.choice(["fp32", "fp64"], size=64)
+    tuned = {}
+    geoms = {}
+    items = []
+    for k in range(64):
+        lmax, spin, prec = int(lmaxes[k]), int(spins[k]), str(precs[k])
+        eps = 1e-5 if prec == "fp32" else 1e-9
+        th0, ph0 = W.healpix_centres(lmax // 2)
+        th, ph, chi = W.displaced_points(th0, ph0, 2.5, seed=k)
+        key = (lmax, spin, prec)
+        if key not in tuned:  # one autotuner run per (lmax, spin, precision) class
+            best = autotune(lmax, th, ph, chi, spin=spin, epsilon=eps, precision=prec, reps=1, device=DEV)
+            tuned[key] = {k2: v for k2, v in best.items() if k2 != "ms"}
+        plan, alm, x, a = _instance(k, lmax, spin, prec, eps, th, ph, chi, **tuned[key])
+        geoms[k] = (th, ph, chi, a)
+        items.append((plan, alm, x))
+    batch = LensBatch(device=DEV)
+    outs = []
+    for plan, alm, x in items:
+        m = torch.empty(plan.ncomp, plan.npoints, dtype=plan.real_dtype, device=DEV)
+        a = torch.empty(plan.ncomp, plan.nalm, dtype=plan.complex_dtype, device=DEV)
+        batch.add(plan, "synthesis", alm, m)
+        batch.add(plan, "adjoint", x, a)
+        outs.append((m, a))
+    batch.instantiate(nbranches=8)
+    batch.launch()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.launch()
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t0
+    npts = sum(p.npoints for p, *_ in items)
+    print("64 instances, %d points: graph %.3f s (%.3g lensed points/s, forward + adjoint)"
+          % (npts, t_graph, 2 * npts / t_graph))
+    # every instance equals its individual call; two small ones also against the oracle
+    for k, ((plan, alm, x), (m, a)) in enumerate(zip(items, outs)):
+        tol = 1e-6 if plan.precision == "fp32" else 1e-13
+        assert rel(m, plan.synthesis(alm)) <= tol, k
+        assert rel(a, plan.adjoint(x)) <= tol, k
+    small = [k for k in range(64) if items[k][0].lmax == 256][:2]
+    for k in small:
+        plan, alm, x = items[k]
+        th, ph, chi, a = geoms[k]
+        s = np.arange(0, th.size, max(1, th.size // 200))
+        got = outs[k][0][:, torch.as_tensor(s, device=DEV)].cpu().numpy()
+        ref = O.synthesis(plan.lmax, plan.lmax, plan.spin, th[s], ph[s], a, chi[s] if plan.spin else None)
+        assert np.linalg.norm(got - ref) <= plan.epsilon * np.linalg.norm(ref)
+    batch.close()
+    for plan, *_ in items:
+        plan.close()
