@@ -53,7 +53,7 @@ EXPORTS = {
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("W", ctypes.c_int), ("beta", ctypes.c_double),
                 ("ntheta", ctypes.c_int), ("legendre_rpt_fwd", ctypes.c_int), ("legendre_rpt_adj", ctypes.c_int),
-                ("legendre_df32_mmin", ctypes.c_int)]
+                ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):

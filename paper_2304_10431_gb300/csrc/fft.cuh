@@ -10,12 +10,60 @@
 // form y_k = x_0 + sum_q (x_q + x_{p-q}) cos(2 pi qk/p) -+ i (x_q - x_{p-q}) sin(2 pi qk/p).
 //
 // DIR = -1: forward, sum x_n e^{-2 pi i nk/N};  DIR = +1: inverse (unnormalised).
+//
+// Vectors longer than one CTA's shared memory are split over a cluster of
+// two CTAs (Blackwell distributed shared memory): elements [0, chunk) live in
+// rank 0's shared memory and [chunk, N) in rank 1's, the butterflies of both
+// CTAs address either half through the cluster's shared window, and the
+// stage barrier is a cluster barrier.  Team<CL> and Buf<C, CL> hide the
+// difference; CL = 1 is the plain single-CTA path.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "internal.h"
 
 namespace gsl {
+
+// The threads that share one vector: one CTA (CL = 1) or a cluster of two.
+template <int CL> struct Team;
+template <> struct Team<1> {
+    int tid, nthr;
+    __device__ Team() : tid(threadIdx.x), nthr(blockDim.x) {}
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int vec() const { return blockIdx.x; }
+};
+template <> struct Team<2> {
+    int tid, nthr;
+    __device__ Team()
+    {
+        const int rank = (int)cooperative_groups::this_cluster().block_rank();
+        tid = rank * blockDim.x + threadIdx.x;
+        nthr = 2 * blockDim.x;
+    }
+    __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+    __device__ __forceinline__ int vec() const { return blockIdx.x >> 1; }
+};
+
+// Element access of the vector: a shared-memory array, or two halves.
+template <typename C, int CL> struct Buf;
+template <typename C> struct Buf<C, 1> {
+    C *p;
+    __device__ explicit Buf(C *local) : p(local) {}
+    __device__ __forceinline__ C &operator[](int i) const { return p[i]; }
+};
+template <typename C> struct Buf<C, 2> {
+    C *p0, *p1;
+    int chunk;
+    __device__ Buf(C *local, int chunk_) : chunk(chunk_)
+    {
+        auto cl = cooperative_groups::this_cluster();
+        p0 = cl.map_shared_rank(local, 0);
+        p1 = cl.map_shared_rank(local, 1);
+    }
+    __device__ __forceinline__ C &operator[](int i) const { return i < chunk ? p0[i] : p1[i - chunk]; }
+};
 
 template <typename T> struct FftConst;
 #define GSL_FFT_CONSTS(T)                                                                                  \
@@ -160,13 +208,14 @@ template <int DIR, typename T> struct SmallDft<7, DIR, T> {
     static __device__ __forceinline__ void run(cplx<T> *x) { OddDft<7, DIR, T>::run(x); }
 };
 
-template <int R, int DIR, typename T>
-__device__ __forceinline__ void fft_stage(cplx<T> *buf, int N, int Lp, const cplx<T> *__restrict__ tw)
+template <int R, int DIR, typename T, class B>
+__device__ __forceinline__ void fft_stage(const B &buf, int N, int Lp, const cplx<T> *__restrict__ tw, int tid,
+                                          int nthr)
 {
     const int L = Lp * R;
     const int nb = N / R;
     const int tstep = N / L;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    for (int b = tid; b < nb; b += nthr) {
         const int g = b / Lp;
         const int j = b - g * Lp;
         const int base = g * L + j;
@@ -187,36 +236,43 @@ __device__ __forceinline__ void fft_stage(cplx<T> *buf, int N, int Lp, const cpl
 }
 
 // Full transform of buf (digit-reversed input -> natural output).  Ends with
-// a barrier.
-template <int DIR, typename T> __device__ void fft_smem(cplx<T> *buf, const FftDesc &d)
+// a barrier of the team.
+template <int DIR, typename T, int CL>
+__device__ void fft_smem(const Buf<cplx<T>, CL> &buf, const FftDesc &d, const Team<CL> &tm)
 {
     const cplx<T> *tw = (const cplx<T> *)d.tw;
     int Lp = 1;
     for (int st = 0; st < d.nst; ++st) {
         const int r = d.radix[st];
         switch (r) {
-        case 2: fft_stage<2, DIR, T>(buf, d.n, Lp, tw); break;
-        case 3: fft_stage<3, DIR, T>(buf, d.n, Lp, tw); break;
-        case 4: fft_stage<4, DIR, T>(buf, d.n, Lp, tw); break;
-        case 5: fft_stage<5, DIR, T>(buf, d.n, Lp, tw); break;
-        case 7: fft_stage<7, DIR, T>(buf, d.n, Lp, tw); break;
-        default: fft_stage<8, DIR, T>(buf, d.n, Lp, tw); break;
+        case 2: fft_stage<2, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 3: fft_stage<3, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 4: fft_stage<4, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 5: fft_stage<5, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 7: fft_stage<7, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        default: fft_stage<8, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         }
         Lp *= r;
-        __syncthreads();
+        tm.sync();
     }
+}
+
+template <int DIR, typename T> __device__ void fft_smem(cplx<T> *buf, const FftDesc &d)
+{
+    fft_smem<DIR, T, 1>(Buf<cplx<T>, 1>(buf), d, Team<1>());
 }
 
 // Decimation-in-frequency variant (the transpose of fft_smem): natural-order
 // input, output element i at position perm[i].  Stages run in reverse order
 // and the twiddles are applied after each small DFT.  Ends with a barrier.
-template <int R, int DIR, typename T>
-__device__ __forceinline__ void fft_stage_dif(cplx<T> *buf, int N, int Lp, const cplx<T> *__restrict__ tw)
+template <int R, int DIR, typename T, class B>
+__device__ __forceinline__ void fft_stage_dif(const B &buf, int N, int Lp, const cplx<T> *__restrict__ tw, int tid,
+                                              int nthr)
 {
     const int L = Lp * R;
     const int nb = N / R;
     const int tstep = N / L;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    for (int b = tid; b < nb; b += nthr) {
         const int g = b / Lp;
         const int j = b - g * Lp;
         const int base = g * L + j;
@@ -236,7 +292,8 @@ __device__ __forceinline__ void fft_stage_dif(cplx<T> *buf, int N, int Lp, const
     }
 }
 
-template <int DIR, typename T> __device__ void fft_smem_dif(cplx<T> *buf, const FftDesc &d)
+template <int DIR, typename T, int CL>
+__device__ void fft_smem_dif(const Buf<cplx<T>, CL> &buf, const FftDesc &d, const Team<CL> &tm)
 {
     const cplx<T> *tw = (const cplx<T> *)d.tw;
     int Lp = d.n;
@@ -244,15 +301,20 @@ template <int DIR, typename T> __device__ void fft_smem_dif(cplx<T> *buf, const 
         const int r = d.radix[st];
         Lp /= r;
         switch (r) {
-        case 2: fft_stage_dif<2, DIR, T>(buf, d.n, Lp, tw); break;
-        case 3: fft_stage_dif<3, DIR, T>(buf, d.n, Lp, tw); break;
-        case 4: fft_stage_dif<4, DIR, T>(buf, d.n, Lp, tw); break;
-        case 5: fft_stage_dif<5, DIR, T>(buf, d.n, Lp, tw); break;
-        case 7: fft_stage_dif<7, DIR, T>(buf, d.n, Lp, tw); break;
-        default: fft_stage_dif<8, DIR, T>(buf, d.n, Lp, tw); break;
+        case 2: fft_stage_dif<2, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 3: fft_stage_dif<3, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 4: fft_stage_dif<4, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 5: fft_stage_dif<5, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 7: fft_stage_dif<7, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        default: fft_stage_dif<8, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         }
-        __syncthreads();
+        tm.sync();
     }
+}
+
+template <int DIR, typename T> __device__ void fft_smem_dif(cplx<T> *buf, const FftDesc &d)
+{
+    fft_smem_dif<DIR, T, 1>(Buf<cplx<T>, 1>(buf), d, Team<1>());
 }
 
 }  // namespace gsl

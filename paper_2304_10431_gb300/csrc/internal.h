@@ -49,6 +49,7 @@ struct Plan {
     double beta = 0, sigma = 0;
     int r_lo = 0, R = 0;  // kept torus rows r in [r_lo, r_lo + R)
     int pitch = 0;        // grid row stride (elements)
+    int cl_theta = 1, cl_phi = 1;  // CTAs per FFT vector (2: a cluster sharing the vector)
     int ncol = 0;         // m columns: mmax+1 (spin 0) or 2 mmax + 1
     int64_t nalm = 0;
 

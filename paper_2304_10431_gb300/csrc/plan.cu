@@ -295,7 +295,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // plans and eps/4 in FP32 plans, where FP32 rounding in the Legendre sums and
     // the FFTs takes ~1e-6 at lmax ~ 4096.  sigma is then picked by a cost model.
     const size_t esz = prec == LENS_FP32 ? 8 : 16;
-    const size_t fft_max = kSmemLimit / esz;
+    // one CTA holds fft_one elements; a cluster of two CTAs twice that
+    const size_t fft_one = kSmemLimit / esz, fft_max = 2 * fft_one;
+    const int force_cl = prm ? prm->fft_cluster : 0;
+    if (force_cl < 0 || force_cl > 2) return bail(LENS_ERR_INVALID, "fft_cluster must be 0, 1 or 2");
     const double eps_nufft = (prec == LENS_FP32 ? 0.25 : 0.5) * epsilon;
     const int ncomp = spin ? 2 : 1;
     Choice best;
@@ -306,10 +309,13 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if (W > 16) continue;
         int N1, N2;
         sizes_for(lmax, mmax, p->M, sg, W, N1, N2);
-        if ((size_t)N1 > fft_max || (size_t)N2 > fft_max) continue;
-        // per-point taps + kernel evaluations, grid passes (FFT + interp)
+        const size_t lim = force_cl == 1 ? fft_one : fft_max;
+        if ((size_t)N1 > lim || (size_t)N2 > lim) continue;
+        // per-point taps + kernel evaluations, grid passes (FFT + interp); FFTs
+        // split over a two-CTA cluster cost more (remote shared-memory accesses)
         const double pts = (double)npoints * ncomp * ((double)W * W + 16.0 * W);
-        const double grd = 12.0 * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1;
+        const double clf = ((size_t)N1 > fft_one || (size_t)N2 > fft_one) ? 1.5 : 1.0;
+        const double grd = clf * (12.0 * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1);
         const double cost = pts + grd;
         if (cost < best.cost) { best.cost = cost; best.sigma = sg; best.W = W; best.N1 = N1; best.N2 = N2; }
     }
@@ -326,6 +332,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     p->W = best.W;
     p->N1 = best.N1;
     p->N2 = best.N2;
+    p->cl_theta = (force_cl == 2 || (size_t)std::max(p->N1, p->M) > fft_one) ? 2 : 1;
+    p->cl_phi = (force_cl == 2 || (size_t)p->N2 > fft_one) ? 2 : 1;
+    if (force_cl == 1 && (p->cl_theta == 2 || p->cl_phi == 2))
+        return bail(LENS_ERR_UNSUPPORTED, "FFT length above one CTA's shared memory with fft_cluster = 1");
     {
         const double s1 = (double)p->N1 / (2 * lmax + 2), s2 = (double)p->N2 / (2 * mmax + 2);
         p->sigma = std::min(s1, s2);

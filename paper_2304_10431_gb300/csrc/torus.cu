@@ -34,29 +34,52 @@ __device__ __forceinline__ int pmod(int a, int n)
     return r < 0 ? r + n : r;
 }
 
+template <typename C, int CL> __device__ __forceinline__ Buf<C, CL> make_buf(C *local, int chunk);
+template <> __device__ __forceinline__ Buf<float2, 1> make_buf<float2, 1>(float2 *l, int) { return Buf<float2, 1>(l); }
+template <> __device__ __forceinline__ Buf<double2, 1> make_buf<double2, 1>(double2 *l, int)
+{
+    return Buf<double2, 1>(l);
+}
+template <> __device__ __forceinline__ Buf<float2, 2> make_buf<float2, 2>(float2 *l, int ch)
+{
+    return Buf<float2, 2>(l, ch);
+}
+template <> __device__ __forceinline__ Buf<double2, 2> make_buf<double2, 2>(double2 *l, int ch)
+{
+    return Buf<double2, 2>(l, ch);
+}
+
+// Every kernel below is written for a team of CL CTAs sharing one vector
+// (fft.cuh): CL = 1 is one CTA with the vector in its shared memory, CL = 2 a
+// cluster of two CTAs holding `chunk` elements each.  Teams of two start with
+// a cluster barrier (both CTAs resident before any remote access) and end
+// with one (no CTA exits while its partner may still read its half).
+
 // ----------------------------------------------------------------- theta fwd
-template <typename T>
+template <typename T, int CL>
 __global__ void __launch_bounds__(1024) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
-                                                    int spin, int ncol, int r_lo, int R)
+                                                    int spin, int ncol, int r_lo, int R, int chunk)
 {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    const int c = blockIdx.x;
+    const Team<CL> tm;
+    if (CL > 1) tm.sync();
+    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
+    const int c = tm.vec();
     const int mc = spin == 0 ? c : c - mmax;
     const T par = ((mc + spin) & 1) ? T(-1) : T(1);
     const int M = fM.n, N1 = fN1.n;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = tm.tid, nthr = tm.nthr;
     const C *F = ring + (int64_t)c * ntheta;
 
     for (int i = tid; i < M; i += nthr) {
         C v = i < ntheta ? F[i] : cscale(F[M - i], par);
         buf[__ldg(fM.perm + i)] = v;
     }
-    __syncthreads();
-    fft_smem<-1, T>(buf, fM);  // natural order c_k * M
+    tm.sync();
+    fft_smem<-1, T, CL>(buf, fM, tm);  // natural order c_k * M
 
     // move k < 0 from M + k to N1 + k (top first: never overwrites an unread
     // source, since N1 >= M), scaling every kept k by w1(k) w2(m)
@@ -65,45 +88,48 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(const cplx<T> *__restrict__ 
         const int k = k0 - tid;
         C v = mkc(T(0), T(0));
         if (k >= -lmax) v = cscale(buf[M + k], w1[k + lmax] * wm);
-        __syncthreads();
+        tm.sync();
         if (k >= -lmax) buf[N1 + k] = v;
-        __syncthreads();
+        tm.sync();
     }
     for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
     for (int i = lmax + 1 + tid; i < N1 - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
-    __syncthreads();
-    fft_smem_dif<+1, T>(buf, fN1);  // y_r at position perm_N1[r]
+    tm.sync();
+    fft_smem_dif<+1, T, CL>(buf, fN1, tm);  // y_r at position perm_N1[r]
 
     for (int rr = tid; rr < R; rr += nthr) {
         const int r = pmod(r_lo + rr, N1);
         X[(int64_t)rr * ncol + c] = buf[__ldg(fN1.perm + r)];
     }
+    if (CL > 1) tm.sync();
 }
 
 // ----------------------------------------------------------------- theta adj
-template <typename T>
+template <typename T, int CL>
 __global__ void __launch_bounds__(1024) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
-                                                    int spin, int ncol, int r_lo, int R)
+                                                    int spin, int ncol, int r_lo, int R, int chunk)
 {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    const int c = blockIdx.x;
+    const Team<CL> tm;
+    if (CL > 1) tm.sync();
+    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
+    const int c = tm.vec();
     const int mc = spin == 0 ? c : c - mmax;
     const T par = ((mc + spin) & 1) ? T(-1) : T(1);
     const int M = fM.n, N1 = fN1.n;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = tm.tid, nthr = tm.nthr;
 
     for (int i = tid; i < N1; i += nthr) buf[i] = mkc(T(0), T(0));
-    __syncthreads();
+    tm.sync();
     for (int rr = tid; rr < R; rr += nthr) {
         const int r = pmod(r_lo + rr, N1);
         buf[__ldg(fN1.perm + r)] = X[(int64_t)rr * ncol + c];
     }
-    __syncthreads();
-    fft_smem<-1, T>(buf, fN1);  // natural order
+    tm.sync();
+    fft_smem<-1, T, CL>(buf, fN1, tm);  // natural order
 
     // move k < 0 from N1 + k down to M + k (lowest first), scale by w1 w2
     const T wm = w2[c];
@@ -111,14 +137,14 @@ __global__ void __launch_bounds__(1024) k_theta_adj(const cplx<T> *__restrict__ 
         const int k = k0 + tid;
         C v = mkc(T(0), T(0));
         if (k <= -1) v = cscale(buf[N1 + k], w1[k + lmax] * wm);
-        __syncthreads();
+        tm.sync();
         if (k <= -1) buf[M + k] = v;
-        __syncthreads();
+        tm.sync();
     }
     for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
     for (int i = lmax + 1 + tid; i < M - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
-    __syncthreads();
-    fft_smem_dif<+1, T>(buf, fM);  // H_j at position perm_M[j]
+    tm.sync();
+    fft_smem_dif<+1, T, CL>(buf, fM, tm);  // H_j at position perm_M[j]
 
     C *F = ring + (int64_t)c * ntheta;
     for (int j = tid; j < ntheta; j += nthr) {
@@ -126,23 +152,26 @@ __global__ void __launch_bounds__(1024) k_theta_adj(const cplx<T> *__restrict__ 
         if (j > 0 && j < ntheta - 1) v = cadd(v, cscale(buf[__ldg(fM.perm + (M - j))], par));
         F[j] = v;
     }
+    if (CL > 1) tm.sync();
 }
 
 // ------------------------------------------------------------------- phi fwd
-// spin 0: CTA = row pair (2b, 2b+1); spin s: CTA = one row.
-template <typename T, bool SPIN>
+// spin 0: team = row pair (2b, 2b+1); spin s: team = one row.
+template <typename T, bool SPIN, int CL>
 __global__ void __launch_bounds__(512) k_phi_fwd(const cplx<T> *__restrict__ X, void *__restrict__ grid,
-                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W)
+                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk)
 {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    const Team<CL> tm;
+    if (CL > 1) tm.sync();
+    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
     const int N2 = fN2.n;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = tm.tid, nthr = tm.nthr;
     for (int i = tid; i < N2; i += nthr) buf[i] = mkc(T(0), T(0));
-    __syncthreads();
+    tm.sync();
     if (!SPIN) {
-        const int ra = 2 * blockIdx.x, rb = ra + 1;
+        const int ra = 2 * tm.vec(), rb = ra + 1;
         const bool hb = rb < R;
         const C *xa = X + (int64_t)ra * ncol;
         const C *xb = X + (int64_t)rb * ncol;
@@ -157,8 +186,8 @@ __global__ void __launch_bounds__(512) k_phi_fwd(const cplx<T> *__restrict__ X, 
                 buf[__ldg(fN2.perm + (N2 - m))] = mkc(a.x + b.y, b.x - a.y);
             }
         }
-        __syncthreads();
-        fft_smem<+1, T>(buf, fN2);
+        tm.sync();
+        fft_smem<+1, T, CL>(buf, fN2, tm);
         T *ga = (T *)grid + (int64_t)ra * pitch;
         T *gb = (T *)grid + (int64_t)rb * pitch;
         for (int c = tid; c < N2 + W - 1; c += nthr) {
@@ -167,31 +196,34 @@ __global__ void __launch_bounds__(512) k_phi_fwd(const cplx<T> *__restrict__ X, 
             if (hb) gb[c] = v.y;
         }
     } else {
-        const int r = blockIdx.x;
+        const int r = tm.vec();
         const C *xr = X + (int64_t)r * ncol;
         for (int i = tid; i < ncol; i += nthr) {
             const int m = i - mmax;
             buf[__ldg(fN2.perm + pmod(m, N2))] = xr[i];
         }
-        __syncthreads();
-        fft_smem<+1, T>(buf, fN2);
+        tm.sync();
+        fft_smem<+1, T, CL>(buf, fN2, tm);
         C *gr = (C *)grid + (int64_t)r * pitch;
         for (int c = tid; c < N2 + W - 1; c += nthr) gr[c] = buf[c < N2 ? c : c - N2];
     }
+    if (CL > 1) tm.sync();
 }
 
 // ------------------------------------------------------------------- phi adj
-template <typename T, bool SPIN>
+template <typename T, bool SPIN, int CL>
 __global__ void __launch_bounds__(512) k_phi_adj(const void *__restrict__ grid, cplx<T> *__restrict__ X,
-                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W)
+                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk)
 {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    const Team<CL> tm;
+    if (CL > 1) tm.sync();
+    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
     const int N2 = fN2.n;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = tm.tid, nthr = tm.nthr;
     if (!SPIN) {
-        const int ra = 2 * blockIdx.x, rb = ra + 1;
+        const int ra = 2 * tm.vec(), rb = ra + 1;
         const bool hb = rb < R;
         const T *ga = (const T *)grid + (int64_t)ra * pitch;
         const T *gb = (const T *)grid + (int64_t)rb * pitch;
@@ -200,8 +232,8 @@ __global__ void __launch_bounds__(512) k_phi_adj(const void *__restrict__ grid, 
             if (c < W - 1) { a += ga[N2 + c]; if (hb) b += gb[N2 + c]; }
             buf[__ldg(fN2.perm + c)] = mkc(a, b);
         }
-        __syncthreads();
-        fft_smem<-1, T>(buf, fN2);
+        tm.sync();
+        fft_smem<-1, T, CL>(buf, fN2, tm);
         C *xa = X + (int64_t)ra * ncol;
         C *xb = X + (int64_t)rb * ncol;
         for (int m = tid; m <= mmax; m += nthr) {
@@ -213,131 +245,142 @@ __global__ void __launch_bounds__(512) k_phi_adj(const void *__restrict__ grid, 
             if (hb) xb[m] = B;
         }
     } else {
-        const int r = blockIdx.x;
+        const int r = tm.vec();
         const C *gr = (const C *)grid + (int64_t)r * pitch;
         for (int c = tid; c < N2; c += nthr) {
             C v = gr[c];
             if (c < W - 1) v = cadd(v, gr[N2 + c]);
             buf[__ldg(fN2.perm + c)] = v;
         }
-        __syncthreads();
-        fft_smem<-1, T>(buf, fN2);
+        tm.sync();
+        fft_smem<-1, T, CL>(buf, fN2, tm);
         C *xr = X + (int64_t)r * ncol;
         for (int i = tid; i < ncol; i += nthr) {
             const int m = i - mmax;
             xr[i] = buf[pmod(m, N2)];
         }
     }
+    if (CL > 1) tm.sync();
 }
-
-template <typename T> size_t csz() { return sizeof(cplx<T>); }
 
 }  // namespace
 
-size_t theta_smem_bytes(const Plan &p) { return (size_t)(p.N1 > p.M ? p.N1 : p.M) * (p.prec == LENS_FP32 ? 8 : 16); }
-size_t phi_smem_bytes(const Plan &p) { return (size_t)p.N2 * (p.prec == LENS_FP32 ? 8 : 16); }
-
-static int theta_threads(const Plan &p) { return p.prec == LENS_FP32 ? 512 : 512; }
-static int phi_threads(const Plan &p) { return p.prec == LENS_FP32 ? 512 : 256; }
-
-template <typename T> static cudaError_t set_smem(const void *fn, size_t bytes)
+// Per-CTA shared memory: the vector's elements divided over the team.
+size_t theta_smem_bytes(const Plan &p)
 {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const size_t n = (size_t)(p.N1 > p.M ? p.N1 : p.M);
+    return (n + p.cl_theta - 1) / p.cl_theta * (p.prec == LENS_FP32 ? 8 : 16);
 }
+size_t phi_smem_bytes(const Plan &p)
+{
+    return ((size_t)p.N2 + p.cl_phi - 1) / p.cl_phi * (p.prec == LENS_FP32 ? 8 : 16);
+}
+
+namespace {
+
+constexpr int kThetaThreads = 512;
+int phi_threads(const Plan &p) { return p.prec == LENS_FP32 ? 512 : 256; }
+
+// Launches nvec teams of cl CTAs (a cluster of two when cl = 2).
+template <class... KArgs, class... Args>
+cudaError_t launch_team(void (*kern)(KArgs...), int cl, int nvec, int threads, size_t smem, cudaStream_t st,
+                        Args... args)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || nvec == 0) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nvec * (unsigned)cl);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cl > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename T>
+cudaError_t theta_fwd_t(const Plan &p, const void *ring, void *X, cudaStream_t st)
+{
+    using C = cplx<T>;
+    const size_t sm = theta_smem_bytes(p);
+    const int chunk = (int)(sm / sizeof(C));
+    auto args = [&](auto kern) {
+        return launch_team(kern, p.cl_theta, p.ncol, kThetaThreads, sm, st, (const C *)ring, (C *)X, p.fM, p.fN1,
+                           (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
+                           chunk);
+    };
+    return p.cl_theta == 2 ? args(k_theta_fwd<T, 2>) : args(k_theta_fwd<T, 1>);
+}
+
+template <typename T>
+cudaError_t theta_adj_t(const Plan &p, const void *X, void *ring, cudaStream_t st)
+{
+    using C = cplx<T>;
+    const size_t sm = theta_smem_bytes(p);
+    const int chunk = (int)(sm / sizeof(C));
+    auto args = [&](auto kern) {
+        return launch_team(kern, p.cl_theta, p.ncol, kThetaThreads, sm, st, (const C *)X, (C *)ring, p.fM, p.fN1,
+                           (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
+                           chunk);
+    };
+    return p.cl_theta == 2 ? args(k_theta_adj<T, 2>) : args(k_theta_adj<T, 1>);
+}
+
+template <typename T, bool SPIN>
+cudaError_t phi_fwd_t(const Plan &p, const void *X, void *grid, cudaStream_t st)
+{
+    using C = cplx<T>;
+    const size_t sm = phi_smem_bytes(p);
+    const int chunk = (int)(sm / sizeof(C));
+    const int nvec = SPIN ? p.R : (p.R + 1) / 2;
+    auto args = [&](auto kern) {
+        return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const C *)X, grid, p.fN2, p.mmax, p.ncol,
+                           p.R, p.pitch, p.W, chunk);
+    };
+    return p.cl_phi == 2 ? args(k_phi_fwd<T, SPIN, 2>) : args(k_phi_fwd<T, SPIN, 1>);
+}
+
+template <typename T, bool SPIN>
+cudaError_t phi_adj_t(const Plan &p, const void *grid, void *X, cudaStream_t st)
+{
+    using C = cplx<T>;
+    const size_t sm = phi_smem_bytes(p);
+    const int chunk = (int)(sm / sizeof(C));
+    const int nvec = SPIN ? p.R : (p.R + 1) / 2;
+    auto args = [&](auto kern) {
+        return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const void *)grid, (C *)X, p.fN2, p.mmax,
+                           p.ncol, p.R, p.pitch, p.W, chunk);
+    };
+    return p.cl_phi == 2 ? args(k_phi_adj<T, SPIN, 2>) : args(k_phi_adj<T, SPIN, 1>);
+}
+
+}  // namespace
 
 cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st)
 {
-    const size_t sm = theta_smem_bytes(p);
-    if (p.prec == LENS_FP32) {
-        cudaError_t e = set_smem<float>((const void *)k_theta_fwd<float>, sm);
-        if (e != cudaSuccess) return e;
-        k_theta_fwd<float><<<p.ncol, theta_threads(p), sm, st>>>(
-            (const float2 *)ring, (float2 *)X, p.fM, p.fN1, (const float *)p.w1, (const float *)p.w2, p.ntheta,
-            p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R);
-    } else {
-        cudaError_t e = set_smem<double>((const void *)k_theta_fwd<double>, sm);
-        if (e != cudaSuccess) return e;
-        k_theta_fwd<double><<<p.ncol, theta_threads(p), sm, st>>>(
-            (const double2 *)ring, (double2 *)X, p.fM, p.fN1, (const double *)p.w1, (const double *)p.w2, p.ntheta,
-            p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R);
-    }
-    return cudaGetLastError();
+    return p.prec == LENS_FP32 ? theta_fwd_t<float>(p, ring, X, st) : theta_fwd_t<double>(p, ring, X, st);
 }
 
 cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st)
 {
-    const size_t sm = theta_smem_bytes(p);
-    if (p.prec == LENS_FP32) {
-        cudaError_t e = set_smem<float>((const void *)k_theta_adj<float>, sm);
-        if (e != cudaSuccess) return e;
-        k_theta_adj<float><<<p.ncol, theta_threads(p), sm, st>>>(
-            (const float2 *)X, (float2 *)ring, p.fM, p.fN1, (const float *)p.w1, (const float *)p.w2, p.ntheta,
-            p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R);
-    } else {
-        cudaError_t e = set_smem<double>((const void *)k_theta_adj<double>, sm);
-        if (e != cudaSuccess) return e;
-        k_theta_adj<double><<<p.ncol, theta_threads(p), sm, st>>>(
-            (const double2 *)X, (double2 *)ring, p.fM, p.fN1, (const double *)p.w1, (const double *)p.w2,
-            p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R);
-    }
-    return cudaGetLastError();
+    return p.prec == LENS_FP32 ? theta_adj_t<float>(p, X, ring, st) : theta_adj_t<double>(p, X, ring, st);
 }
 
 cudaError_t launch_phi_fwd(const Plan &p, const void *X, void *grid, cudaStream_t st)
 {
-    const size_t sm = phi_smem_bytes(p);
-    const int nblk = p.spin ? p.R : (p.R + 1) / 2;
-    cudaError_t e;
-    if (p.prec == LENS_FP32) {
-        if (p.spin) {
-            if ((e = set_smem<float>((const void *)k_phi_fwd<float, true>, sm)) != cudaSuccess) return e;
-            k_phi_fwd<float, true><<<nblk, phi_threads(p), sm, st>>>((const float2 *)X, grid, p.fN2, p.mmax, p.ncol,
-                                                                     p.R, p.pitch, p.W);
-        } else {
-            if ((e = set_smem<float>((const void *)k_phi_fwd<float, false>, sm)) != cudaSuccess) return e;
-            k_phi_fwd<float, false><<<nblk, phi_threads(p), sm, st>>>((const float2 *)X, grid, p.fN2, p.mmax,
-                                                                      p.ncol, p.R, p.pitch, p.W);
-        }
-    } else {
-        if (p.spin) {
-            if ((e = set_smem<double>((const void *)k_phi_fwd<double, true>, sm)) != cudaSuccess) return e;
-            k_phi_fwd<double, true><<<nblk, phi_threads(p), sm, st>>>((const double2 *)X, grid, p.fN2, p.mmax,
-                                                                      p.ncol, p.R, p.pitch, p.W);
-        } else {
-            if ((e = set_smem<double>((const void *)k_phi_fwd<double, false>, sm)) != cudaSuccess) return e;
-            k_phi_fwd<double, false><<<nblk, phi_threads(p), sm, st>>>((const double2 *)X, grid, p.fN2, p.mmax,
-                                                                       p.ncol, p.R, p.pitch, p.W);
-        }
-    }
-    return cudaGetLastError();
+    if (p.prec == LENS_FP32) return p.spin ? phi_fwd_t<float, true>(p, X, grid, st) : phi_fwd_t<float, false>(p, X, grid, st);
+    return p.spin ? phi_fwd_t<double, true>(p, X, grid, st) : phi_fwd_t<double, false>(p, X, grid, st);
 }
 
 cudaError_t launch_phi_adj(const Plan &p, const void *grid, void *X, cudaStream_t st)
 {
-    const size_t sm = phi_smem_bytes(p);
-    const int nblk = p.spin ? p.R : (p.R + 1) / 2;
-    cudaError_t e;
-    if (p.prec == LENS_FP32) {
-        if (p.spin) {
-            if ((e = set_smem<float>((const void *)k_phi_adj<float, true>, sm)) != cudaSuccess) return e;
-            k_phi_adj<float, true><<<nblk, phi_threads(p), sm, st>>>(grid, (float2 *)X, p.fN2,
-                                                                     p.mmax, p.ncol, p.R, p.pitch, p.W);
-        } else {
-            if ((e = set_smem<float>((const void *)k_phi_adj<float, false>, sm)) != cudaSuccess) return e;
-            k_phi_adj<float, false><<<nblk, phi_threads(p), sm, st>>>(grid, (float2 *)X, p.fN2, p.mmax, p.ncol, p.R, p.pitch, p.W);
-        }
-    } else {
-        if (p.spin) {
-            if ((e = set_smem<double>((const void *)k_phi_adj<double, true>, sm)) != cudaSuccess) return e;
-            k_phi_adj<double, true><<<nblk, phi_threads(p), sm, st>>>(grid, (double2 *)X, p.fN2, p.mmax, p.ncol, p.R,
-                                                                      p.pitch, p.W);
-        } else {
-            if ((e = set_smem<double>((const void *)k_phi_adj<double, false>, sm)) != cudaSuccess) return e;
-            k_phi_adj<double, false><<<nblk, phi_threads(p), sm, st>>>(grid, (double2 *)X, p.fN2, p.mmax, p.ncol, p.R,
-                                                                       p.pitch, p.W);
-        }
-    }
-    return cudaGetLastError();
+    if (p.prec == LENS_FP32) return p.spin ? phi_adj_t<float, true>(p, grid, X, st) : phi_adj_t<float, false>(p, grid, X, st);
+    return p.spin ? phi_adj_t<double, true>(p, grid, X, st) : phi_adj_t<double, false>(p, grid, X, st);
 }
 
 }  // namespace gsl
