@@ -51,6 +51,11 @@ def _load():
         lib.oracle_synthesis.argtypes = [i32, i32, i32, i64, dp, dp, dp, dp, dp]
         lib.oracle_adjoint.restype = i32
         lib.oracle_adjoint.argtypes = [i32, i32, i32, i64, dp, dp, dp, dp, dp]
+        for name in ("oracle_synthesis_dd", "oracle_adjoint_dd"):
+            getattr(lib, name).restype = i32
+            getattr(lib, name).argtypes = [i32, i32, i32, i64, dp, dp, dp, dp, dp]
+        lib.oracle_slambda_dd.restype = i32
+        lib.oracle_slambda_dd.argtypes = [i32, i32, i32, ctypes.c_double, dp]
         lib.oracle_pointing.restype = i32
         lib.oracle_pointing.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp]
         lib.oracle_num_threads.restype = i32
@@ -80,10 +85,13 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
-def slambda(lmax: int, m: int, spin: int, theta: float) -> np.ndarray:
-    """spin lambda_{l,m}(theta) for l = 0..lmax, so that sY_lm = slambda * e^{i m phi}."""
+def slambda(lmax: int, m: int, spin: int, theta: float, precise: bool = False) -> np.ndarray:
+    """spin lambda_{l,m}(theta) for l = 0..lmax, so that sY_lm = slambda * e^{i m phi}.
+
+    precise=True runs the start value and recursion in double-double (~106 bits)."""
     out = np.zeros(lmax + 1)
-    rc = _load().oracle_slambda(lmax, m, spin, float(theta), _ptr(out))
+    fn = _load().oracle_slambda_dd if precise else _load().oracle_slambda
+    rc = fn(lmax, m, spin, float(theta), _ptr(out))
     if rc:
         raise ValueError("oracle_slambda: bad arguments")
     return out
@@ -105,11 +113,13 @@ def ring_coeffs(lmax: int, mmax: int, spin: int, theta, alm) -> np.ndarray:
     return out
 
 
-def synthesis(lmax: int, mmax: int, spin: int, theta, phi, alm, chi=None) -> np.ndarray:
+def synthesis(lmax: int, mmax: int, spin: int, theta, phi, alm, chi=None, precise: bool = False) -> np.ndarray:
     """Forward lensing operator by direct summation.
 
     alm: [ncomp, nalm] complex (spin 0: [1, nalm] or [nalm]); returns [ncomp, npts]
     (spin 0: T; spin s: Q, U).  Imaginary parts of the m = 0 entries are ignored.
+    precise=True evaluates the harmonics in double-double (for targets near 1e-12
+    at lmax ~ 5000, where the FP64 recursion's own rounding reaches ~1e-12).
     """
     theta, phi = _f64(theta), _f64(phi)
     chi = None if chi is None else _f64(chi)
@@ -121,15 +131,16 @@ def synthesis(lmax: int, mmax: int, spin: int, theta, phi, alm, chi=None) -> np.
     # imaginary part there is outside the domain and ignored, as by the library
     alm[:, :lmax + 1] = alm[:, :lmax + 1].real
     out = np.zeros((ncomp, theta.size))
-    rc = _load().oracle_synthesis(lmax, mmax, spin, theta.size, _ptr(theta), _ptr(phi), _ptr(chi),
-                                  _ptr(alm), _ptr(out))
+    fn = _load().oracle_synthesis_dd if precise else _load().oracle_synthesis
+    rc = fn(lmax, mmax, spin, theta.size, _ptr(theta), _ptr(phi), _ptr(chi), _ptr(alm), _ptr(out))
     if rc:
         raise ValueError("oracle_synthesis: bad arguments")
     return out
 
 
-def adjoint(lmax: int, mmax: int, spin: int, theta, phi, m, chi=None) -> np.ndarray:
-    """Adjoint lensing operator by direct summation; returns [ncomp, nalm] complex."""
+def adjoint(lmax: int, mmax: int, spin: int, theta, phi, m, chi=None, precise: bool = False) -> np.ndarray:
+    """Adjoint lensing operator by direct summation; returns [ncomp, nalm] complex.
+    precise=True as for synthesis."""
     theta, phi = _f64(theta), _f64(phi)
     chi = None if chi is None else _f64(chi)
     ncomp = 1 if spin == 0 else 2
@@ -137,8 +148,8 @@ def adjoint(lmax: int, mmax: int, spin: int, theta, phi, m, chi=None) -> np.ndar
     if m.shape[1] != theta.size:
         raise ValueError("map has the wrong size")
     out = np.zeros((ncomp, nalm(lmax, mmax)), dtype=np.complex128)
-    rc = _load().oracle_adjoint(lmax, mmax, spin, theta.size, _ptr(theta), _ptr(phi), _ptr(chi),
-                                _ptr(m), _ptr(out))
+    fn = _load().oracle_adjoint_dd if precise else _load().oracle_adjoint
+    rc = fn(lmax, mmax, spin, theta.size, _ptr(theta), _ptr(phi), _ptr(chi), _ptr(m), _ptr(out))
     if rc:
         raise ValueError("oracle_adjoint: bad arguments")
     return out

@@ -1,5 +1,5 @@
 /*
- * FP64 CPU oracle for the general spherical harmonic transform of CMB lensing
+ * FP64 (and double-double) CPU oracle for the general spherical harmonic transform of CMB lensing
  * (Reinecke, Belkner & Carron, arXiv:2304.10431).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
@@ -37,6 +37,12 @@
  * Underflow of sin^m is handled by carrying an explicit power-of-two exponent
  * next to the recursion values; values whose true magnitude is below the
  * double range contribute exactly zero.
+ *
+ * The *_dd entry points evaluate the same definitions with the harmonics
+ * (cos and sin of the angles, start values, recursion coefficients and
+ * values, e^{i m phi}) in double-double arithmetic (~106 bits) and the sums
+ * as above: at lmax ~ 5000 the FP64 recursion's own rounding reaches ~1e-12,
+ * the level of the smallest accuracy targets.
  *
  * a_lm layout: index(l,m) = m(2 lmax + 1 - m)/2 + l for 0 <= m <= mmax,
  * m <= l <= lmax; complex numbers are (re, im) pairs of doubles.
@@ -177,20 +183,223 @@ static void lambda_run(int lmax, int m, int sigma, double theta, sdbl st, double
     }
 }
 
+/* ------------------------------------------------- double-double mode
+ * For targets near or below 1e-12 the FP64 recursion above is not accurate
+ * enough at lmax ~ 5000 (cos(theta) and cos(theta/2)^m rounded to FP64, the
+ * recursion's own rounding, cos(m phi) of a rounded argument: each ~1e-12).
+ * The "precise" entry points therefore carry cos, sin, the start values, the
+ * recursion coefficients and values, and e^{i m phi} as unevaluated sums of
+ * two doubles (Dekker / Knuth error-free transformations, FMA products),
+ * about 106 bits; each value is rounded to one double only where it enters a
+ * compensated sum. */
+typedef struct { double h, l; } dd;
+static inline dd dd_make(double h, double l) { dd r = {h, l}; return r; }
+static inline dd dd_fast(double a, double b) /* |a| >= |b| */
+{
+    double s = a + b;
+    return dd_make(s, b - (s - a));
+}
+static inline dd dd_two_sum(double a, double b)
+{
+    double s = a + b, bb = s - a;
+    return dd_make(s, (a - (s - bb)) + (b - bb));
+}
+static inline dd dd_add(dd a, dd b)
+{
+    dd s = dd_two_sum(a.h, b.h), t = dd_two_sum(a.l, b.l);
+    s.l += t.h;
+    s = dd_fast(s.h, s.l);
+    s.l += t.l;
+    return dd_fast(s.h, s.l);
+}
+static inline dd dd_neg(dd a) { return dd_make(-a.h, -a.l); }
+static inline dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+static inline dd dd_mul(dd a, dd b)
+{
+    double p = a.h * b.h;
+    double e = fma(a.h, b.h, -p) + (a.h * b.l + a.l * b.h);
+    return dd_fast(p, e);
+}
+static inline dd dd_mul_d(dd a, double b)
+{
+    double p = a.h * b;
+    double e = fma(a.h, b, -p) + a.l * b;
+    return dd_fast(p, e);
+}
+static inline dd dd_div(dd a, dd b)
+{
+    double q1 = a.h / b.h;
+    dd r = dd_sub(a, dd_mul_d(b, q1));
+    double q2 = r.h / b.h;
+    r = dd_sub(r, dd_mul_d(b, q2));
+    double q3 = r.h / b.h;
+    dd q = dd_fast(q1, q2);
+    return dd_add(q, dd_make(q3, 0.0));
+}
+static inline dd dd_sqrt(dd a)
+{
+    double s;
+    dd r;
+    if (a.h <= 0.0) return dd_make(0.0, 0.0);
+    s = sqrt(a.h);
+    r = dd_sub(a, dd_mul(dd_make(s, 0.0), dd_make(s, 0.0)));
+    return dd_fast(s, r.h / (2.0 * s));
+}
+static inline dd dd_ldexp(dd a, int e) { return dd_make(ldexp(a.h, e), ldexp(a.l, e)); }
+static const dd DD_PI = {3.141592653589793116e+00, 1.224646799147353207e-16};
+
+/* sin and cos of an exact double t: Taylor series of t / 2^K (|t| / 2^K <=
+ * 2^-9), then K angle doublings. */
+static void dd_sincos(double t, dd *sn, dd *cs)
+{
+    int K = 12;
+    while (fabs(ldexp(t, -K)) > 0x1p-9) ++K;
+    dd u = dd_make(ldexp(t, -K), 0.0), u2 = dd_mul(u, u);
+    dd s = u, c = dd_make(1.0, 0.0), ts = u, tc = dd_make(1.0, 0.0);
+    int k;
+    for (k = 1; k <= 10; ++k) {
+        ts = dd_div(dd_mul(ts, u2), dd_make(-(double)((2 * k) * (2 * k + 1)), 0.0));
+        tc = dd_div(dd_mul(tc, u2), dd_make(-(double)((2 * k - 1) * (2 * k)), 0.0));
+        s = dd_add(s, ts);
+        c = dd_add(c, tc);
+    }
+    for (k = 0; k < K; ++k) {
+        dd s2 = dd_ldexp(dd_mul(s, c), 1);
+        dd c2 = dd_mul(dd_sub(c, s), dd_add(c, s));
+        s = s2;
+        c = c2;
+    }
+    *sn = s;
+    *cs = c;
+}
+
+/* scaled double-double x = v 2^e, |v.h| in [0.5, 1) */
+typedef struct { dd v; int e; } sdd;
+static inline sdd sdd_norm(dd v, int e)
+{
+    int k;
+    sdd r;
+    if (v.h == 0.0) { r.v = dd_make(0.0, 0.0); r.e = 0; return r; }
+    frexp(v.h, &k);
+    r.v = dd_ldexp(v, -k);
+    r.e = e + k;
+    return r;
+}
+static inline sdd sdd_mul(sdd a, sdd b) { return sdd_norm(dd_mul(a.v, b.v), a.e + b.e); }
+static sdd sdd_pow(dd x, int n)
+{
+    sdd r = sdd_norm(dd_make(1.0, 0.0), 0), b = sdd_norm(x, 0);
+    while (n > 0) {
+        if (n & 1) r = sdd_mul(r, b);
+        b = sdd_mul(b, b);
+        n >>= 1;
+    }
+    return r;
+}
+
+/* start value (the closed form of start_value) and the recursion of
+ * lambda_run, in double-double; out[l] receives the value rounded to double */
+static void lambda_run_dd(int lmax, int m, int sigma, double theta, double *out)
+{
+    int a = sigma < 0 ? -sigma : sigma;
+    int l0 = m >= a ? m : a, l, i;
+    int n = 2 * l0, k = m >= a ? m + sigma : a + m, pc, ps, sign, E;
+    dd sh, ch, x, prev, cur;
+    sdd r, bin;
+    double m1 = m, m2 = -sigma;
+    for (l = 0; l <= lmax && l < l0; ++l) out[l] = 0.0;
+    if (l0 > lmax) return;
+    dd_sincos(0.5 * theta, &sh, &ch);
+    x = dd_sub(dd_mul(ch, ch), dd_mul(sh, sh)); /* cos theta */
+    if (m >= a) { pc = m - sigma; ps = m + sigma; sign = (m & 1) ? -1 : 1; }
+    else if (sigma > 0) { pc = a - m; ps = a + m; sign = (m & 1) ? -1 : 1; }
+    else { pc = a + m; ps = a - m; sign = (a & 1) ? -1 : 1; }
+    if (ps > 0 && sh.h == 0.0) { for (l = l0; l <= lmax; ++l) out[l] = 0.0; return; }
+    if (pc > 0 && ch.h == 0.0) { for (l = l0; l <= lmax; ++l) out[l] = 0.0; return; }
+    bin = sdd_norm(dd_make(1.0, 0.0), 0);
+    for (i = 1; i <= k; ++i)
+        bin = sdd_norm(dd_div(dd_mul_d(bin.v, (double)(n - k + i)), dd_make((double)i, 0.0)), bin.e);
+    /* sqrt(bin (2 l0 + 1) / (4 pi)) with an even exponent */
+    if (bin.e & 1) { bin.v = dd_ldexp(bin.v, 1); bin.e -= 1; }
+    r.v = dd_sqrt(dd_div(dd_mul_d(bin.v, 2.0 * l0 + 1.0), dd_ldexp(DD_PI, 2)));
+    r = sdd_norm(r.v, bin.e / 2);
+    if (pc > 0) r = sdd_mul(r, sdd_pow(ch, pc));
+    if (ps > 0) r = sdd_mul(r, sdd_pow(sh, ps));
+    if (sign < 0) r.v = dd_neg(r.v);
+    /* values carried as cur * 2^E, E a multiple of 128 (or 0) */
+    E = 0;
+    if (r.e < 0) { E = -((-r.e + 127) / 128) * 128; }
+    cur = dd_ldexp(r.v, r.e - E);
+    prev = dd_make(0.0, 0.0);
+    out[l0] = ldexp(cur.h + cur.l, E);
+    for (l = l0; l < lmax; ++l) {
+        double lp = l + 1.0, ll = l;
+        dd den = dd_mul(dd_make((lp - m1) * (lp + m1), 0.0), dd_make((lp - m2) * (lp + m2), 0.0));
+        dd alpha = dd_mul_d(dd_sqrt(dd_div(dd_make((2.0 * ll + 3.0) * (2.0 * ll + 1.0), 0.0), den)), lp);
+        dd cc = dd_make(0.0, 0.0), beta = dd_make(0.0, 0.0), nxt;
+        if (l > 0) {
+            dd num = dd_mul(dd_make((ll - m1) * (ll + m1), 0.0), dd_make((ll - m2) * (ll + m2), 0.0));
+            cc = dd_div(dd_make(m1 * m2, 0.0), dd_make(ll * lp, 0.0));
+            beta = dd_mul(dd_div(dd_make(lp, 0.0), dd_make(ll, 0.0)),
+                          dd_sqrt(dd_mul(dd_div(dd_make(2.0 * ll + 3.0, 0.0), dd_make(2.0 * ll - 1.0, 0.0)),
+                                         dd_div(num, den))));
+        }
+        nxt = dd_sub(dd_mul(dd_mul(alpha, dd_sub(x, cc)), cur), dd_mul(beta, prev));
+        prev = cur;
+        cur = nxt;
+        if (E < 0 && fabs(cur.h) > 0x1p128) {
+            cur = dd_ldexp(cur, -128); prev = dd_ldexp(prev, -128); E += 128;
+        }
+        out[l + 1] = E == 0 ? cur.h + cur.l : ldexp(cur.h + cur.l, E);
+    }
+}
+
+/* e^{i m phi}, m = 0..mmax, by repeated double-double multiplication */
+static void eimphi_dd(int mmax, double phi, double *cm, double *sm)
+{
+    dd s1, c1, c = dd_make(1.0, 0.0), s = dd_make(0.0, 0.0);
+    int m;
+    dd_sincos(phi, &s1, &c1);
+    for (m = 0; m <= mmax; ++m) {
+        dd cn, sn;
+        cm[m] = c.h + c.l;
+        sm[m] = s.h + s.l;
+        cn = dd_sub(dd_mul(c, c1), dd_mul(s, s1));
+        sn = dd_add(dd_mul(s, c1), dd_mul(c, s1));
+        c = cn;
+        s = sn;
+    }
+}
+
+/* sigma lambda_{l,m}(theta) for l = 0..lmax in FP64 or double-double */
+static void lambda_any(int lmax, int m, int sigma, double theta, int precise, double *out)
+{
+    if (precise) lambda_run_dd(lmax, m, sigma, theta, out);
+    else lambda_run(lmax, m, sigma, theta, start_value(m, sigma, theta), out);
+}
+
 /* Pin helper: sigma lambda_{l,m}(theta), l = 0..lmax, for any sign of m. */
-int oracle_slambda(int lmax, int m, int sigma, double theta, double *out)
+static int slambda_impl(int lmax, int m, int sigma, double theta, int precise, double *out)
 {
     int am = m < 0 ? -m : m;
     if (lmax < 0 || am > lmax) return 1;
     if (m >= 0) {
-        lambda_run(lmax, m, sigma, theta, start_value(m, sigma, theta), out);
+        lambda_any(lmax, m, sigma, theta, precise, out);
     } else {
         /* s lambda_{l,-m} = (-1)^{s+m} (-s) lambda_{l,m} */
         int l, sg = ((sigma + am) & 1) ? -1 : 1;
-        lambda_run(lmax, am, -sigma, theta, start_value(am, -sigma, theta), out);
+        lambda_any(lmax, am, -sigma, theta, precise, out);
         for (l = 0; l <= lmax; ++l) out[l] *= sg;
     }
     return 0;
+}
+int oracle_slambda(int lmax, int m, int sigma, double theta, double *out)
+{
+    return slambda_impl(lmax, m, sigma, theta, 0, out);
+}
+int oracle_slambda_dd(int lmax, int m, int sigma, double theta, double *out)
+{
+    return slambda_impl(lmax, m, sigma, theta, 1, out);
 }
 
 /* ------------------------------------------------------------- forward */
@@ -262,8 +471,8 @@ int oracle_ring_coeffs(int lmax, int mmax, int spin, int64_t npts, const double 
  * alm: [ncomp][nalm] complex (ncomp = 1 for spin 0: T; 2 for spin s: G, C).
  * map: [ncomp][npts] real (spin 0: T; spin s: Q = Re, U = Im).
  * chi may be NULL (no phase). */
-int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *theta,
-                     const double *phi, const double *chi, const double *alm, double *map)
+static int synthesis_impl(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                          const double *phi, const double *chi, const double *alm, double *map, int precise)
 {
     int64_t nalm = oracle_nalm(lmax, mmax);
     int64_t i;
@@ -272,16 +481,20 @@ int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *t
     {
         double *lp = (double *)malloc(sizeof(double) * (lmax + 1));
         double *lm = (double *)malloc(sizeof(double) * (lmax + 1));
+        double *cmv = (double *)malloc(sizeof(double) * (mmax + 1));
+        double *smv = (double *)malloc(sizeof(double) * (mmax + 1));
 #pragma omp for schedule(dynamic, 1)
         for (i = 0; i < npts; ++i) {
             int m, l;
             double th = theta[i], ph = phi[i];
+            if (precise) eimphi_dd(mmax, ph, cmv, smv);
+            else for (m = 0; m <= mmax; ++m) { cmv[m] = cos(m * ph); smv[m] = sin(m * ph); }
             if (spin == 0) {
                 nsum tot = {0, 0};
                 for (m = 0; m <= mmax; ++m) {
                     nsum re = {0, 0}, im = {0, 0};
-                    double cm = cos(m * ph), sm = sin(m * ph), w = m == 0 ? 1.0 : 2.0;
-                    lambda_run(lmax, m, 0, th, start_value(m, 0, th), lp);
+                    double cm = cmv[m], sm = smv[m], w = m == 0 ? 1.0 : 2.0;
+                    lambda_any(lmax, m, 0, th, precise, lp);
                     for (l = m; l <= lmax; ++l) {
                         const double *a = alm + 2 * alm_index(lmax, l, m);
                         ns_add(&re, a[0] * lp[l]);
@@ -298,9 +511,9 @@ int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *t
                 double ps, pc, zr, zi;
                 for (m = 0; m <= mmax; ++m) {
                     nsum pr = {0, 0}, pi = {0, 0}, qr = {0, 0}, qi = {0, 0};
-                    double cm = cos(m * ph), sm = sin(m * ph);
-                    lambda_run(lmax, m, spin, th, start_value(m, spin, th), lp);
-                    lambda_run(lmax, m, -spin, th, start_value(m, -spin, th), lm);
+                    double cm = cmv[m], sm = smv[m];
+                    lambda_any(lmax, m, spin, th, precise, lp);
+                    lambda_any(lmax, m, -spin, th, precise, lm);
                     for (l = m; l <= lmax; ++l) {
                         const double *g = G + 2 * alm_index(lmax, l, m);
                         const double *c = C + 2 * alm_index(lmax, l, m);
@@ -327,8 +540,22 @@ int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *t
         }
         free(lp);
         free(lm);
+        free(cmv);
+        free(smv);
     }
     return 0;
+}
+
+int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                     const double *phi, const double *chi, const double *alm, double *map)
+{
+    return synthesis_impl(lmax, mmax, spin, npts, theta, phi, chi, alm, map, 0);
+}
+
+int oracle_synthesis_dd(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                        const double *phi, const double *chi, const double *alm, double *map)
+{
+    return synthesis_impl(lmax, mmax, spin, npts, theta, phi, chi, alm, map, 1);
 }
 
 /* ------------------------------------------------------------- adjoint */
@@ -338,8 +565,8 @@ int oracle_synthesis(int lmax, int mmax, int spin, int64_t npts, const double *t
  *            G = -(sA + (-1)^s (-s)A)/2,  C = -(sA - (-1)^s (-s)A)/(2i)
  * Parallel over m; points are processed in blocks so that the per-point
  * start values (one scaled number per m and spin sign) fit in memory. */
-int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *theta,
-                   const double *phi, const double *chi, const double *map, double *alm)
+static int adjoint_impl(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                        const double *phi, const double *chi, const double *map, double *alm, int precise)
 {
     int64_t nalm = oracle_nalm(lmax, mmax);
     int nsig = spin == 0 ? 1 : 2;
@@ -354,16 +581,25 @@ int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *the
     for (b0 = 0; b0 < npts; b0 += blk) {
         int64_t nb = npts - b0 < blk ? npts - b0 : blk;
         sdbl *st = (sdbl *)malloc(sizeof(sdbl) * (size_t)(nb * (mmax + 1) * nsig));
+        double *ec = (double *)malloc(sizeof(double) * (size_t)(nb * (mmax + 1)));
+        double *es = (double *)malloc(sizeof(double) * (size_t)(nb * (mmax + 1)));
         int64_t j;
         int m;
-        if (!st) { free(acc); return 2; }
+        if (!st || !ec || !es) { free(st); free(ec); free(es); free(acc); return 2; }
 #pragma omp parallel for schedule(static)
         for (j = 0; j < nb; ++j) {
             int mm, sg;
-            for (mm = 0; mm <= mmax; ++mm)
-                for (sg = 0; sg < nsig; ++sg)
-                    st[(j * (mmax + 1) + mm) * nsig + sg] =
-                        start_value(mm, sg == 0 ? spin : -spin, theta[b0 + j]);
+            if (!precise)
+                for (mm = 0; mm <= mmax; ++mm)
+                    for (sg = 0; sg < nsig; ++sg)
+                        st[(j * (mmax + 1) + mm) * nsig + sg] =
+                            start_value(mm, sg == 0 ? spin : -spin, theta[b0 + j]);
+            if (precise) eimphi_dd(mmax, phi[b0 + j], ec + j * (mmax + 1), es + j * (mmax + 1));
+            else
+                for (mm = 0; mm <= mmax; ++mm) {
+                    ec[j * (mmax + 1) + mm] = cos(mm * phi[b0 + j]);
+                    es[j * (mmax + 1) + mm] = sin(mm * phi[b0 + j]);
+                }
         }
 #pragma omp parallel
         {
@@ -377,7 +613,7 @@ int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *the
                     int64_t jj;
                     for (jj = 0; jj < nb; ++jj) {
                         int64_t i = b0 + jj;
-                        double cm = cos(m * phi[i]), sm = sin(m * phi[i]);
+                        double cm = ec[jj * (mmax + 1) + m], sm = es[jj * (mmax + 1) + m];
                         double xr, xi, wr, wi;
                         if (spin == 0) { xr = map[i]; xi = 0.0; }
                         else {
@@ -391,7 +627,8 @@ int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *the
                         /* times e^{-i m phi} */
                         wr = xr * cm + xi * sm;
                         wi = xi * cm - xr * sm;
-                        lambda_run(lmax, m, sigma, theta[i], st[(jj * (mmax + 1) + m) * nsig + sg], lp);
+                        if (precise) lambda_run_dd(lmax, m, sigma, theta[i], lp);
+                        else lambda_run(lmax, m, sigma, theta[i], st[(jj * (mmax + 1) + m) * nsig + sg], lp);
                         for (l = m; l <= lmax; ++l) {
                             ns_add(&A[2 * (l - m)], wr * lp[l]);
                             ns_add(&A[2 * (l - m) + 1], wi * lp[l]);
@@ -402,6 +639,8 @@ int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *the
             free(lp);
         }
         free(st);
+        free(ec);
+        free(es);
     }
     {
         int64_t k;
@@ -425,6 +664,18 @@ int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *the
     }
     free(acc);
     return 0;
+}
+
+int oracle_adjoint(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                   const double *phi, const double *chi, const double *map, double *alm)
+{
+    return adjoint_impl(lmax, mmax, spin, npts, theta, phi, chi, map, alm, 0);
+}
+
+int oracle_adjoint_dd(int lmax, int mmax, int spin, int64_t npts, const double *theta,
+                      const double *phi, const double *chi, const double *map, double *alm)
+{
+    return adjoint_impl(lmax, mmax, spin, npts, theta, phi, chi, map, alm, 1);
 }
 
 /* ------------------------------------------------------------ pointing */

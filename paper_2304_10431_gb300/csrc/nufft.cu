@@ -41,10 +41,25 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kPi = 3.141592653589793238462643383280;
 constexpr int kSpreadThreads = 128;
 
+// Grid coordinate u = t c with c = N / (2 pi) held as a double-double (c.x +
+// c.y): the product's rounding error, ~1e-16 of u (up to N/2 ~ 10^4 cells),
+// would otherwise move the point by about one ulp of theta, i.e. a relative
+// error of ~lmax * 1e-16 in the interpolated field.  Returns the cell index
+// ceil(u - W/2) and the offset u - index to full double precision.
+__device__ __forceinline__ int grid_coord(double t, double2 c, double hw, double &frac)
+{
+    const double p = t * c.x;
+    const double e = fma(t, c.x, -p) + t * c.y;
+    const int i0 = (int)ceil((p + e) - hw);
+    frac = (p - (double)i0) + e;  // p - i0 is exact: both lie within W of each other
+    return i0;
+}
+
 __global__ void k_prep(const double *__restrict__ theta, const double *__restrict__ phi,
                        const double *__restrict__ chi, int64_t n, int N1, int N2, int W, int r_lo, int R, int pitch,
-                       int spin, uint32_t *__restrict__ key, int32_t *__restrict__ idx, uint32_t *__restrict__ cell_u,
-                       double2 *__restrict__ frac_u, double2 *__restrict__ phase_u, unsigned *__restrict__ flags)
+                       int spin, double2 c1, double2 c2, uint32_t *__restrict__ key, int32_t *__restrict__ idx,
+                       uint32_t *__restrict__ cell_u, double2 *__restrict__ frac_u, double2 *__restrict__ phase_u,
+                       unsigned *__restrict__ flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -59,11 +74,9 @@ __global__ void k_prep(const double *__restrict__ theta, const double *__restric
     if (ph < 0.0) ph += kTwoPi;
     if (ph >= kTwoPi) ph = 0.0;
     const double hw = 0.5 * W;
-    const double u = th * (N1 / kTwoPi);
-    const double v = ph * (N2 / kTwoPi);
-    const int i0 = (int)ceil(u - hw);
-    int j0 = (int)ceil(v - hw);
-    const double fu = u - i0, fv = v - j0;
+    double fu, fv;
+    const int i0 = grid_coord(th, c1, hw, fu);
+    int j0 = grid_coord(ph, c2, hw, fv);
     if (j0 < 0) j0 += N2;
     if (j0 >= N2) j0 -= N2;
     int row = i0 - r_lo;
@@ -442,8 +455,18 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
     GSL_TRY(cudaMemsetAsync(p.flags, 0, sizeof(unsigned), st));
     const int thr = 256;
     const unsigned blocks = (unsigned)((n + thr - 1) / thr);
-    k_prep<<<blocks, thr, 0, st>>>(theta, phi, chi, n, p.N1, p.N2, p.W, p.r_lo, p.R, p.pitch, p.spin, key, idx,
-                                   cell_u, frac_u, phase_u, p.flags);
+    // N / (2 pi) as double-doubles: quotient of N by 2 pi = T_HI + T_LO, refined once
+    auto scale_of = [](int N) {
+        const double th = 6.283185307179586232, tl = 2.4492935982947064e-16;
+        const double q1 = N / th;
+        const double p = q1 * th, pe = fma(q1, th, -p);
+        const double r = (((double)N - p) - pe) - q1 * tl;
+        const double q2 = r / th;
+        const double hi = q1 + q2;
+        return make_double2(hi, q2 - (hi - q1));
+    };
+    k_prep<<<blocks, thr, 0, st>>>(theta, phi, chi, n, p.N1, p.N2, p.W, p.r_lo, p.R, p.pitch, p.spin, scale_of(p.N1),
+                                   scale_of(p.N2), key, idx, cell_u, frac_u, phase_u, p.flags);
     GSL_TRY(cudaGetLastError());
     const int ntc = (p.N2 + kTileC - 1) / kTileC;
     const uint64_t nkeys = (uint64_t)((p.R + kTileR - 1) / kTileR) * ntc;

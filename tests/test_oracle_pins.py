@@ -172,6 +172,50 @@ def test_high_l_underflow_region():
         assert abs(v[l] - r) < 1e-11
 
 
+def test_double_double_harmonics_against_mpmath():
+    """The double-double mode (used where FP64's own rounding, ~1e-12 at l ~ 5000,
+    would reach the target) against mpmath at l up to 4096: correct to ~1e-16 where
+    the FP64 recursion is off by up to ~1e-12; spin-2 values against the FP64 mode."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+
+    def ref(l, m, t):
+        nrm = mp.sqrt((2 * l + 1) / (4 * mp.pi) * mp.factorial(l - m) / mp.factorial(l + m))
+        return float(nrm * mp.legenp(l, m, mp.cos(t)))
+
+    worst64, worstdd = 0.0, 0.0
+    for m, t in [(0, 0.3), (30, 1.0), (500, 2.0), (1200, 0.9)]:
+        vd = O.slambda(4096, m, 0, t, precise=True)
+        v6 = O.slambda(4096, m, 0, t)
+        for l in [4096, 4095, 4089]:
+            r = ref(l, m, t)
+            worstdd = max(worstdd, abs(vd[l] - r) / abs(r))
+            worst64 = max(worst64, abs(v6[l] - r) / abs(r))
+    assert worstdd <= 1e-15 and worst64 > 10 * worstdd, (worstdd, worst64)
+    for s in (2, -2):
+        vd = O.slambda(300, 7, s, 1.3, precise=True)
+        v6 = O.slambda(300, 7, s, 1.3)
+        assert np.max(np.abs(vd - v6)) <= 1e-13 * np.max(np.abs(v6))
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_double_double_transforms_match_fp64_mode(spin):
+    """Same conventions in both modes: synthesis and adjoint agree to FP64 rounding
+    at a small band limit (the e^{im phi} recurrence and the start values included)."""
+    L = 40
+    th, ph, chi = W.random_points(60, 12)
+    nc = 1 if spin == 0 else 2
+    a = np.stack([W.draw_alm(W.cmb_cl(L, 30.0), L, 50 + k, spin=spin) for k in range(nc)])
+    c = chi if spin else None
+    m6 = O.synthesis(L, L, spin, th, ph, a, c)
+    md = O.synthesis(L, L, spin, th, ph, a, c, precise=True)
+    assert np.linalg.norm(md - m6) <= 1e-14 * np.linalg.norm(m6)
+    y = np.random.default_rng(3).standard_normal((nc, th.size))
+    a6 = O.adjoint(L, L, spin, th, ph, y, c)
+    ad = O.adjoint(L, L, spin, th, ph, y, c, precise=True)
+    assert np.linalg.norm(ad - a6) <= 1e-14 * np.linalg.norm(a6)
+
+
 # ----------------------------------------------------------- quadrature
 @pytest.mark.parametrize("s", [0, 1, 2, -2])
 def test_gauss_legendre_orthonormality(s):
