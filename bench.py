@@ -47,7 +47,7 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
 # source makes the entry stale and the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("legendre_adjoint/spin2/fp32", "ae41d6e7cfab"): 742155008,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
+    ("legendre_adjoint/spin2/fp32", "a263ead9553a"): 742960896,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
 }
 
 
@@ -389,10 +389,26 @@ def run_gpu(args):
                            "achieved": round(wk / (av * 1e-3) / (1e12 if bd == "alu" else 1e9), 3),
                            "unit": "TFLOP/s (FP64 ALU work)" if bd == "alu" else un})
         rows64.sort(key=lambda r: -r["ms_per_step"])
+        top64 = rows64[0]
+        if top64["bound"] == "alu":
+            # the FP64 plans' Legendre kernels run orders m >= m_df in double-float on the
+            # FP32 pipes and the orders below natively on the FP64 pipe
+            peak64 = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
+            note64 = ("FP32 FMA peak derived (152 SMs x 128 lanes x 2 flop x %.0f MHz): the double-float "
+                      "orders m >= m_df carry most of the work; the FP64 pipe's nominal rate is 1.25 TFLOP/s"
+                      % sm_mhz_max)
+        else:
+            peak64 = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+            note64 = "HBM copy bandwidth (%s)" % peak_src
+        roof64 = {"bound": top64["bound"], "achieved": top64["achieved"], "peak": round(peak64, 1),
+                  "unit": "TFLOP/s" if top64["bound"] == "alu" else "GB/s",
+                  "frac": round(top64["achieved"] / peak64, 4), "traffic": None,
+                  "kernel": "%s (spin %d, fp64)" % (top64["stage"], top64["spin"]),
+                  "avg_launch_ms": top64["avg_launch_ms"], "peak_source": note64}
         fp64 = {"value": round(world * npts / (ms64 * 1e-3), 1), "unit": "lensed points/s", "epsilon": 1e-10,
                 "ms_per_step": round(ms64, 3), "steps": k64, "per_transform": per_transform(qT, qP, c, reps=1),
                 "plan": {k: qT.info()[k] for k in ("n1", "W", "sigma")} | {"W_spin2": qP.info()["W"]},
-                "stages": rows64}
+                "roofline": roof64, "stages": rows64}
         qT.close(); qP.close()
 
     result = {

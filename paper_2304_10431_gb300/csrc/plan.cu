@@ -311,11 +311,16 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         sizes_for(lmax, mmax, p->M, sg, W, N1, N2);
         const size_t lim = force_cl == 1 ? fft_one : fft_max;
         if ((size_t)N1 > lim || (size_t)N2 > lim) continue;
-        // per-point taps + kernel evaluations, grid passes (FFT + interp); FFTs
-        // split over a two-CTA cluster cost more (remote shared-memory accesses)
-        const double pts = (double)npoints * ncomp * ((double)W * W + 16.0 * W);
+        // per-point taps (+ kernel evaluations in FP32 plans; FP64 plans keep the
+        // weights) against grid passes (FFTs).  Grid weight per cell, in taps, from
+        // the stage times at lmax 4096: ~12 in FP32, ~60 in FP64 (FP64 butterflies
+        // run on the narrow FP64 pipe).  FFTs split over a two-CTA cluster cost
+        // more (remote shared-memory accesses).
+        const bool f64 = prec == LENS_FP64;
+        const double pts = (double)npoints * ncomp * ((double)W * W + (f64 ? 0.0 : 16.0 * W));
         const double clf = ((size_t)N1 > fft_one || (size_t)N2 > fft_one) ? 1.5 : 1.0;
-        const double grd = clf * (12.0 * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1);
+        const double cell_w = f64 ? 60.0 : 12.0;
+        const double grd = clf * (cell_w * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1);
         const double cost = pts + grd;
         if (cost < best.cost) { best.cost = cost; best.sigma = sg; best.W = W; best.N1 = N1; best.N2 = N2; }
     }
