@@ -271,6 +271,44 @@ int lens_autotune(int lmax, int mmax, int spin, int64_t npoints, const double *t
                   double *best_ms);
 
 /*
+ * Intermediate grids for lensed harmonic coefficients (Sect. 4: remap onto a
+ * pixelization, then a standard backward SHT; no counterpart in the paper's
+ * interface).  A Gauss-Legendre grid: nrings rings at the roots of P_nrings
+ * (theta ascending), nphi equispaced longitudes phi_k = 2 pi k / nphi, point
+ * index ring * nphi + k.  weight_d (may be NULL) receives w_j 2 pi / nphi, so
+ * that the adjoint transform at the grid points applied to weight * map is the
+ * backward SHT, exact for band limits below nrings (and nphi > 2 lmax).
+ *   theta_d, phi_d, weight_d  device double [nrings * nphi].
+ * Synchronises the stream once (the ring table is computed on the host).
+ */
+int lens_gl_grid(int nrings, int nphi, double *theta_d, double *phi_d, double *weight_d, void *stream);
+
+/*
+ * out[c][i] = weight[i] * in[c][i] for c < ncomp, i < n (quadrature weights,
+ * magnification weights).  prec selects float or double values; in_d may equal
+ * out_d.
+ */
+int lens_scale_points(int64_t n, int ncomp, int prec, const double *weight_d, const void *in_d, void *out_d,
+                      void *stream);
+
+/*
+ * Magnification determinant |A| = |d^2 n' / d^2 n| of the remapping (App. B):
+ *   |A| = (sin a / a)((1 - kappa)^2 + omega^2 - |gamma|^2)
+ *       + (cos a - sin a / a)(1 - kappa - cos(2 beta) gamma_1 - sin(2 beta) gamma_2),
+ * kappa + i omega = ethbar(1alpha)/2, gamma = eth(1alpha)/2; for a deflection
+ * that is the gradient of phi, omega = 0, kappa is the spin-0 synthesis of
+ * l(l+1)/2 phi_lm and gamma the spin-2 synthesis of G = sqrt((l-1)l(l+1)(l+2))/2
+ * phi_lm, C = 0 (Eq. "forwardpol" convention).  Inverse lensing (App. B) is
+ * then lens_adjoint of T |A| (times quadrature weights).
+ *   p0, p2    FP64 plans of spin 0 and 2 on the observed (undeflected) points,
+ *             band limit of phi, no chi.
+ *   phi_lm_d  complex double [nalm];  alpha_d  double [2][npoints] (lens_deflection);
+ *   det_d     double [npoints] (written).
+ */
+int lens_magnification(lens_plan p0, lens_plan p2, const void *phi_lm_d, const double *alpha_d, double *det_d,
+                       void *stream);
+
+/*
  * The same two operations on host buffers: the inputs are copied to the
  * device, the transform runs, the outputs are copied back; returns after the
  * stream has finished.  Pinned host memory gives full copy bandwidth.

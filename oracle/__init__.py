@@ -278,3 +278,28 @@ def phi_gradient(lmax: int, spin: int, theta0, phi0, phi_lm, lmax_phi: int, x, g
     da = deflection_vjp(spin, alpha[0], alpha[1], g, p, a_up, b_down)
     adj = adjoint(lmax_phi, lmax_phi, 1, theta0, phi0, np.stack([da.real, da.imag]))
     return np.sqrt(ellp * (ellp + 1.0)) * _mweight(lmax_phi) * adj[0]
+
+
+# ---------------------------------------------------------------- App. B
+def magnification(theta, phi, phi_lm, lmax_phi: int) -> np.ndarray:
+    """Magnification determinant |A| = |d^2 n'/d^2 n| of the remapping (App. B):
+    (sin a / a)((1 - kappa)^2 - |gamma|^2) + (cos a - sin a / a)(1 - kappa - cos 2b gamma_1 - sin 2b gamma_2)
+    with kappa = ethbar(1alpha)/2 (spin-0 synthesis of l(l+1)/2 phi_lm), gamma = eth(1alpha)/2
+    (spin-2 synthesis of G = sqrt((l-1)l(l+1)(l+2))/2 phi_lm, C = 0), omega = 0 for a gradient
+    deflection, a = |alpha| and b the angle of alpha from e_theta towards e_phi."""
+    theta, phi = _f64(theta), _f64(phi)
+    L = lmax_phi
+    ell = _ell(L)
+    p = _c128(phi_lm)
+    kap = synthesis(L, L, 0, theta, phi, 0.5 * ell * (ell + 1.0) * p)[0]
+    gam = synthesis(L, L, 2, theta, phi,
+                    np.stack([0.5 * np.sqrt(np.maximum((ell - 1) * ell * (ell + 1) * (ell + 2), 0.0)) * p,
+                              np.zeros_like(p)]))
+    al = synthesis(L, L, 1, theta, phi, np.stack([np.sqrt(ell * (ell + 1.0)) * p, np.zeros_like(p)]))
+    a = np.hypot(al[0], al[1])
+    safe = np.where(a > 0, a, 1.0)
+    sa = np.where(a > 0, np.sin(a) / safe, 1.0)
+    ct, st = np.where(a > 0, al[0] / safe, 1.0), np.where(a > 0, al[1] / safe, 0.0)
+    c2b, s2b = ct * ct - st * st, 2 * ct * st
+    cma = np.where(a > 0, np.cos(a) - sa, 0.0)
+    return sa * ((1 - kap) ** 2 - (gam[0] ** 2 + gam[1] ** 2)) + cma * (1 - kap - c2b * gam[0] - s2b * gam[1])

@@ -23,8 +23,8 @@ import torch
 from . import _native
 from ._native import LensError, PlanInfo, PlanParams
 
-__all__ = ["LensPlan", "LensingModel", "LensBatch", "LensError", "synthesis", "adjoint", "lensed", "autotune",
-           "pointing", "nalm", "lib_path"]
+__all__ = ["LensPlan", "LensingModel", "LensedAlm", "LensBatch", "LensError", "synthesis", "adjoint", "lensed",
+           "autotune", "gl_grid", "scale_points", "pointing", "nalm", "lib_path"]
 
 _PREC = {"fp32": 0, "fp64": 1}
 
@@ -322,9 +322,93 @@ class LensingModel:
             g.data_ptr(), out.data_ptr(), _stream_handle(stream)))
         return out
 
+    def magnification(self, stream=None) -> torch.Tensor:
+        """|A| = |d^2 n' / d^2 n| at the undeflected points (App. B; lens_magnification)."""
+        if getattr(self, "_mag_plans", None) is None:
+            self._mag_plans = tuple(LensPlan(self.lmax_phi, self.theta0, self.phi0, spin=s, epsilon=1e-12,
+                                             precision="fp64", device=self.device) for s in (0, 2))
+        det = torch.empty(self.npoints, dtype=torch.float64, device=self.device)
+        _native.check(_native.load().lens_magnification(self._mag_plans[0].handle, self._mag_plans[1].handle,
+                                                        self.phi_lm.data_ptr(), self.alpha.data_ptr(),
+                                                        det.data_ptr(), _stream_handle(stream)))
+        return det
+
     def close(self):
         self._close_lensed()
         self.defl.close()
+        for pl in getattr(self, "_mag_plans", None) or ():
+            pl.close()
+        self._mag_plans = None
+
+
+class LensedAlm:
+    """Lensed harmonic coefficients (Sect. 4): the unlensed field (band limit lmax_unl)
+    is remapped onto a Gauss-Legendre grid (nrings x nphi) by the lensing synthesis, and
+    a backward SHT (the adjoint at the grid points times the quadrature weights) returns
+    the coefficients up to lmax_len.  adjoint() is the exact transpose (a forward SHT onto
+    the grid, weights, then the adjoint remapping); inverse() is App. B's inverse lensing
+    of a lensed map on the grid, the adjoint applied to the map times |A|."""
+
+    def __init__(self, lmax_unl: int, lmax_len: int, spin: int = 0, lmax_phi: int | None = None,
+                 nrings: int | None = None, nphi: int | None = None, epsilon: float = 1e-5,
+                 precision: str = "fp32", device=None):
+        self.nrings = int(nrings or lmax_len + 1 + lmax_len // 2)
+        self.nphi = int(nphi or 2 * self.nrings)
+        if self.nrings <= lmax_len or self.nphi <= 2 * lmax_len:
+            raise ValueError("the grid must resolve lmax_len: nrings > lmax_len and nphi > 2 lmax_len")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.theta, self.phi, self.weight = gl_grid(self.nrings, self.nphi, device=dev)
+        self.model = LensingModel(lmax_unl, self.theta, self.phi, spin=spin, lmax_phi=lmax_phi, epsilon=epsilon,
+                                  precision=precision, device=dev)
+        self.analysis = LensPlan(lmax_len, self.theta, self.phi, spin=spin, epsilon=epsilon, precision=precision,
+                                 device=dev)
+
+    def set_phi(self, phi_lm: torch.Tensor):
+        self.model.set_phi(phi_lm)
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        d = self.model.forward(x)
+        return self.analysis.adjoint(scale_points(self.weight, d, out=d))
+
+    def adjoint(self, a: torch.Tensor) -> torch.Tensor:
+        m = self.analysis.synthesis(a)
+        return self.model.lensed.adjoint(scale_points(self.weight, m, out=m))
+
+    def inverse(self, d: torch.Tensor) -> torch.Tensor:
+        """Unlensed coefficients (lmax_unl) of a lensed map d on the grid (App. B)."""
+        t = scale_points(self.weight, d)
+        return self.model.lensed.adjoint(scale_points(self.model.magnification(), t, out=t))
+
+    def close(self):
+        self.model.close()
+        self.analysis.close()
+
+
+def gl_grid(nrings: int, nphi: int, device=None, stream=None):
+    """Gauss-Legendre grid (lens_gl_grid): theta, phi and quadrature weights w_j 2 pi / nphi
+    (FP64 device tensors of nrings * nphi points, ring-major)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    n = int(nrings) * int(nphi)
+    th = torch.empty(n, dtype=torch.float64, device=dev)
+    ph = torch.empty_like(th)
+    w = torch.empty_like(th)
+    with torch.cuda.device(dev):
+        _native.check(_native.load().lens_gl_grid(int(nrings), int(nphi), th.data_ptr(), ph.data_ptr(), w.data_ptr(),
+                                                  _stream_handle(stream)))
+    return th, ph, w
+
+
+def scale_points(weight: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """out[c, i] = weight[i] x[c, i] (lens_scale_points); x real [ncomp, n] or [n]."""
+    x = x.contiguous()
+    n = weight.numel()
+    ncomp = x.numel() // n if n else 1
+    if out is None:
+        out = torch.empty_like(x)
+    prec = 0 if x.dtype == torch.float32 else 1
+    _native.check(_native.load().lens_scale_points(n, ncomp, prec, weight.data_ptr(), x.data_ptr(), out.data_ptr(),
+                                                   _stream_handle(stream)))
+    return out
 
 
 class _Lensed(torch.autograd.Function):

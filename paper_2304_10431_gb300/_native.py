@@ -33,6 +33,9 @@ EXPORTS = {
     "lens_batch_info": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_batch_destroy": (_i32, [_vp]),
     "lens_autotune": (_i32, [_i32, _i32, _i32, _i64, _vp, _vp, _vp, _f64, _i32, _vp, _i32, _vp, _vp]),
+    "lens_gl_grid": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp]),
+    "lens_scale_points": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "lens_magnification": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),

@@ -470,3 +470,26 @@ def test_eth_coefficients_against_derivatives():
     dth = (8 * (P(th + h) - P(th - h)) - (P(th + 2 * h) - P(th - 2 * h))) / (12 * h)
     got = -0.5 * ((up[0] + 1j * up[1]) + (dn[0] + 1j * dn[1]))
     assert np.max(np.abs(got - dth)) <= 1e-8 * np.max(np.abs(dth))
+
+
+def test_magnification_is_the_area_ratio_of_the_remapping():
+    """App. B's determinant formula against the area ratio of the pointing map
+    n -> n' computed by central differences of the oracle's own deflection and
+    pointing (0.05 rad rms deflection, so |A| - 1 is a few per cent)."""
+    L = 16
+    phi = _phi_scaled(L, 21, 0.05)
+    th = np.array([0.5, 1.0, 1.6, 2.2, 2.8])
+    ph = np.array([0.3, 2.0, 4.0, 5.0, 1.0])
+    det = O.magnification(th, ph, phi, L)
+    h = 1e-5
+
+    def npv(t, p):
+        t2, p2, _ = O.deflected_points(t, p, phi, L)
+        return np.stack([np.sin(t2) * np.cos(p2), np.sin(t2) * np.sin(p2), np.cos(t2)], axis=-1)
+
+    dt = (npv(th + h, ph) - npv(th - h, ph)) / (2 * h)
+    dp = (npv(th, ph + h) - npv(th, ph - h)) / (2 * h)
+    n2 = npv(th, ph)
+    area = np.abs(np.sum(np.cross(dt, dp) * n2, axis=-1)) / np.sin(th)
+    assert np.max(np.abs(det - 1)) > 1e-3  # the test is not trivial
+    assert np.max(np.abs(det - area)) <= 1e-8, (det, area)
