@@ -63,8 +63,10 @@ struct Plan {
 
     // tables (device)
     // monic-form recursion coefficients per alm index: alpha and (spin s) tau,
-    // as df32 float2 (FP32 plans) or double (FP64 plans); FP64 plans with
-    // m_df <= mmax also hold df32 copies.  scale: c_l (double, per alm index).
+    // as df32 (FP32 plans: float2 alpha, or for spin s float4 (alpha, tau) in
+    // rec_a) or double (FP64 plans: rec_a, rec_t); FP64 plans with m_df <= mmax
+    // also hold the df32 table in rec_a_df (rec_t_df unused).  scale: c_l
+    // (double, per alm index).
     void *rec_a = nullptr, *rec_t = nullptr;
     void *rec_a_df = nullptr, *rec_t_df = nullptr;
     double *scale = nullptr;

@@ -382,13 +382,15 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     cudaError_t e;
     // ---- device buffers
     if ((e = B.alloc((void **)&p->flags, sizeof(unsigned) * 4, false)) != cudaSuccess) return bailc(e, "alloc flags");
-    if ((e = B.alloc(&p->rec_a, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_a");
-    if (spin && (e = B.alloc(&p->rec_t, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_t");
+    // FP32 spin plans interleave alpha and tau in rec_a (16 bytes per entry)
+    const size_t ra_b = (prec == LENS_FP32 && spin) ? 16 : 8;
+    if ((e = B.alloc(&p->rec_a, (size_t)p->nalm * ra_b, false)) != cudaSuccess) return bailc(e, "alloc rec_a");
+    if (spin && prec == LENS_FP64 && (e = B.alloc(&p->rec_t, (size_t)p->nalm * 8, false)) != cudaSuccess)
+        return bailc(e, "alloc rec_t");
     if ((e = B.alloc((void **)&p->scale, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc scale");
     if (prec == LENS_FP64 && p->m_df <= mmax) {
-        if ((e = B.alloc(&p->rec_a_df, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc rec_a_df");
-        if (spin && (e = B.alloc(&p->rec_t_df, (size_t)p->nalm * 8, false)) != cudaSuccess)
-            return bailc(e, "alloc rec_t_df");
+        if ((e = B.alloc(&p->rec_a_df, (size_t)p->nalm * (spin ? 16 : 8), false)) != cudaSuccess)
+            return bailc(e, "alloc rec_a_df");
     }
     if ((e = B.alloc(&p->coef, (size_t)p->nalm * esz * ncomp, true)) != cudaSuccess) return bailc(e, "alloc coef");
     if ((e = B.alloc(&p->ring, esz * (size_t)p->ncol * p->ntheta, true)) != cudaSuccess) return bailc(e, "alloc ring");

@@ -57,7 +57,7 @@ template <> __device__ __forceinline__ Buf<double2, 2> make_buf<double2, 2>(doub
 
 // ----------------------------------------------------------------- theta fwd
 template <typename T, int CL>
-__global__ void __launch_bounds__(1024) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
+__global__ void __launch_bounds__(512) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
                                                     int spin, int ncol, int r_lo, int R, int chunk)
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(const cplx<T> *__restrict__ 
 
 // ----------------------------------------------------------------- theta adj
 template <typename T, int CL>
-__global__ void __launch_bounds__(1024) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
+__global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
                                                     int spin, int ncol, int r_lo, int R, int chunk)
