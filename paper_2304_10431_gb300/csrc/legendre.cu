@@ -116,6 +116,22 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
     static __device__ __forceinline__ X mul(X a, X b) { return df_mul(a, b); }
     static __device__ __forceinline__ X add(X a, X b) { return df_add_u(a, b); }
     static __device__ __forceinline__ X sub(X a, X b) { return df_sub_u(a, b); }
+    // alpha x +- tau: Fast2Sum on the high words (exact when |alpha x| >= |tau|,
+    // i.e. everywhere except on rings within ~m / l^2 of the equator, where the
+    // step coefficient then carries an FP32-size error: negligible for the
+    // FP32 plans' 2e-6 floor), plus the low words.
+    static __device__ __forceinline__ X addx(X a, X t)
+    {
+        const float s = __fadd_rn(a.h, t.h);
+        const float e = __fsub_rn(t.h, __fsub_rn(s, a.h));
+        return {s, __fadd_rn(e, __fadd_rn(a.l, t.l))};
+    }
+    static __device__ __forceinline__ X subx(X a, X t)
+    {
+        const float s = __fsub_rn(a.h, t.h);
+        const float e = __fsub_rn(__fsub_rn(a.h, s), t.h);
+        return {s, __fadd_rn(e, __fsub_rn(a.l, t.l))};
+    }
     // new = y q - p, written over p
     static __device__ __forceinline__ void step(df32 &p, const df32 &q, X y) { p = df_sub_u(df_mul(y, q), p); }
     // The words are not renormalised after every step (the low word carries
@@ -211,6 +227,8 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static __device__ __forceinline__ X mul(X a, X b) { return a * b; }
     static __device__ __forceinline__ X add(X a, X b) { return a + b; }
     static __device__ __forceinline__ X sub(X a, X b) { return a - b; }
+    static __device__ __forceinline__ X addx(X a, X t) { return a + t; }
+    static __device__ __forceinline__ X subx(X a, X t) { return a - t; }
     static __device__ __forceinline__ void step(double &p, const double &q, X y) { p = __fma_rn(y, q, -p); }
     static __device__ __forceinline__ V val(const double &a) { return a; }
     static __device__ __forceinline__ void renorm(St &) {}
@@ -281,6 +299,9 @@ struct PolDD : PolDF {
     using K = df32;
     using A = df32;
     static __device__ __forceinline__ V val(const df32 &a) { return a; }
+    // FP64 plans: the step coefficients keep full double-float accuracy
+    static __device__ __forceinline__ X addx(X a, X t) { return df_add_u(a, t); }
+    static __device__ __forceinline__ X subx(X a, X t) { return df_sub_u(a, t); }
     // start mantissa to df32 accuracy (exp2 in FP64, split in two words)
     static __device__ __forceinline__ void start(St &s, double L2, int sign, bool zero)
     {
@@ -416,8 +437,8 @@ template <class P, int RPT, bool SPIN> struct Rings {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const typename P::X ax = P::mul(al, x[k]);
-                P::step(sp[k].w[NW], sp[k].w[1 - NW], P::add(ax, t));
-                P::step(sm[k].w[NW], sm[k].w[1 - NW], P::sub(ax, t));
+                P::step(sp[k].w[NW], sp[k].w[1 - NW], P::addx(ax, t));
+                P::step(sm[k].w[NW], sm[k].w[1 - NW], P::subx(ax, t));
                 if (CHECK) { P::rescale(sp[k], NW); P::rescale(sm[k], NW); }
             }
         }
