@@ -47,7 +47,7 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
 # source makes the entry stale and the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("legendre_adjoint/spin2/fp32", "a263ead9553a"): 742960896,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
+    ("legendre_adjoint/spin2/fp32", "3b189f72a88f"): 740843776,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
 }
 
 
@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--scan", default=None,
+                    help="N_side x lmax scan (the paper's Fig. 4): comma list of NSIDE:LMAX pairs; prints one JSON "
+                         "line per pair and precision instead of the benchmark line")
+    ap.add_argument("--scan-eps", default="fp32:1e-5,fp64:1e-13")
     return ap.parse_args()
 
 
@@ -513,9 +517,56 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_scan(args):
+    """Forward + adjoint time of one spin-0 and one spin-2 map per (N_side, lmax) pair, on
+    HEALPix centres displaced by 2.5 arcmin (the paper's Fig. 4 grid, one GPU)."""
+    import torch
+    from paper_2304_10431_gb300 import LensPlan
+    from paper_2304_10431_gb300 import workloads as Wk
+    dev = torch.device("cuda:0")
+    precs = [(q.split(":")[0], float(q.split(":")[1])) for q in args.scan_eps.split(",")]
+    for pair in args.scan.split(","):
+        nside, lmax = (int(v) for v in pair.split(":"))
+        th0, ph0 = Wk.healpix_centres(nside)
+        th, ph, chi = Wk.displaced_points(th0, ph0, 2.5, seed=nside)
+        for prec, eps in precs:
+            row = {"scan": "nside x lmax", "nside": nside, "lmax": lmax, "npoints": int(th.size),
+                   "precision": prec, "epsilon": eps}
+            try:
+                for spin in (0, 2):
+                    plan = LensPlan(lmax, th, ph, chi if spin else None, spin=spin, epsilon=eps, precision=prec,
+                                    device=dev)
+                    nc = plan.ncomp
+                    a = torch.zeros(nc, plan.nalm, dtype=plan.complex_dtype, device=dev)
+                    a.real.normal_()
+                    m = plan.synthesis(a)
+                    plan.adjoint(m, out=a)  # warm-up
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    torch.cuda.synchronize()
+                    ev[0].record()
+                    plan.synthesis(a, out=m)
+                    ev[1].record()
+                    plan.adjoint(m, out=a)
+                    ev[2].record()
+                    torch.cuda.synchronize()
+                    inf = plan.info()
+                    row["spin%d" % spin] = {"synthesis_s": round(ev[0].elapsed_time(ev[1]) * 1e-3, 4),
+                                            "adjoint_s": round(ev[1].elapsed_time(ev[2]) * 1e-3, 4),
+                                            "W": inf["W"], "sigma": round(inf["sigma"], 3),
+                                            "plan_GB": round((inf["plan_bytes"] + inf["workspace_bytes"]) / 1e9, 2)}
+                    plan.close()
+                    del a, m
+                    torch.cuda.empty_cache()
+            except Exception as exc:  # a configuration outside this build's limits
+                row["error"] = str(exc)
+            print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.scan:
+        run_scan(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
