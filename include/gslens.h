@@ -85,8 +85,8 @@ typedef struct {
     int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (1 or 2) */
     int legendre_df32_mmin; /* FP64 plans: orders m >= this value use the double-float Legendre
                                recursion (0 = choose, -1 = never) */
-    int fft_cluster;        /* CTAs per FFT vector: 0 = choose (1, or a cluster of 2 when the
-                               vector exceeds one CTA's shared memory), 1 or 2 to force */
+    int fft_cluster;        /* CTAs per FFT vector: 0 = choose (1, or a cluster of 2 or 4 when
+                               the vector exceeds one CTA's shared memory), 1, 2 or 4 to force */
 } lens_plan_params;
 
 typedef struct {

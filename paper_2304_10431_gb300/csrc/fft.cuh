@@ -12,9 +12,9 @@
 // DIR = -1: forward, sum x_n e^{-2 pi i nk/N};  DIR = +1: inverse (unnormalised).
 //
 // Vectors longer than one CTA's shared memory are split over a cluster of
-// two CTAs (Blackwell distributed shared memory): elements [0, chunk) live in
-// rank 0's shared memory and [chunk, N) in rank 1's, the butterflies of both
-// CTAs address either half through the cluster's shared window, and the
+// two or four CTAs (Blackwell distributed shared memory): elements
+// [r chunk, (r+1) chunk) live in rank r's shared memory, the butterflies of
+// all CTAs address any part through the cluster's shared window, and the
 // stage barrier is a cluster barrier.  Team<CL> and Buf<C, CL> hide the
 // difference; CL = 1 is the plain single-CTA path.
 #pragma once
@@ -34,16 +34,17 @@ template <> struct Team<1> {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ int vec() const { return blockIdx.x; }
 };
-template <> struct Team<2> {
+template <int CL> struct Team {  // CL = 2 or 4: a cluster of CL CTAs
+    static_assert(CL == 2 || CL == 4, "teams of 1, 2 or 4 CTAs");
     int tid, nthr;
     __device__ Team()
     {
         const int rank = (int)cooperative_groups::this_cluster().block_rank();
         tid = rank * blockDim.x + threadIdx.x;
-        nthr = 2 * blockDim.x;
+        nthr = CL * blockDim.x;
     }
     __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
-    __device__ __forceinline__ int vec() const { return blockIdx.x >> 1; }
+    __device__ __forceinline__ int vec() const { return blockIdx.x / CL; }
 };
 
 // Element access of the vector: a shared-memory array, or two halves.
@@ -63,6 +64,23 @@ template <typename C> struct Buf<C, 2> {
         p1 = cl.map_shared_rank(local, 1);
     }
     __device__ __forceinline__ C &operator[](int i) const { return i < chunk ? p0[i] : p1[i - chunk]; }
+};
+template <typename C> struct Buf<C, 4> {
+    C *p0, *p1, *p2, *p3;
+    int chunk;
+    __device__ Buf(C *local, int chunk_) : chunk(chunk_)
+    {
+        auto cl = cooperative_groups::this_cluster();
+        p0 = cl.map_shared_rank(local, 0);
+        p1 = cl.map_shared_rank(local, 1);
+        p2 = cl.map_shared_rank(local, 2);
+        p3 = cl.map_shared_rank(local, 3);
+    }
+    __device__ __forceinline__ C &operator[](int i) const
+    {
+        if (i < 2 * chunk) return i < chunk ? p0[i] : p1[i - chunk];
+        return i < 3 * chunk ? p2[i - 2 * chunk] : p3[i - 3 * chunk];
+    }
 };
 
 template <typename T> struct FftConst;

@@ -295,10 +295,11 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // plans and eps/4 in FP32 plans, where FP32 rounding in the Legendre sums and
     // the FFTs takes ~1e-6 at lmax ~ 4096.  sigma is then picked by a cost model.
     const size_t esz = prec == LENS_FP32 ? 8 : 16;
-    // one CTA holds fft_one elements; a cluster of two CTAs twice that
-    const size_t fft_one = kSmemLimit / esz, fft_max = 2 * fft_one;
+    // one CTA holds fft_one elements; a cluster of two or four CTAs 2x or 4x that
+    const size_t fft_one = kSmemLimit / esz, fft_max = 4 * fft_one;
     const int force_cl = prm ? prm->fft_cluster : 0;
-    if (force_cl < 0 || force_cl > 2) return bail(LENS_ERR_INVALID, "fft_cluster must be 0, 1 or 2");
+    if (force_cl != 0 && force_cl != 1 && force_cl != 2 && force_cl != 4)
+        return bail(LENS_ERR_INVALID, "fft_cluster must be 0, 1, 2 or 4");
     const double eps_nufft = (prec == LENS_FP32 ? 0.25 : 0.5) * epsilon;
     const int ncomp = spin ? 2 : 1;
     Choice best;
@@ -309,7 +310,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if (W > 16) continue;
         int N1, N2;
         sizes_for(lmax, mmax, p->M, sg, W, N1, N2);
-        const size_t lim = force_cl == 1 ? fft_one : fft_max;
+        const size_t lim = force_cl ? force_cl * fft_one : fft_max;
         if ((size_t)N1 > lim || (size_t)N2 > lim) continue;
         // per-point taps (+ kernel evaluations in FP32 plans; FP64 plans keep the
         // weights) against grid passes (FFTs).  Grid weight per cell, in taps, from
@@ -318,7 +319,8 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         // more (remote shared-memory accesses).
         const bool f64 = prec == LENS_FP64;
         const double pts = (double)npoints * ncomp * ((double)W * W + (f64 ? 0.0 : 16.0 * W));
-        const double clf = ((size_t)N1 > fft_one || (size_t)N2 > fft_one) ? 1.5 : 1.0;
+        const size_t nmax = std::max<size_t>(N1, N2);
+        const double clf = nmax > 2 * fft_one ? 2.0 : nmax > fft_one ? 1.5 : 1.0;
         const double cell_w = f64 ? 60.0 : 12.0;
         const double grd = clf * (cell_w * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1);
         const double cost = pts + grd;
@@ -337,10 +339,13 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     p->W = best.W;
     p->N1 = best.N1;
     p->N2 = best.N2;
-    p->cl_theta = (force_cl == 2 || (size_t)std::max(p->N1, p->M) > fft_one) ? 2 : 1;
-    p->cl_phi = (force_cl == 2 || (size_t)p->N2 > fft_one) ? 2 : 1;
-    if (force_cl == 1 && (p->cl_theta == 2 || p->cl_phi == 2))
-        return bail(LENS_ERR_UNSUPPORTED, "FFT length above one CTA's shared memory with fft_cluster = 1");
+    {  // CTAs per FFT vector: the fewest of 1, 2, 4 that hold it (or the forced count)
+        auto team = [&](size_t n) { return n <= fft_one ? 1 : n <= 2 * fft_one ? 2 : 4; };
+        p->cl_theta = force_cl ? force_cl : team((size_t)std::max(p->N1, p->M));
+        p->cl_phi = force_cl ? force_cl : team((size_t)p->N2);
+        if ((size_t)std::max(p->N1, p->M) > (size_t)p->cl_theta * fft_one || (size_t)p->N2 > (size_t)p->cl_phi * fft_one)
+            return bail(LENS_ERR_UNSUPPORTED, "FFT length above the forced fft_cluster's shared memory");
+    }
     {
         const double s1 = (double)p->N1 / (2 * lmax + 2), s2 = (double)p->N2 / (2 * mmax + 2);
         p->sigma = std::min(s1, s2);
@@ -407,9 +412,12 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
             return bailc(e, "alloc tile table");
         if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
         // FP64 plans keep the 2W kernel weights of every point (GB300's FP64 pipe makes
-        // evaluating exp/sqrt per tap far dearer than reading 16 W bytes per point)
-        if (prec == LENS_FP64 &&
-            (e = B.alloc((void **)&p->wts, sizeof(double) * 2 * (size_t)p->W * npoints, false)) != cudaSuccess)
+        // evaluating exp/sqrt per tap far dearer than reading 16 W bytes per point),
+        // unless the table would exceed 48 GB (e.g. 805M points at W = 16: 206 GB);
+        // then the taps are evaluated per call
+        const size_t wbytes = sizeof(double) * 2 * (size_t)p->W * npoints;
+        if (prec == LENS_FP64 && wbytes <= (size_t)48 << 30 &&
+            (e = B.alloc((void **)&p->wts, wbytes, false)) != cudaSuccess)
             return bailc(e, "alloc weights");
     }
 

@@ -48,12 +48,20 @@ template <> __device__ __forceinline__ Buf<double2, 2> make_buf<double2, 2>(doub
 {
     return Buf<double2, 2>(l, ch);
 }
+template <> __device__ __forceinline__ Buf<float2, 4> make_buf<float2, 4>(float2 *l, int ch)
+{
+    return Buf<float2, 4>(l, ch);
+}
+template <> __device__ __forceinline__ Buf<double2, 4> make_buf<double2, 4>(double2 *l, int ch)
+{
+    return Buf<double2, 4>(l, ch);
+}
 
 // Every kernel below is written for a team of CL CTAs sharing one vector
-// (fft.cuh): CL = 1 is one CTA with the vector in its shared memory, CL = 2 a
-// cluster of two CTAs holding `chunk` elements each.  Teams of two start with
-// a cluster barrier (both CTAs resident before any remote access) and end
-// with one (no CTA exits while its partner may still read its half).
+// (fft.cuh): CL = 1 is one CTA with the vector in its shared memory, CL = 2 or
+// 4 a cluster of CTAs holding `chunk` elements each.  Cluster teams start
+// with a cluster barrier (all CTAs resident before any remote access) and end
+// with one (no CTA exits while a partner may still read its part).
 
 // ----------------------------------------------------------------- theta fwd
 template <typename T, int CL>
@@ -314,7 +322,7 @@ cudaError_t theta_fwd_t(const Plan &p, const void *ring, void *X, cudaStream_t s
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
-    return p.cl_theta == 2 ? args(k_theta_fwd<T, 2>) : args(k_theta_fwd<T, 1>);
+    return p.cl_theta == 4 ? args(k_theta_fwd<T, 4>) : p.cl_theta == 2 ? args(k_theta_fwd<T, 2>) : args(k_theta_fwd<T, 1>);
 }
 
 template <typename T>
@@ -328,7 +336,7 @@ cudaError_t theta_adj_t(const Plan &p, const void *X, void *ring, cudaStream_t s
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
-    return p.cl_theta == 2 ? args(k_theta_adj<T, 2>) : args(k_theta_adj<T, 1>);
+    return p.cl_theta == 4 ? args(k_theta_adj<T, 4>) : p.cl_theta == 2 ? args(k_theta_adj<T, 2>) : args(k_theta_adj<T, 1>);
 }
 
 template <typename T, bool SPIN>
@@ -342,7 +350,9 @@ cudaError_t phi_fwd_t(const Plan &p, const void *X, void *grid, cudaStream_t st)
         return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const C *)X, grid, p.fN2, p.mmax, p.ncol,
                            p.R, p.pitch, p.W, chunk);
     };
-    return p.cl_phi == 2 ? args(k_phi_fwd<T, SPIN, 2>) : args(k_phi_fwd<T, SPIN, 1>);
+    return p.cl_phi == 4   ? args(k_phi_fwd<T, SPIN, 4>)
+           : p.cl_phi == 2 ? args(k_phi_fwd<T, SPIN, 2>)
+                           : args(k_phi_fwd<T, SPIN, 1>);
 }
 
 template <typename T, bool SPIN>
@@ -356,7 +366,9 @@ cudaError_t phi_adj_t(const Plan &p, const void *grid, void *X, cudaStream_t st)
         return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const void *)grid, (C *)X, p.fN2, p.mmax,
                            p.ncol, p.R, p.pitch, p.W, chunk);
     };
-    return p.cl_phi == 2 ? args(k_phi_adj<T, SPIN, 2>) : args(k_phi_adj<T, SPIN, 1>);
+    return p.cl_phi == 4   ? args(k_phi_adj<T, SPIN, 4>)
+           : p.cl_phi == 2 ? args(k_phi_adj<T, SPIN, 2>)
+                           : args(k_phi_adj<T, SPIN, 1>);
 }
 
 }  // namespace

@@ -273,25 +273,26 @@ def test_deflection_field_on_gpu():
     assert rel(a, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("cl", [2, 4])
 @pytest.mark.parametrize("spin,prec,eps", [(0, "fp32", 1e-5), (2, "fp32", 1e-5), (0, "fp64", 1e-10),
                                            (2, "fp64", 1e-10)])
-def test_cluster_fft_matches_single_cta(spin, prec, eps):
-    """FFT vectors split over a two-CTA cluster (distributed shared memory), forced at
-    a size where one CTA would do, give the single-CTA results and the oracle's."""
+def test_cluster_fft_matches_single_cta(spin, prec, eps, cl):
+    """FFT vectors split over a cluster of two or four CTAs (distributed shared memory),
+    forced at a size where one CTA would do, give the single-CTA results and the oracle's."""
     L = 300
     th, ph, chi = W.random_points(40000, 321)
     nc = 1 if spin == 0 else 2
     a = np.stack([W.draw_alm(W.cmb_cl(L, 200.0), L, 900 + k, spin=spin) for k in range(nc)])
     y = np.random.default_rng(4).standard_normal((nc, th.size))
     out = {}
-    for cl in (1, 2):
-        plan = LensPlan(L, th, ph, chi if spin else None, spin=spin, epsilon=eps, precision=prec, fft_cluster=cl,
+    for c in (1, cl):
+        plan = LensPlan(L, th, ph, chi if spin else None, spin=spin, epsilon=eps, precision=prec, fft_cluster=c,
                         device=DEV)
-        out[cl] = (plan.synthesis(gpu_alm(plan, a)).cpu().numpy(),
-                   plan.adjoint(torch.as_tensor(y, dtype=plan.real_dtype, device=DEV)).cpu().numpy())
+        out[c] = (plan.synthesis(gpu_alm(plan, a)).cpu().numpy(),
+                  plan.adjoint(torch.as_tensor(y, dtype=plan.real_dtype, device=DEV)).cpu().numpy())
         plan.close()
     tol = 1e-6 if prec == "fp32" else 1e-13
-    assert rel(out[2][0], out[1][0]) <= tol and rel(out[2][1], out[1][1]) <= tol
+    assert rel(out[cl][0], out[1][0]) <= tol and rel(out[cl][1], out[1][1]) <= tol
     s = np.arange(0, th.size, 157)
     ref = O.synthesis(L, L, spin, th[s], ph[s], a, chi[s] if spin else None)
-    assert rel(out[2][0][:, s], ref) <= eps
+    assert rel(out[cl][0][:, s], ref) <= eps
