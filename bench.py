@@ -355,17 +355,27 @@ def run_gpu(args):
             pP.synthesis_host(hP, o_mP)
             pP.adjoint_host(hmP, o_aP)
 
-        for _ in range(2):
+        for _ in range(max(args.warmup, 3)):
             hstep()
         barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
+        # wall time of every step (each host call returns after its stream finished);
+        # the median over the steps, max over ranks, is the reported figure
+        times = []
+        for _ in range(max(args.steps, 10)):
+            t0 = time.perf_counter()
             hstep()
-        barrier()
-        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+            barrier()
+            times.append((time.perf_counter() - t0) * 1e3)
+        ems = float(np.median(times))
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
         h2d = sum(x.numel() * x.element_size() for x in (hT, hP, hmT, hmP))
         e2e = {"value": round(world * npts / (ems * 1e-3), 1), "unit": "lensed points/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3),
+               "statistic": "median of %d steps" % len(times), "ms_mean": round(float(np.mean(times)), 3),
+               "ms_min": round(float(np.min(times)), 3), "ms_max": round(float(np.max(times)), 3)}
 
     # ---------------- FP64 plans (epsilon 1e-10), same geometry
     fp64 = None

@@ -142,8 +142,18 @@ int lens_plan_info(lens_plan p, lens_plan_info_t *info);
  *   map_d  device [nmaps][ncomp][npoints] real
  * Entries with l < spin are ignored.  Imaginary parts of m = 0 entries are
  * ignored (real fields).
+ * FP32 plans with nmaps >= 2 synthesise the Legendre step of four (then two)
+ * maps in one pass that shares the recursion among them; the first such call
+ * allocates a workspace of 4 x (ring + a_lm) bytes on the plan (outside a
+ * stream capture only; inside one, or if the allocation fails, the maps run
+ * one by one).  The result equals the per-map result up to FP32 rounding
+ * order (identical arithmetic per map).
  */
 int lens_synthesis(lens_plan p, const void *alm_d, void *map_d, int nmaps, void *stream);
+
+/* Turns the grouped multi-map synthesis above on (on != 0, the default) or off
+ * for this plan.  Returns LENS_ERR_INVALID for a NULL plan. */
+int lens_plan_set_grouping(lens_plan p, int on);
 
 /*
  * Adjoint lensing (Sect. 2 Eq. "adjoint" and its spin-s form; Sect. 3 adjoint

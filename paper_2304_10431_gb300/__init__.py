@@ -98,6 +98,11 @@ class LensPlan:
         _native.check(_native.load().lens_plan_info(self._h, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
 
+    def set_grouping(self, on: bool):
+        """FP32 plans: synthesise several maps per call with a shared Legendre
+        recursion (default on); off runs every map alone."""
+        _native.check(_native.load().lens_plan_set_grouping(self._h, 1 if on else 0))
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _native.load().lens_plan_destroy(self._h)

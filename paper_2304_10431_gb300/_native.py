@@ -19,6 +19,7 @@ EXPORTS = {
                                    _vp, _vp]),
     "lens_plan_destroy": (_i32, [_vp]),
     "lens_plan_info": (_i32, [_vp, _vp]),
+    "lens_plan_set_grouping": (_i32, [_vp, _i32]),
     "lens_synthesis": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp]),

@@ -59,6 +59,7 @@ struct Plan {
     // every order in df32 (m_df = 0).
     struct LegShape { int rpt = 0, warps = 0, chunks = 0; };
     LegShape leg_f, leg_a, leg_fd, leg_ad;
+    LegShape leg_fb[2];  // FP32 forward sharing the recursion among 2 / 4 maps
     int m_df = 0;
 
     // tables (device)
@@ -72,6 +73,10 @@ struct Plan {
     double *scale = nullptr;
     void *coef = nullptr;     // workspace: forward coefficients c_l a_lm of one call
                               // ([ncomp][nalm], float2 / double2 / df32 float4)
+    // FP32 plans, several maps per call: ring coefficients and prepared
+    // coefficients of up to 4 maps, allocated on the first such call
+    void *ring_batch = nullptr, *coef_batch = nullptr;
+    bool group_maps = true;  // false: every map runs alone (lens_plan_set_grouping)
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;
     void *w1 = nullptr;       // [2 lmax + 1]  1/psihat(2 pi k / N1), k = -lmax..lmax
@@ -101,7 +106,7 @@ struct Plan {
     int nallocs = 0;
 };
 
-Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt);
+Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int nm = 1);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);
@@ -109,6 +114,10 @@ cudaError_t launch_rec_tables(Plan &p);
 // gradient entry points use 1/2 forward and 2 adjoint)
 cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st, double wpos = 1.0);
 cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st, double wpos = 1.0);
+// FP32 plans: Legendre synthesis of nm = 2 or 4 maps (a_lm consecutive) sharing
+// one recursion; ring and coef hold nm maps' ring / prepared coefficients
+cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring, void *coef, int nm, cudaStream_t st,
+                                      double wpos);
 cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st);
 cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st);
 cudaError_t launch_phi_fwd(const Plan &p, const void *X, void *grid, cudaStream_t st);

@@ -481,10 +481,12 @@ template <class P, int RPT, bool SPIN> struct Rings {
 //   spin s: (r0, i0) = sum a s-lambda (north, +m), (r1, i1) = sum rel a (-s)lambda
 //           (south, +m), (r2, i2) = sum b (-s)lambda (north, -m), (r3, i3) =
 //           sum rel b s-lambda (south, -m); the south sums are multiplied by s0.
-template <class P, int RPT, bool SPIN> struct FwdAcc {
+template <class P, int RPT, bool SPIN, int NM = 1> struct FwdAcc {
+    // NM maps share the recursion: map b's prepared coefficients start at
+    // tab + b * (ncomp nalm) entries and it has its own accumulators
     using A = typename P::A;
     using K = typename P::K;
-    A r0[RPT], i0[RPT], r1[RPT], i1[RPT], r2[RPT], i2[RPT], r3[RPT], i3[RPT];
+    A r0[NM][RPT], i0[NM][RPT], r1[NM][RPT], i1[NM][RPT], r2[NM][RPT], i2[NM][RPT], r3[NM][RPT], i3[NM][RPT];
     const void *tab;
     int64_t nalm, base;
 
@@ -494,45 +496,59 @@ template <class P, int RPT, bool SPIN> struct FwdAcc {
         nalm = nalm_;
         base = base_;
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            r0[k] = P::azero(); i0[k] = r0[k]; r1[k] = r0[k]; i1[k] = r0[k];
-            r2[k] = r0[k]; i2[k] = r0[k]; r3[k] = r0[k]; i3[k] = r0[k];
-        }
+        for (int b = 0; b < NM; ++b)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                r0[b][k] = P::azero(); i0[b][k] = r0[b][k]; r1[b][k] = r0[b][k]; i1[b][k] = r0[b][k];
+                r2[b][k] = r0[b][k]; i2[b][k] = r0[b][k]; r3[b][k] = r0[b][k]; i3[b][k] = r0[b][k];
+            }
     }
     __device__ __forceinline__ void renorm()
     {
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            P::arenorm(r0[k]); P::arenorm(i0[k]); P::arenorm(r1[k]); P::arenorm(i1[k]);
-            if (SPIN) { P::arenorm(r2[k]); P::arenorm(i2[k]); P::arenorm(r3[k]); P::arenorm(i3[k]); }
-        }
+        for (int b = 0; b < NM; ++b)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                P::arenorm(r0[b][k]); P::arenorm(i0[b][k]); P::arenorm(r1[b][k]); P::arenorm(i1[b][k]);
+                if (SPIN) {
+                    P::arenorm(r2[b][k]); P::arenorm(i2[b][k]); P::arenorm(r3[b][k]); P::arenorm(i3[b][k]);
+                }
+            }
     }
     // contribution of degree l (value in word NW), ODD: rel = -1
     template <int NW, bool SCALED, bool ODD> __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, int l)
     {
-        K ar, ai;
-        P::coef(tab, nalm, 0, base + l, ar, ai);
-        if (!SPIN) {
+        typename P::V vp[RPT], vm[RPT];
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const typename P::V v = st.template vplus<NW, SCALED>(k);
-                if (!ODD) { P::fma(r0[k], ar, v); P::fma(i0[k], ai, v); }
-                else { P::fma(r1[k], ar, v); P::fma(i1[k], ai, v); }
-            }
-        } else {
-            K br, bi;
-            P::coef(tab, nalm, 1, base + l, br, bi);
+        for (int k = 0; k < RPT; ++k) {
+            vp[k] = st.template vplus<NW, SCALED>(k);
+            if (SPIN) vm[k] = st.template vminus<NW, SCALED>(k);
+        }
+        const int64_t mstride = (SPIN ? 2 : 1) * nalm;
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const typename P::V vp = st.template vplus<NW, SCALED>(k), vm = st.template vminus<NW, SCALED>(k);
-                P::fma(r0[k], ar, vp); P::fma(i0[k], ai, vp);
-                P::fma(r2[k], br, vm); P::fma(i2[k], bi, vm);
-                if (!ODD) {
-                    P::fma(r1[k], ar, vm); P::fma(i1[k], ai, vm);
-                    P::fma(r3[k], br, vp); P::fma(i3[k], bi, vp);
-                } else {
-                    P::fms(r1[k], ar, vm); P::fms(i1[k], ai, vm);
-                    P::fms(r3[k], br, vp); P::fms(i3[k], bi, vp);
+        for (int b = 0; b < NM; ++b) {
+            K ar, ai;
+            P::coef(tab, nalm, 0, b * mstride + base + l, ar, ai);
+            if (!SPIN) {
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    if (!ODD) { P::fma(r0[b][k], ar, vp[k]); P::fma(i0[b][k], ai, vp[k]); }
+                    else { P::fma(r1[b][k], ar, vp[k]); P::fma(i1[b][k], ai, vp[k]); }
+                }
+            } else {
+                K br, bi;
+                P::coef(tab, nalm, 1, b * mstride + base + l, br, bi);
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    P::fma(r0[b][k], ar, vp[k]); P::fma(i0[b][k], ai, vp[k]);
+                    P::fma(r2[b][k], br, vm[k]); P::fma(i2[b][k], bi, vm[k]);
+                    if (!ODD) {
+                        P::fma(r1[b][k], ar, vm[k]); P::fma(i1[b][k], ai, vm[k]);
+                        P::fma(r3[b][k], br, vp[k]); P::fma(i3[b][k], bi, vp[k]);
+                    } else {
+                        P::fms(r1[b][k], ar, vm[k]); P::fms(i1[b][k], ai, vm[k]);
+                        P::fms(r3[b][k], br, vp[k]); P::fms(i3[b][k], bi, vp[k]);
+                    }
                 }
             }
         }
@@ -545,8 +561,8 @@ template <class P, int RPT, bool SPIN> struct FwdAcc {
     }
 };
 
-template <class P, int RPT, bool SPIN, int REG>
-__device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN> &acc,
+template <class P, int RPT, bool SPIN, int REG, int NM>
+__device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, NM> &acc,
                                           const typename P::Tab *reca, const typename P::TTab *rect, int lb)
 {
 #pragma unroll
@@ -562,11 +578,14 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
     }
 }
 
-template <class P, int RPT, bool SPIN>
+// NM maps share each recursion (prepared coefficients of map b at coef + b *
+// ncomp nalm entries, its ring coefficients at ring + b * ring_stride).
+template <class P, int RPT, bool SPIN, int NM = 1>
 __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_a,
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
-                                                 int spin, int ntheta, int nnorth, int64_t nalm, int m_begin)
+                                                 int spin, int ntheta, int nnorth, int64_t nalm, int m_begin,
+                                                 int64_t ring_stride)
 {
     using Sg = decltype(P::fac(0));
     using Cx = typename P::C;
@@ -585,7 +604,7 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
-    FwdAcc<P, RPT, SPIN> acc;
+    FwdAcc<P, RPT, SPIN, NM> acc;
     acc.init(coef, nalm, base);
 
     const int lf = l0 + 1;
@@ -595,9 +614,9 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         const int reg = st.regime();
         acc.renorm();
-        if (reg == 0) fwd_block<P, RPT, SPIN, 0>(st, acc, reca, rect, l);
-        else if (reg == 1) fwd_block<P, RPT, SPIN, 1>(st, acc, reca, rect, l);
-        else fwd_block<P, RPT, SPIN, 2>(st, acc, reca, rect, l);
+        if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM>(st, acc, reca, rect, l);
+        else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM>(st, acc, reca, rect, l);
+        else fwd_block<P, RPT, SPIN, 2, NM>(st, acc, reca, rect, l);
     }
     for (; l <= lmax; ++l) {  // tail: general path
         st.advance_moved(reca, rect, l);
@@ -606,28 +625,31 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
 
     // write: spin 0 column m; spin s columns mmax + m (P) and mmax - m (Q), with the minus sign
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int jn = rp0 + k;
-        if (jn >= nnorth) continue;
-        const int js = ntheta - 1 - jn;
-        if (!SPIN) {
-            Cx *col = ring + (int64_t)m * ntheta;
-            col[jn] = P::cout(P::aadd(acc.r0[k], acc.r1[k]), P::aadd(acc.i0[k], acc.i1[k]));
-            if (js != jn)
-                col[js] = P::cout(P::ascale(P::asub(acc.r0[k], acc.r1[k]), s0),
-                                  P::ascale(P::asub(acc.i0[k], acc.i1[k]), s0));
-        } else {
-            const Sg ms0 = -s0;
-            Cx *colp = ring + (int64_t)(mmax + m) * ntheta;
-            colp[jn] = P::cout(P::ascale(acc.r0[k], Sg(-1)), P::ascale(acc.i0[k], Sg(-1)));
-            if (js != jn) colp[js] = P::cout(P::ascale(acc.r1[k], ms0), P::ascale(acc.i1[k], ms0));
-            if (m > 0) {
-                Cx *colq = ring + (int64_t)(mmax - m) * ntheta;
-                colq[jn] = P::cout(P::ascale(acc.r2[k], Sg(-1)), P::ascale(acc.i2[k], Sg(-1)));
-                if (js != jn) colq[js] = P::cout(P::ascale(acc.r3[k], ms0), P::ascale(acc.i3[k], ms0));
+    for (int b = 0; b < NM; ++b)
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int jn = rp0 + k;
+            if (jn >= nnorth) continue;
+            const int js = ntheta - 1 - jn;
+            Cx *rb = ring + b * ring_stride;
+            if (!SPIN) {
+                Cx *col = rb + (int64_t)m * ntheta;
+                col[jn] = P::cout(P::aadd(acc.r0[b][k], acc.r1[b][k]), P::aadd(acc.i0[b][k], acc.i1[b][k]));
+                if (js != jn)
+                    col[js] = P::cout(P::ascale(P::asub(acc.r0[b][k], acc.r1[b][k]), s0),
+                                      P::ascale(P::asub(acc.i0[b][k], acc.i1[b][k]), s0));
+            } else {
+                const Sg ms0 = -s0;
+                Cx *colp = rb + (int64_t)(mmax + m) * ntheta;
+                colp[jn] = P::cout(P::ascale(acc.r0[b][k], Sg(-1)), P::ascale(acc.i0[b][k], Sg(-1)));
+                if (js != jn) colp[js] = P::cout(P::ascale(acc.r1[b][k], ms0), P::ascale(acc.i1[b][k], ms0));
+                if (m > 0) {
+                    Cx *colq = rb + (int64_t)(mmax - m) * ntheta;
+                    colq[jn] = P::cout(P::ascale(acc.r2[b][k], Sg(-1)), P::ascale(acc.i2[b][k], Sg(-1)));
+                    if (js != jn) colq[js] = P::cout(P::ascale(acc.r3[b][k], ms0), P::ascale(acc.i3[b][k], ms0));
+                }
             }
         }
-    }
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1032,15 +1054,16 @@ __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restric
     }
 }
 
-template <class P, int RPT, bool SPIN>
+template <class P, int RPT, bool SPIN, int NM = 1>
 cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                        void *ring, int m_begin, int m_end, cudaStream_t st)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
-    k_leg_fwd<P, RPT, SPIN><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring, p.lmax,
-                                                    p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin);
+    k_leg_fwd<P, RPT, SPIN, NM><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring,
+                                                        p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin,
+                                                        (int64_t)p.ncol * p.ntheta);
     return cudaGetLastError();
 }
 
@@ -1106,16 +1129,28 @@ template <class P> const void *kernel_of(bool spin, int rpt, bool adjoint)
     return rpt == 1 ? (const void *)k_leg_fwd<P, 1, false> : (const void *)k_leg_fwd<P, 2, false>;
 }
 
+// FP32 forward kernel sharing the recursion among nm = 2 or 4 maps
+const void *kernel_of_batch(bool spin, int rpt, int nm)
+{
+    if (nm == 2) {
+        if (spin) return rpt == 1 ? (const void *)k_leg_fwd<PolDF, 1, true, 2> : (const void *)k_leg_fwd<PolDF, 2, true, 2>;
+        return rpt == 1 ? (const void *)k_leg_fwd<PolDF, 1, false, 2> : (const void *)k_leg_fwd<PolDF, 2, false, 2>;
+    }
+    if (spin) return rpt == 1 ? (const void *)k_leg_fwd<PolDF, 1, true, 4> : (const void *)k_leg_fwd<PolDF, 2, true, 4>;
+    return rpt == 1 ? (const void *)k_leg_fwd<PolDF, 1, false, 4> : (const void *)k_leg_fwd<PolDF, 2, false, 4>;
+}
+
 }  // namespace
 
 // Launch shape of a Legendre kernel: among 4..16 warps per CTA, the one with
 // the most resident warps per SM (registers decide how many CTAs fit), then
-// the fewest idle ring slots.
-Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt)
+// the fewest idle ring slots.  nm > 1: the FP32 forward kernel for nm maps.
+Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int nm)
 {
-    const void *fn = p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, rpt, adjoint)
-                     : dd               ? kernel_of<PolDD>(p.spin != 0, rpt, adjoint)
-                                        : kernel_of<PolF64>(p.spin != 0, rpt, adjoint);
+    const void *fn = (nm > 1)            ? kernel_of_batch(p.spin != 0, rpt, nm)
+                     : p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, rpt, adjoint)
+                     : dd                  ? kernel_of<PolDD>(p.spin != 0, rpt, adjoint)
+                                           : kernel_of<PolF64>(p.spin != 0, rpt, adjoint);
     const int nw = (p.nnorth + 32 * rpt - 1) / (32 * rpt);
     Plan::LegShape best;
     long best_active = -1, best_slots = 0;
@@ -1184,6 +1219,36 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fwd_spin<PolF64>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.m_df, st)) != cudaSuccess) return e;
     return fwd_spin<PolDD>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
+}
+
+cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring, void *coef, int nm, cudaStream_t st,
+                                      double wpos)
+{
+    if (p.prec != LENS_FP32 || (nm != 2 && nm != 4)) return cudaErrorInvalidValue;
+    const size_t ring_elems = (size_t)p.ncol * p.ntheta;
+    cudaError_t e = cudaMemsetAsync(ring, 0, 8 * ring_elems * nm, st);
+    if (e != cudaSuccess) return e;
+    const int ncomp = p.spin ? 2 : 1;
+    const dim3 g(4, p.mmax + 1);
+    for (int b = 0; b < nm; ++b) {
+        k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm + (size_t)b * ncomp * p.nalm,
+                                                               p.scale, (float2 *)coef + (size_t)b * ncomp * p.nalm,
+                                                               p.lmax, p.spin, p.nalm, p.mmax + 1, wpos);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const Plan::LegShape &sh = p.leg_fb[nm == 2 ? 0 : 1];
+    if (p.spin) {
+        if (sh.rpt == 1)
+            return nm == 2 ? fwd_launch<PolDF, 1, true, 2>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st)
+                           : fwd_launch<PolDF, 1, true, 4>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
+        return nm == 2 ? fwd_launch<PolDF, 2, true, 2>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st)
+                       : fwd_launch<PolDF, 2, true, 4>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
+    }
+    if (sh.rpt == 1)
+        return nm == 2 ? fwd_launch<PolDF, 1, false, 2>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st)
+                       : fwd_launch<PolDF, 1, false, 4>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
+    return nm == 2 ? fwd_launch<PolDF, 2, false, 2>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st)
+                   : fwd_launch<PolDF, 2, false, 4>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
 }
 
 cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st, double wpos)

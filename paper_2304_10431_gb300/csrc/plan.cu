@@ -383,6 +383,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if (prec == LENS_FP64)
             (adj ? p->leg_ad : p->leg_fd) = legendre_shape(*p, adj != 0, true, legendre_rpt_dd(spin, adj != 0));
     }
+    if (prec == LENS_FP32) {  // synthesis of 2 / 4 maps sharing one recursion
+        p->leg_fb[0] = legendre_shape(*p, false, false, p->leg_f.rpt, 2);
+        p->leg_fb[1] = legendre_shape(*p, false, false, 1, 4);
+    }
 
     cudaError_t e;
     // ---- device buffers
@@ -625,6 +629,54 @@ int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st, doub
 
 size_t alm_bytes(const Plan &p) { return (size_t)p.nalm * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 8 : 16); }
 size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 4 : 8); }
+size_t ring_bytes(const Plan &p) { return (size_t)p.ncol * p.ntheta * 8; }
+
+// Workspace of the grouped synthesis (FP32 plans): ring and prepared
+// coefficients of four maps, allocated on the first call with two or more
+// maps.  Not inside a stream capture (an allocation there would not be
+// replayed): such calls then run map by map.
+bool group_workspace(Plan &p, cudaStream_t st)
+{
+    if (p.ring_batch) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    if (p.nallocs + 2 > (int)(sizeof(p.allocs) / sizeof(p.allocs[0]))) return false;
+    void *r = nullptr, *c = nullptr;
+    if (cudaMalloc(&r, 4 * ring_bytes(p)) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (cudaMalloc(&c, 4 * alm_bytes(p)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(r);
+        return false;
+    }
+    p.ring_batch = r;
+    p.coef_batch = c;
+    p.allocs[p.nallocs++] = r;
+    p.allocs[p.nallocs++] = c;
+    p.work_bytes += 4 * (ring_bytes(p) + alm_bytes(p));
+    return true;
+}
+
+// Synthesis of nm = 2 or 4 consecutive maps: one Legendre launch shares the
+// recursion among them, then the Fourier stages and the interpolation per map.
+int forward_group(const Plan &p, const char *alm, char *map, int nm, cudaStream_t st, double wpos)
+{
+    cudaError_t e;
+    if ((e = staged(p, 0, st, [&] {
+             return launch_legendre_fwd_batch(p, alm, p.ring_batch, p.coef_batch, nm, st, wpos);
+         })) != cudaSuccess)
+        return cuda_fail(e, "legendre synthesis");
+    for (int b = 0; b < nm; ++b) {
+        const void *ring = (const char *)p.ring_batch + b * ring_bytes(p);
+        if ((e = staged(p, 1, st, [&] { return launch_theta_fwd(p, ring, p.X, st); })) != cudaSuccess)
+            return cuda_fail(e, "theta transform");
+        if ((e = staged(p, 2, st, [&] { return launch_phi_fwd(p, p.X, p.grid, st); })) != cudaSuccess)
+            return cuda_fail(e, "phi transform");
+        if ((e = staged(p, 3, st, [&] { return launch_interp(p, p.grid, map + b * map_bytes(p), st); })) !=
+            cudaSuccess)
+            return cuda_fail(e, "interpolation");
+    }
+    return LENS_OK;
+}
 
 }  // namespace
 
@@ -650,18 +702,34 @@ extern "C" {
 static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, void *stream, bool fwd, double wpos)
 {
     if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
-    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    Plan &p = *reinterpret_cast<Plan *>(pl);
     const void *alm_d = fwd ? in_d : out_d, *map_d = fwd ? out_d : in_d;
     if (nmaps > 0 && (!alm_d || (!map_d && p.npts > 0))) return fail(LENS_ERR_INVALID, "NULL buffer");
     DeviceGuard g(p.device);
     cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
     const size_t ib = fwd ? alm_bytes(p) : map_bytes(p), ob = fwd ? map_bytes(p) : alm_bytes(p);
-    for (int i = 0; i < nmaps; ++i) {
+    int i = 0;
+    // FP32 synthesis of several maps: groups of 4, then 2, share the recursion
+    if (fwd && p.prec == LENS_FP32 && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
+        for (int nm = 4; nm >= 2; nm /= 2)
+            for (; nmaps - i >= nm; i += nm) {
+                const int r = forward_group(p, (const char *)in_d + i * ib, (char *)out_d + i * ob, nm, st, wpos);
+                if (r != LENS_OK) return r;
+            }
+    }
+    for (; i < nmaps; ++i) {
         const void *in = (const char *)in_d + i * ib;
         void *out = (char *)out_d + i * ob;
         int r = fwd ? forward_one(p, in, out, st, wpos) : adjoint_one(p, in, out, st, wpos);
         if (r != LENS_OK) return r;
     }
+    return LENS_OK;
+}
+
+int lens_plan_set_grouping(lens_plan pl, int on)
+{
+    if (!pl) return fail(LENS_ERR_INVALID, "bad plan");
+    reinterpret_cast<Plan *>(pl)->group_maps = on != 0;
     return LENS_OK;
 }
 
