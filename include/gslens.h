@@ -73,6 +73,17 @@ typedef enum {
 
 typedef enum { LENS_FP32 = 0, LENS_FP64 = 1 } lens_prec;
 
+/* Plan flags (lens_plan_create's flags argument, OR-ed). */
+typedef enum {
+    /* Gradient-only spin-s transforms (Sect. 4: a vanishing curl component,
+     * C = 0, e.g. the spin-1 deflection field of Sect. 3 or E-only
+     * polarisation).  a_lm buffers then hold G alone, [nmaps][1][nalm]:
+     * lens_synthesis takes C = 0 and lens_adjoint returns only G.  The
+     * Legendre steps accumulate two sums per degree instead of four.
+     * Needs spin > 0 (LENS_ERR_INVALID otherwise). */
+    LENS_GRAD_ONLY = 1
+} lens_flags;
+
 typedef struct lens_plan_s *lens_plan;
 
 /* Optional overrides for lens_plan_create_ex; zero fields mean "choose". */
@@ -102,6 +113,8 @@ typedef struct {
     int row_pitch;      /* grid row stride in elements */
     size_t workspace_bytes;    /* per-call work buffers */
     size_t plan_bytes;         /* point tables and coefficient tables */
+    unsigned flags;            /* lens_flags the plan was created with */
+    int alm_ncomp;             /* components of an a_lm buffer: 1 (spin 0, LENS_GRAD_ONLY) or 2 */
 } lens_plan_info_t;
 
 /*
@@ -117,7 +130,7 @@ typedef struct {
  *              epsilon >= 2e-6 (FP32 rounding alone leaves ~1.2e-6 at lmax
  *              4096), FP64 plans epsilon >= 1e-13.
  *   prec       LENS_FP32 or LENS_FP64.
- *   flags      reserved, must be 0.
+ *   flags      0 or LENS_GRAD_ONLY (lens_flags); other bits: LENS_ERR_INVALID.
  *   stream     cudaStream_t (NULL = legacy default stream).
  * Synchronises the stream once (coordinate validation).  LENS_ERR_DOMAIN if a
  * coordinate is not finite or theta is outside [0, pi].
@@ -189,7 +202,9 @@ int lens_adjoint_vjp(lens_plan p, const void *grad_alm_d, void *grad_map_d, int 
  *   phi_lm_d  device complex double [nalm] (real-field layout of a_lm).
  *   alpha_d   device double [2][npoints]: alpha_theta then alpha_phi; feed
  *             them to lens_pointing for theta', phi', chi.
- * LENS_ERR_INVALID unless defl is FP64 spin 1.
+ * LENS_ERR_INVALID unless defl is FP64 spin 1.  defl may be LENS_GRAD_ONLY
+ * (the deflection has no curl component): the same result with half the
+ * Legendre accumulation work.
  */
 int lens_deflection(lens_plan defl, const void *phi_lm_d, double *alpha_d, void *stream);
 
@@ -220,7 +235,8 @@ int lens_alm_eth(int lmax, int mmax, int spin, int lower, int prec, const void *
  *   lensed       plan of spin s (0 or >= 2) on the deflected points, with chi.
  *   lensed_up    plan of spin s+1, same points, chi, band limit, precision.
  *   lensed_down  plan of spin s-1 for s >= 2 (NULL for s = 0).
- *   defl         FP64 spin-1 plan on the undeflected points, band limit of phi.
+ *   defl         FP64 spin-1 plan on the undeflected points, band limit of phi
+ *                (LENS_GRAD_ONLY or not; the three lensed plans must not be).
  *   alpha_d      device double [2][npoints], the deflection the points came from.
  *   x_alm_d      device complex [ncomp][nalm], lensed's precision.
  *   map_d        lensed map A(phi) x, [ncomp][npoints], or NULL (recomputed).

@@ -56,7 +56,7 @@ class LensPlan:
                  epsilon: float = 1e-5, precision: str = "fp32", sigma: float | None = None,
                  W: int | None = None, beta: float | None = None, ntheta: int | None = None,
                  legendre_rpt: tuple | None = None, legendre_df32_mmin: int = 0, fft_cluster: int = 0,
-                 device=None, stream=None):
+                 grad_only: bool = False, device=None, stream=None):
         lib = _native.load()
         if precision not in _PREC:
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -65,7 +65,9 @@ class LensPlan:
         self.precision = precision
         self.real_dtype = torch.float32 if precision == "fp32" else torch.float64
         self.complex_dtype = torch.complex64 if precision == "fp32" else torch.complex128
-        self.ncomp = 1 if self.spin == 0 else 2
+        self.ncomp = 1 if self.spin == 0 else 2  # components of a map
+        self.grad_only = bool(grad_only)  # spin s with C = 0: a_lm buffers hold G alone
+        self.alm_ncomp = 1 if (self.spin == 0 or self.grad_only) else 2
         with torch.cuda.device(self.device):
             th = _dev_f64(theta, self.device)
             ph = _dev_f64(phi, self.device)
@@ -82,7 +84,7 @@ class LensPlan:
                                          th.data_ptr() if self.npoints else None,
                                          ph.data_ptr() if self.npoints else None,
                                          ch.data_ptr() if ch is not None else None, float(epsilon),
-                                         _PREC[precision], 0, st, ctypes.byref(prm))
+                                         _PREC[precision], 1 if self.grad_only else 0, st, ctypes.byref(prm))
             _native.check(rc)
         self._h = handle
         self.nalm = nalm(self.lmax, self.mmax)
@@ -120,9 +122,9 @@ class LensPlan:
         if alm.dtype != self.complex_dtype:
             raise TypeError("alm must be %s for a %s plan" % (self.complex_dtype, self.precision))
         alm = alm.contiguous()
-        if alm.shape[-1] != self.nalm or (alm.dim() >= 2 and alm.shape[-2] != self.ncomp) or \
-                (alm.dim() == 1 and self.ncomp != 1):
-            raise ValueError("alm must have shape [..., %d, %d]" % (self.ncomp, self.nalm))
+        if alm.shape[-1] != self.nalm or (alm.dim() >= 2 and alm.shape[-2] != self.alm_ncomp) or \
+                (alm.dim() == 1 and self.alm_ncomp != 1):
+            raise ValueError("alm must have shape [..., %d, %d]" % (self.alm_ncomp, self.nalm))
         nmaps = 1 if alm.dim() <= 2 else int(np.prod(alm.shape[:-2]))
         return alm, nmaps
 
@@ -154,7 +156,7 @@ class LensPlan:
         m, nmaps = self._map_arg(m)
         lead = m.shape[:-2] if m.dim() > 2 else ()
         if out is None:
-            out = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+            out = torch.empty(*lead, self.alm_ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
         _native.check(_native.load().lens_adjoint(self._h, m.data_ptr(), out.data_ptr(), nmaps,
                                                   _stream_handle(stream)))
         return out
@@ -164,7 +166,7 @@ class LensPlan:
         g, nmaps = self._map_arg(grad_map)
         lead = g.shape[:-2] if g.dim() > 2 else ()
         if out is None:
-            out = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+            out = torch.empty(*lead, self.alm_ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
         _native.check(_native.load().lens_synthesis_vjp(self._h, g.data_ptr(), out.data_ptr(), nmaps,
                                                         _stream_handle(stream)))
         return out
@@ -195,7 +197,7 @@ class LensPlan:
         nmaps = 1 if m_h.dim() <= 2 else int(np.prod(m_h.shape[:-2]))
         lead = m_h.shape[:-2] if m_h.dim() > 2 else ()
         if out_h is None:
-            out_h = torch.empty(*lead, self.ncomp, self.nalm, dtype=self.complex_dtype)
+            out_h = torch.empty(*lead, self.alm_ncomp, self.nalm, dtype=self.complex_dtype)
         _native.check(_native.load().lens_adjoint_host(self._h, m_h.data_ptr(), out_h.data_ptr(), nmaps,
                                                        _stream_handle(stream)))
         return out_h
@@ -212,7 +214,7 @@ class LensPlan:
 
     def ring_adjoint(self, ring: torch.Tensor, stream=None) -> torch.Tensor:
         ring = ring.contiguous()
-        out = torch.empty(self.ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
+        out = torch.empty(self.alm_ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)
         _native.check(_native.load().lens_ring_adjoint(self._h, ring.data_ptr(), out.data_ptr(),
                                                        _stream_handle(stream)))
         return out
@@ -273,8 +275,9 @@ class LensingModel:
         self.theta0 = _dev_f64(theta0, self.device)
         self.phi0 = _dev_f64(phi0, self.device)
         self.npoints = int(self.theta0.numel())
+        # the deflection is a pure gradient (no curl): a gradient-only spin-1 plan
         self.defl = LensPlan(self.lmax_phi, self.theta0, self.phi0, spin=1, epsilon=epsilon_deflection,
-                             precision="fp64", device=self.device)
+                             precision="fp64", grad_only=True, device=self.device)
         self.alpha = torch.empty(2, self.npoints, dtype=torch.float64, device=self.device)
         self.phi_lm = None
         self.lensed = self._up = self._down = None

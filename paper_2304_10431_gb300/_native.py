@@ -66,7 +66,7 @@ class PlanInfo(ctypes.Structure):
                 ("ntheta_fft", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("W", ctypes.c_int),
                 ("beta", ctypes.c_double), ("sigma", ctypes.c_double), ("rows_kept", ctypes.c_int),
                 ("row_pitch", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
-                ("plan_bytes", ctypes.c_size_t)]
+                ("plan_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint), ("alm_ncomp", ctypes.c_int)]
 
 
 def lib_path() -> str:

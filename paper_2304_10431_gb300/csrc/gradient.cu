@@ -228,11 +228,13 @@ int lens_phi_gradient(lens_plan lensed, lens_plan lensed_up, lens_plan lensed_do
         return record_failure(LENS_ERR_INVALID,
                               "lens_phi_gradient: lensed_up must be spin s+1 with the lensed plan's points, band "
                               "limit and precision; defl an FP64 spin-1 plan on the same points");
+    if (p.grad || pu.grad)
+        return record_failure(LENS_ERR_INVALID, "lens_phi_gradient: lensed plans must not be LENS_GRAD_ONLY");
     const Plan *pdn = nullptr;
     if (s >= 2) {
         if (!lensed_down) return record_failure(LENS_ERR_INVALID, "lens_phi_gradient: spin s >= 2 needs lensed_down");
         pdn = as_plan(lensed_down);
-        if (pdn->spin != s - 1 || pdn->prec != p.prec || pdn->lmax != p.lmax || pdn->mmax != p.mmax ||
+        if (pdn->spin != s - 1 || pdn->grad || pdn->prec != p.prec || pdn->lmax != p.lmax || pdn->mmax != p.mmax ||
             pdn->npts != p.npts || pdn->device != p.device)
             return record_failure(LENS_ERR_INVALID, "lens_phi_gradient: lensed_down must be spin s-1 like lensed");
     }

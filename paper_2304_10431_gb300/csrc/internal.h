@@ -77,6 +77,8 @@ struct Plan {
     // coefficients of up to 4 maps, allocated on the first such call
     void *ring_batch = nullptr, *coef_batch = nullptr;
     bool group_maps = true;  // false: every map runs alone (lens_plan_set_grouping)
+    bool grad = false;       // gradient-only spin s plan (C = 0): a_lm holds G alone
+    int alm_ncomp() const { return spin && !grad ? 2 : 1; }
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;
     void *w1 = nullptr;       // [2 lmax + 1]  1/psihat(2 pi k / N1), k = -lmax..lmax
@@ -142,7 +144,7 @@ int run_adjoint(const Plan &p, const void *map, void *alm, cudaStream_t st, doub
 bool profile_swap(bool on);
 
 // Bytes of one map's a_lm / point values for a plan.
-inline size_t plan_alm_bytes(const Plan &p) { return (size_t)p.nalm * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 8 : 16); }
+inline size_t plan_alm_bytes(const Plan &p) { return (size_t)p.nalm * p.alm_ncomp() * (p.prec == LENS_FP32 ? 8 : 16); }
 inline size_t plan_map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 4 : 8); }
 
 // Records a failing status and message in the calling thread's error state

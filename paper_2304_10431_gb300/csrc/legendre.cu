@@ -481,7 +481,10 @@ template <class P, int RPT, bool SPIN> struct Rings {
 //   spin s: (r0, i0) = sum a s-lambda (north, +m), (r1, i1) = sum rel a (-s)lambda
 //           (south, +m), (r2, i2) = sum b (-s)lambda (north, -m), (r3, i3) =
 //           sum rel b s-lambda (south, -m); the south sums are multiplied by s0.
-template <class P, int RPT, bool SPIN, int NM = 1> struct FwdAcc {
+//   gradient-only spin s (C = 0, so b = (-1)^s conj a): (r0, i0) / (r1, i1) sum
+//           a s-lambda over degrees with rel = +1 / -1, (r2, i2) / (r3, i3)
+//           a (-s)lambda; the four spin-s sums follow from them at the end.
+template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false> struct FwdAcc {
     // NM maps share the recursion: map b's prepared coefficients start at
     // tab + b * (ncomp nalm) entries and it has its own accumulators
     using A = typename P::A;
@@ -529,7 +532,18 @@ template <class P, int RPT, bool SPIN, int NM = 1> struct FwdAcc {
         for (int b = 0; b < NM; ++b) {
             K ar, ai;
             P::coef(tab, nalm, 0, b * mstride + base + l, ar, ai);
-            if (!SPIN) {
+            if (GRAD) {
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    if (!ODD) {
+                        P::fma(r0[b][k], ar, vp[k]); P::fma(i0[b][k], ai, vp[k]);
+                        P::fma(r2[b][k], ar, vm[k]); P::fma(i2[b][k], ai, vm[k]);
+                    } else {
+                        P::fma(r1[b][k], ar, vp[k]); P::fma(i1[b][k], ai, vp[k]);
+                        P::fma(r3[b][k], ar, vm[k]); P::fma(i3[b][k], ai, vm[k]);
+                    }
+                }
+            } else if (!SPIN) {
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) {
                     if (!ODD) { P::fma(r0[b][k], ar, vp[k]); P::fma(i0[b][k], ai, vp[k]); }
@@ -561,8 +575,8 @@ template <class P, int RPT, bool SPIN, int NM = 1> struct FwdAcc {
     }
 };
 
-template <class P, int RPT, bool SPIN, int REG, int NM>
-__device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, NM> &acc,
+template <class P, int RPT, bool SPIN, int REG, int NM, bool GRAD>
+__device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, NM, GRAD> &acc,
                                           const typename P::Tab *reca, const typename P::TTab *rect, int lb)
 {
 #pragma unroll
@@ -580,7 +594,8 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
 
 // NM maps share each recursion (prepared coefficients of map b at coef + b *
 // ncomp nalm entries, its ring coefficients at ring + b * ring_stride).
-template <class P, int RPT, bool SPIN, int NM = 1>
+// GRAD: gradient-only spin s (prepared coefficients of G alone, see FwdAcc).
+template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false>
 __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_a,
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
@@ -604,7 +619,7 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
-    FwdAcc<P, RPT, SPIN, NM> acc;
+    FwdAcc<P, RPT, SPIN, NM, GRAD> acc;
     acc.init(coef, nalm, base);
 
     const int lf = l0 + 1;
@@ -614,9 +629,9 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         const int reg = st.regime();
         acc.renorm();
-        if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM>(st, acc, reca, rect, l);
-        else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM>(st, acc, reca, rect, l);
-        else fwd_block<P, RPT, SPIN, 2, NM>(st, acc, reca, rect, l);
+        if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM, GRAD>(st, acc, reca, rect, l);
+        else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM, GRAD>(st, acc, reca, rect, l);
+        else fwd_block<P, RPT, SPIN, 2, NM, GRAD>(st, acc, reca, rect, l);
     }
     for (; l <= lmax; ++l) {  // tail: general path
         st.advance_moved(reca, rect, l);
@@ -638,6 +653,21 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
                 if (js != jn)
                     col[js] = P::cout(P::ascale(P::asub(acc.r0[b][k], acc.r1[b][k]), s0),
                                       P::ascale(P::asub(acc.i0[b][k], acc.i1[b][k]), s0));
+            } else if (GRAD) {
+                // sum a s-lambda, sum rel a (-s)lambda, sgs conj(sum a (-s)lambda), sgs conj(sum rel a s-lambda)
+                const Sg ms0 = -s0, sgs = (s & 1) ? Sg(-1) : Sg(1);
+                const A pr = P::aadd(acc.r0[b][k], acc.r1[b][k]), pi = P::aadd(acc.i0[b][k], acc.i1[b][k]);
+                const A qr = P::asub(acc.r2[b][k], acc.r3[b][k]), qi = P::asub(acc.i2[b][k], acc.i3[b][k]);
+                Cx *colp = rb + (int64_t)(mmax + m) * ntheta;
+                colp[jn] = P::cout(P::ascale(pr, Sg(-1)), P::ascale(pi, Sg(-1)));
+                if (js != jn) colp[js] = P::cout(P::ascale(qr, ms0), P::ascale(qi, ms0));
+                if (m > 0) {
+                    const A ur = P::aadd(acc.r2[b][k], acc.r3[b][k]), ui = P::aadd(acc.i2[b][k], acc.i3[b][k]);
+                    const A wr = P::asub(acc.r0[b][k], acc.r1[b][k]), wi = P::asub(acc.i0[b][k], acc.i1[b][k]);
+                    Cx *colq = rb + (int64_t)(mmax - m) * ntheta;
+                    colq[jn] = P::cout(P::ascale(ur, -sgs), P::ascale(ui, sgs));
+                    if (js != jn) colq[js] = P::cout(P::ascale(wr, sgs * ms0), P::ascale(wi, -(sgs * ms0)));
+                }
             } else {
                 const Sg ms0 = -s0;
                 Cx *colp = rb + (int64_t)(mmax + m) * ntheta;
@@ -688,13 +718,18 @@ template <class P, int NV> __device__ __forceinline__ typename P::A warp_transpo
 // (-1)^(l-m) = s0 rel is +1 or -1.  spin s: hn/hs column +m north/south,
 // gn/gs column -m; the south inputs are multiplied by s0 so that a degree
 // takes them with the sign rel.
-template <class P, int RPT, bool SPIN> struct AdjIn {
+// GRAD (gradient-only spin s: only G is returned): with sgs = (-1)^s,
+//   -2 G = sum_l s-lambda (H_m(N) + rel sgs s0 H_-m(S)) + (-s)lambda (rel s0 H_m(S) + sgs H_-m(N))
+// (real and imaginary parts with the sign of sgs flipped for the imaginary
+// part), so each ring keeps these combinations for rel = +1 (hn*, hs*) and
+// rel = -1 (gn*, gs*) and a degree adds two values instead of four.
+template <class P, int RPT, bool SPIN, bool GRAD = false> struct AdjIn {
     using K = typename P::K;
     using A = typename P::A;
     K hnr[RPT], hni[RPT], hsr[RPT], hsi[RPT], gnr[RPT], gni[RPT], gsr[RPT], gsi[RPT];
 
     __device__ __forceinline__ void init(const typename P::C *ring, int rp0, int nnorth, int ntheta, int m, int mmax,
-                                         bool s0neg)
+                                         bool s0neg, bool sodd = false)
     {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -713,6 +748,16 @@ template <class P, int RPT, bool SPIN> struct AdjIn {
                     if (s0neg) {
                         hsr[k] = P::ksign(hsr[k], -1); hsi[k] = P::ksign(hsi[k], -1);
                         gsr[k] = P::ksign(gsr[k], -1); gsi[k] = P::ksign(gsi[k], -1);
+                    }
+                    if (GRAD) {
+                        const int sg = sodd ? -1 : 1;
+                        const K xgsr = P::ksign(gsr[k], sg), xgsi = P::ksign(gsi[k], sg);
+                        const K xgnr = P::ksign(gnr[k], sg), xgni = P::ksign(gni[k], sg);
+                        const K nr = hnr[k], ni = hni[k], sr = hsr[k], si = hsi[k];
+                        hnr[k] = P::kadd(nr, xgsr); hsr[k] = P::kadd(sr, xgnr);    // rel = +1
+                        hni[k] = P::ksub(ni, xgsi); hsi[k] = P::ksub(si, xgni);
+                        gnr[k] = P::ksub(nr, xgsr); gsr[k] = P::ksub(xgnr, sr);    // rel = -1
+                        gni[k] = P::kadd(ni, xgsi); gsi[k] = P::ksign(P::kadd(si, xgni), -1);
                     }
                 } else {
                     const K ar = hnr[k], ai = hni[k], br = hsr[k], bi = hsi[k];
@@ -733,6 +778,10 @@ template <class P, int RPT, bool SPIN> struct AdjIn {
             if (!SPIN) {
                 P::fma(part[0], ODD ? hsr[k] : hnr[k], vp);
                 P::fma(part[1], ODD ? hsi[k] : hni[k], vp);
+            } else if (GRAD) {
+                const typename P::V vm = st.template vminus<NW, SCALED>(k);
+                P::fma2(part[0], ODD ? gnr[k] : hnr[k], vp, ODD ? gsr[k] : hsr[k], vm);
+                P::fma2(part[1], ODD ? gni[k] : hni[k], vp, ODD ? gsi[k] : hsi[k], vm);
             } else {
                 const typename P::V vm = st.template vminus<NW, SCALED>(k);
                 // U += lam+ H_m(N) + rel lam- s0 H_m(S) ; V += lam- H_-m(N) + rel lam+ s0 H_-m(S)
@@ -854,11 +903,12 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
 // shared memory of one adjoint CTA (FP32 plans): one row block per warp
 template <bool SPIN> __host__ __device__ constexpr size_t adj_smem_per_warp() { return 32 * kRowStride<kBlk * (SPIN ? 4 : 2)> * sizeof(float); }
 
-template <class P, int RPT, bool SPIN, int REG>
-__device__ __forceinline__ void adj_block(Rings<P, RPT, SPIN> &st, const AdjIn<P, RPT, SPIN> &in, typename P::A *part,
-                                          const typename P::Tab *reca, const typename P::TTab *rect, int lb)
+template <class P, int RPT, bool SPIN, int REG, bool GRAD>
+__device__ __forceinline__ void adj_block(Rings<P, RPT, SPIN> &st, const AdjIn<P, RPT, SPIN, GRAD> &in,
+                                          typename P::A *part, const typename P::Tab *reca,
+                                          const typename P::TTab *rect, int lb)
 {
-    constexpr int NCOMP = SPIN ? 4 : 2;
+    constexpr int NCOMP = (SPIN && !GRAD) ? 4 : 2;
 #pragma unroll
     for (int j = 0; j < kBlk; ++j) {
         const int l = lb + j;
@@ -872,7 +922,9 @@ __device__ __forceinline__ void adj_block(Rings<P, RPT, SPIN> &st, const AdjIn<P
     }
 }
 
-template <class P, int RPT, bool SPIN>
+// GRAD: gradient-only spin s, G alone is written (out [nalm]); the reduction
+// then has the shape of spin 0's, with the factor -1/2 in the weight.
+template <class P, int RPT, bool SPIN, bool GRAD = false>
 __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_a,
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  const double *__restrict__ scale, RingTab rt,
@@ -882,7 +934,8 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     using A = typename P::A;
     using R = typename P::R;
     using Sg = decltype(P::fac(0));
-    constexpr int NCOMP = SPIN ? 4 : 2;
+    constexpr int NCOMP = (SPIN && !GRAD) ? 4 : 2;
+    constexpr bool FSPIN = SPIN && !GRAD;  // reduction shape: four values per degree
     constexpr int NV = kBlk * NCOMP;
     const int m = m_begin + blockIdx.y;
     const int s = SPIN ? spin : 0;
@@ -899,41 +952,41 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     const Sg sgs = (s & 1) ? Sg(-1) : Sg(1);
     R *out = reinterpret_cast<R *>(alm);
     const int lf = l0 + 1;
-    const double wm = m > 0 ? wpos : 1.0;
+    const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
-    AdjIn<P, RPT, SPIN> in;
-    in.init(ring, rp0, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0);
+    AdjIn<P, RPT, SPIN, GRAD> in;
+    in.init(ring, rp0, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
 
     {  // degree l0 (the start value): one reduction of NCOMP values
         A p0[NCOMP];
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
         in.add_rt(st, true, p0);  // l0 = lf - 1
-        flush<P, SPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs);
+        flush<P, FSPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs);
     }
     int l = lf;
     A part[NV];
     // measured at lmax 4096: spin s 42.8 -> 41.6 ms; spin 0 (16 values per lane)
     // 17.2 -> 18.4 ms, so spin 0 keeps the transpose-reduce
-    constexpr bool kSmemFlush = std::is_same<P, PolDF>::value && SPIN;
+    constexpr bool kSmemFlush = std::is_same<P, PolDF>::value && FSPIN;
     extern __shared__ __align__(16) float adj_smem[];
-    float *wbuf = adj_smem + (threadIdx.x >> 5) * (adj_smem_per_warp<SPIN>() / sizeof(float));
+    float *wbuf = adj_smem + (threadIdx.x >> 5) * (adj_smem_per_warp<FSPIN>() / sizeof(float));
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         const int reg = st.regime();
         if (reg == 1) {  // every contribution of this block is below 2^-180: recursion only
-            adj_block<P, RPT, SPIN, 1>(st, in, part, reca, rect, l);
+            adj_block<P, RPT, SPIN, 1, GRAD>(st, in, part, reca, rect, l);
             continue;
         }
 #pragma unroll
         for (int i = 0; i < NV; ++i) part[i] = P::azero();
-        if (reg == 0) adj_block<P, RPT, SPIN, 0>(st, in, part, reca, rect, l);
-        else adj_block<P, RPT, SPIN, 2>(st, in, part, reca, rect, l);
+        if (reg == 0) adj_block<P, RPT, SPIN, 0, GRAD>(st, in, part, reca, rect, l);
+        else adj_block<P, RPT, SPIN, 2, GRAD>(st, in, part, reca, rect, l);
         if constexpr (kSmemFlush)
-            flush_smem<SPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, base, nalm, m, l, lmax, sgs);
+            flush_smem<FSPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, base, nalm, m, l, lmax, sgs);
         else
-            flush<P, SPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
+            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
     }
     if (l <= lmax) {  // tail: fewer than kBlk degrees, general path
 #pragma unroll
@@ -945,7 +998,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                 in.add_rt(st, (j & 1) != 0, part + j * NCOMP);
             }
         }
-        flush<P, SPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
+        flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
     }
 }
 
@@ -1007,7 +1060,8 @@ __global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, flo
 
 // Forward coefficients of one call: spin 0 c_l a_lm; spin s c_l (G + iC) and
 // c_l (-1)^s (conj G + i conj C) (m = 0: imaginary parts of a, G, C dropped),
-// all multiplied by wpos for m > 0;
+// all multiplied by wpos for m > 0; gradient-only plans (grad, alm holds G
+// alone) c_l G only;
 // zero for l < l0.  Entries of orders m < m_split are written as OUT_LO, the
 // others as OUT_HI: float2 (FP32 plans), double2 (FP64 plans, native FP64
 // orders) or float4 df32 (FP64 plans, df32 orders).
@@ -1028,7 +1082,7 @@ template <> __device__ __forceinline__ void put_coef<float4>(void *out, int64_t 
 
 template <typename Tin, typename OUT_LO, typename OUT_HI>
 __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restrict__ scale, void *__restrict__ out,
-                            int lmax, int spin, int64_t nalm, int m_split, double wpos)
+                            int lmax, int spin, int64_t nalm, int m_split, double wpos, bool grad)
 {
     const int m = blockIdx.y;
     const int64_t base = alm_base(lmax, m);
@@ -1043,6 +1097,9 @@ __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restric
         if (!spin) {
             if (hi) put_coef<OUT_HI>(out, i, c * gr, c * gi);
             else put_coef<OUT_LO>(out, i, c * gr, c * gi);
+        } else if (grad) {  // C = 0: a = c G (b = (-1)^s conj a is not stored)
+            if (hi) put_coef<OUT_HI>(out, i, c * gr, c * gi);
+            else put_coef<OUT_LO>(out, i, c * gr, c * gi);
         } else {
             const Tin cv = alm[nalm + i];
             const double cr = cv.x, ci = m == 0 ? 0.0 : (double)cv.y;
@@ -1054,77 +1111,84 @@ __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restric
     }
 }
 
-template <class P, int RPT, bool SPIN, int NM = 1>
+template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false>
 cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                        void *ring, int m_begin, int m_end, cudaStream_t st)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
-    k_leg_fwd<P, RPT, SPIN, NM><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring,
+    k_leg_fwd<P, RPT, SPIN, NM, GRAD><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring,
                                                         p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin,
                                                         (int64_t)p.ncol * p.ntheta);
     return cudaGetLastError();
 }
 
-template <class P, bool SPIN> size_t adj_smem_bytes(int warps)
+template <class P, bool SPIN, bool GRAD = false> size_t adj_smem_bytes(int warps)
 {
-    return (std::is_same<P, PolDF>::value && SPIN) ? (size_t)warps * adj_smem_per_warp<SPIN>() : 0;
+    return (std::is_same<P, PolDF>::value && SPIN && !GRAD) ? (size_t)warps * adj_smem_per_warp<SPIN>() : 0;
 }
 
-template <class P, int RPT, bool SPIN>
+template <class P, int RPT, bool SPIN, bool GRAD = false>
 cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                        void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
     dim3 block(sh.warps * 32);
-    k_leg_adj<P, RPT, SPIN><<<grid, block, adj_smem_bytes<P, SPIN>(sh.warps), st>>>(
+    k_leg_adj<P, RPT, SPIN, GRAD><<<grid, block, adj_smem_bytes<P, SPIN, GRAD>(sh.warps), st>>>(
                                                     (const typename P::C *)ring, ta, tt, p.lognorm, p.scale, p.rings,
                                                     (typename P::C *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
                                                     p.nalm, m_begin, wpos);
     return cudaGetLastError();
 }
 
-template <class P, bool SPIN>
+template <class P, bool SPIN, bool GRAD = false>
 cudaError_t fwd_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                     void *ring, int m_begin, int m_end, cudaStream_t st)
 {
-    if (sh.rpt == 1) return fwd_launch<P, 1, SPIN>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
-    return fwd_launch<P, 2, SPIN>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
+    if (sh.rpt == 1) return fwd_launch<P, 1, SPIN, 1, GRAD>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
+    return fwd_launch<P, 2, SPIN, 1, GRAD>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
 }
 
-template <class P, bool SPIN>
+template <class P, bool SPIN, bool GRAD = false>
 cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                     void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
-    if (sh.rpt == 1) return adj_launch<P, 1, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
-    return adj_launch<P, 2, SPIN>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    if (sh.rpt == 1) return adj_launch<P, 1, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    return adj_launch<P, 2, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
 }
 
 template <class P>
 cudaError_t fwd_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, const void *ta, const void *tt,
                      void *ring, int m_begin, int m_end, cudaStream_t st)
 {
-    return p.spin ? fwd_rpt<P, true>(p, sh, coef, ta, tt, ring, m_begin, m_end, st)
-                  : fwd_rpt<P, false>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
+    if (!p.spin) return fwd_rpt<P, false>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
+    return p.grad ? fwd_rpt<P, true, true>(p, sh, coef, ta, tt, ring, m_begin, m_end, st)
+                  : fwd_rpt<P, true>(p, sh, coef, ta, tt, ring, m_begin, m_end, st);
 }
 
 template <class P>
 cudaError_t adj_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
                      void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
 {
-    return p.spin ? adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos)
-                  : adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    if (!p.spin) return adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    return p.grad ? adj_rpt<P, true, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos)
+                  : adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
 }
 
-// Kernel entry of one (arithmetic, spin, rings-per-thread, direction) variant.
-template <class P> const void *kernel_of(bool spin, int rpt, bool adjoint)
+// Kernel entry of one (arithmetic, spin, gradient-only, rings-per-thread,
+// direction) variant.
+template <class P> const void *kernel_of(bool spin, bool grad, int rpt, bool adjoint)
 {
     if (adjoint) {
+        if (spin && grad)
+            return rpt == 1 ? (const void *)k_leg_adj<P, 1, true, true> : (const void *)k_leg_adj<P, 2, true, true>;
         if (spin) return rpt == 1 ? (const void *)k_leg_adj<P, 1, true> : (const void *)k_leg_adj<P, 2, true>;
         return rpt == 1 ? (const void *)k_leg_adj<P, 1, false> : (const void *)k_leg_adj<P, 2, false>;
     }
+    if (spin && grad)
+        return rpt == 1 ? (const void *)k_leg_fwd<P, 1, true, 1, true> : (const void *)k_leg_fwd<P, 2, true, 1, true>;
     if (spin) return rpt == 1 ? (const void *)k_leg_fwd<P, 1, true> : (const void *)k_leg_fwd<P, 2, true>;
     return rpt == 1 ? (const void *)k_leg_fwd<P, 1, false> : (const void *)k_leg_fwd<P, 2, false>;
 }
@@ -1148,9 +1212,9 @@ const void *kernel_of_batch(bool spin, int rpt, int nm)
 Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int nm)
 {
     const void *fn = (nm > 1)            ? kernel_of_batch(p.spin != 0, rpt, nm)
-                     : p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, rpt, adjoint)
-                     : dd                  ? kernel_of<PolDD>(p.spin != 0, rpt, adjoint)
-                                           : kernel_of<PolF64>(p.spin != 0, rpt, adjoint);
+                     : p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, p.grad, rpt, adjoint)
+                     : dd                  ? kernel_of<PolDD>(p.spin != 0, p.grad, rpt, adjoint)
+                                           : kernel_of<PolF64>(p.spin != 0, p.grad, rpt, adjoint);
     const int nw = (p.nnorth + 32 * rpt - 1) / (32 * rpt);
     Plan::LegShape best;
     long best_active = -1, best_slots = 0;
@@ -1210,12 +1274,12 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     const dim3 g(4, p.mmax + 1);
     if (p.prec == LENS_FP32) {
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef, p.lmax, p.spin,
-                                                               p.nalm, p.mmax + 1, wpos);
+                                                               p.nalm, p.mmax + 1, wpos, p.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return fwd_spin<PolDF>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
     }
     k_coef_prep<double2, double2, float4><<<g, 256, 0, st>>>((const double2 *)alm, p.scale, p.coef, p.lmax, p.spin,
-                                                             p.nalm, p.m_df, wpos);
+                                                             p.nalm, p.m_df, wpos, p.grad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fwd_spin<PolF64>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.m_df, st)) != cudaSuccess) return e;
     return fwd_spin<PolDD>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
@@ -1233,7 +1297,7 @@ cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring
     for (int b = 0; b < nm; ++b) {
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm + (size_t)b * ncomp * p.nalm,
                                                                p.scale, (float2 *)coef + (size_t)b * ncomp * p.nalm,
-                                                               p.lmax, p.spin, p.nalm, p.mmax + 1, wpos);
+                                                               p.lmax, p.spin, p.nalm, p.mmax + 1, wpos, false);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const Plan::LegShape &sh = p.leg_fb[nm == 2 ? 0 : 1];
@@ -1253,7 +1317,7 @@ cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring
 
 cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cudaStream_t st, double wpos)
 {
-    const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * (p.spin ? 2 : 1);
+    const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * p.alm_ncomp();
     cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);  // the kernels add warp sums atomically
     if (e != cudaSuccess) return e;
     if (p.prec == LENS_FP32)

@@ -255,7 +255,8 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if (npoints < 0 || npoints > 0x7fffffffLL) return fail(LENS_ERR_INVALID, "npoints must be in [0, 2^31 - 1]");
     if (npoints > 0 && (!theta_d || !phi_d)) return fail(LENS_ERR_INVALID, "theta/phi pointers are NULL");
     if (prec != LENS_FP32 && prec != LENS_FP64) return fail(LENS_ERR_INVALID, "prec must be LENS_FP32 or LENS_FP64");
-    if (flags != 0) return fail(LENS_ERR_INVALID, "flags must be 0");
+    if (flags & ~(unsigned)LENS_GRAD_ONLY) return fail(LENS_ERR_INVALID, "unknown flag");
+    if ((flags & LENS_GRAD_ONLY) && spin == 0) return fail(LENS_ERR_INVALID, "LENS_GRAD_ONLY needs spin > 0");
     if (!(epsilon > 0) || !(epsilon < 1)) return fail(LENS_ERR_INVALID, "epsilon must be in (0, 1)");
     // FP32 floor: at lmax 4096 an FP32 plan with the narrowest kernel setting
     // measured eps_eff 1.2e-6 (forward), set by FP32 rounding of the sums
@@ -267,6 +268,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     Plan *p = new Plan();
     p->lmax = lmax; p->mmax = mmax; p->spin = spin; p->prec = prec;
     p->npts = npoints; p->eps = epsilon;
+    p->grad = (flags & LENS_GRAD_ONLY) != 0;
     p->stream = (cudaStream_t)stream;
     cudaGetDevice(&p->device);
     p->nalm = lens_nalm(lmax, mmax);
@@ -532,6 +534,8 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
     info->W = p->W; info->beta = p->beta; info->sigma = p->sigma;
     info->rows_kept = p->R; info->row_pitch = p->pitch;
     info->workspace_bytes = p->work_bytes; info->plan_bytes = p->plan_bytes;
+    info->flags = p->grad ? (unsigned)LENS_GRAD_ONLY : 0u;
+    info->alm_ncomp = p->alm_ncomp();
     return LENS_OK;
 }
 
@@ -627,7 +631,7 @@ int adjoint_one(const Plan &p, const void *map, void *alm, cudaStream_t st, doub
     return LENS_OK;
 }
 
-size_t alm_bytes(const Plan &p) { return (size_t)p.nalm * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 8 : 16); }
+size_t alm_bytes(const Plan &p) { return plan_alm_bytes(p); }
 size_t map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 2 : 1) * (p.prec == LENS_FP32 ? 4 : 8); }
 size_t ring_bytes(const Plan &p) { return (size_t)p.ncol * p.ntheta * 8; }
 
@@ -710,7 +714,7 @@ static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, v
     const size_t ib = fwd ? alm_bytes(p) : map_bytes(p), ob = fwd ? map_bytes(p) : alm_bytes(p);
     int i = 0;
     // FP32 synthesis of several maps: groups of 4, then 2, share the recursion
-    if (fwd && p.prec == LENS_FP32 && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
+    if (fwd && p.prec == LENS_FP32 && !p.grad && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
         for (int nm = 4; nm >= 2; nm /= 2)
             for (; nmaps - i >= nm; i += nm) {
                 const int r = forward_group(p, (const char *)in_d + i * ib, (char *)out_d + i * ob, nm, st, wpos);

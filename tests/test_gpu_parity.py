@@ -325,3 +325,40 @@ def test_grouped_synthesis_matches_per_map(spin):
         ref = O.synthesis(L, L, spin, th[s], ph[s], a[i], chi[s] if spin else None)
         assert rel(got[i][:, s], ref) <= 1e-5
     plan.close()
+
+
+@pytest.mark.parametrize("spin", [1, 2, 3])
+@pytest.mark.parametrize("prec,eps", PRECS)
+def test_grad_only_matches_full_and_oracle(spin, prec, eps):
+    """LENS_GRAD_ONLY (Sect. 4, vanishing curl): synthesis of G alone equals the
+    full transform with C = 0, and the adjoint returns the full adjoint's G;
+    both against the oracle.  Odd spins exercise the (-1)^s terms."""
+    L, n = 100, 20000
+    th, ph, chi = W.random_points(n, 90 + spin)
+    full = LensPlan(L, th, ph, chi, spin=spin, epsilon=eps, precision=prec, device=DEV)
+    grad = LensPlan(L, th, ph, chi, spin=spin, epsilon=eps, precision=prec, grad_only=True, device=DEV)
+    assert grad.alm_ncomp == 1 and grad.info()["alm_ncomp"] == 1 and grad.info()["flags"] == 1
+    a = make_alm(L, spin, 600)
+    a[1] = 0.0
+    mf = full.synthesis(gpu_alm(full, a)).cpu().numpy()
+    mg = grad.synthesis(gpu_alm(grad, a[:1])).cpu().numpy()
+    tol = 1e-6 if prec == "fp32" else 1e-13
+    assert rel(mg, mf) <= tol
+    s = np.arange(0, n, 97)
+    assert rel(mg[:, s], O.synthesis(L, L, spin, th[s], ph[s], a, chi[s])) <= eps
+    y = np.random.default_rng(spin).standard_normal((2, n))
+    af = full.adjoint(gpu_map(full, y)).cpu().numpy()
+    ag = grad.adjoint(gpu_map(grad, y)).cpu().numpy()
+    assert ag.shape == (1, full.nalm) and rel(ag[0], af[0]) <= tol
+    k = np.arange(0, n, 41)
+    assert rel(grad.adjoint(gpu_map(grad, np.where(np.isin(np.arange(n), k), y, 0.0))).cpu().numpy()[0],
+               O.adjoint(L, L, spin, th[k], ph[k], y[:, k], chi[k])[0]) <= eps
+    full.close()
+    grad.close()
+
+
+def test_grad_only_needs_spin():
+    th, ph, _ = W.random_points(10, 1)
+    with pytest.raises(LensError) as ex:
+        LensPlan(8, th, ph, spin=0, grad_only=True, device=DEV)
+    assert ex.value.status == 1
