@@ -81,7 +81,22 @@ typedef enum {
      * lens_synthesis takes C = 0 and lens_adjoint returns only G.  The
      * Legendre steps accumulate two sums per degree instead of four.
      * Needs spin > 0 (LENS_ERR_INVALID otherwise). */
-    LENS_GRAD_ONLY = 1
+    LENS_GRAD_ONLY = 1,
+    /* Bit-reproducible adjoints.  The two steps that add with atomics (the
+     * spreading of Sect. 3's NUFFT type 1 and the adjoint Legendre step) then
+     * accumulate in 64-bit fixed point: each term is scaled by a power of two
+     * 2^k and rounded to an integer, and integer additions are exact, so the
+     * result does not depend on their order.  k is chosen per call from a
+     * bound on the sums (spreading: the most points any grid cell receives
+     * times the largest |map value|; adjoint Legendre, per order m: the sum of
+     * |Re| + |Im| of the ring coefficients times sqrt((2 lmax + 1)/(4 pi)) and
+     * the order weight) so that no sum exceeds 2^62; a term loses what lies
+     * below 2^-62 of that bound.  Costs a max-reduction over the map, a sum
+     * over the ring coefficients and two conversion passes per adjoint; FP32
+     * plans hold int64 copies of the grid and of the a_lm sums.  Maps must be
+     * finite (a NaN or infinity makes the whole output NaN).  The forward
+     * transform has no atomics and is reproducible without this flag. */
+    LENS_DETERMINISTIC = 2
 } lens_flags;
 
 typedef struct lens_plan_s *lens_plan;
@@ -130,7 +145,8 @@ typedef struct {
  *              epsilon >= 2e-6 (FP32 rounding alone leaves ~1.2e-6 at lmax
  *              4096), FP64 plans epsilon >= 1e-13.
  *   prec       LENS_FP32 or LENS_FP64.
- *   flags      0 or LENS_GRAD_ONLY (lens_flags); other bits: LENS_ERR_INVALID.
+ *   flags      0, or LENS_GRAD_ONLY and / or LENS_DETERMINISTIC (lens_flags);
+ *              other bits: LENS_ERR_INVALID.
  *   stream     cudaStream_t (NULL = legacy default stream).
  * Synchronises the stream once (coordinate validation).  LENS_ERR_DOMAIN if a
  * coordinate is not finite or theta is outside [0, pi].

@@ -56,7 +56,7 @@ class LensPlan:
                  epsilon: float = 1e-5, precision: str = "fp32", sigma: float | None = None,
                  W: int | None = None, beta: float | None = None, ntheta: int | None = None,
                  legendre_rpt: tuple | None = None, legendre_df32_mmin: int = 0, fft_cluster: int = 0,
-                 grad_only: bool = False, device=None, stream=None):
+                 grad_only: bool = False, deterministic: bool = False, device=None, stream=None):
         lib = _native.load()
         if precision not in _PREC:
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -68,6 +68,7 @@ class LensPlan:
         self.ncomp = 1 if self.spin == 0 else 2  # components of a map
         self.grad_only = bool(grad_only)  # spin s with C = 0: a_lm buffers hold G alone
         self.alm_ncomp = 1 if (self.spin == 0 or self.grad_only) else 2
+        self.deterministic = bool(deterministic)  # bit-reproducible adjoints (fixed-point sums)
         with torch.cuda.device(self.device):
             th = _dev_f64(theta, self.device)
             ph = _dev_f64(phi, self.device)
@@ -84,7 +85,8 @@ class LensPlan:
                                          th.data_ptr() if self.npoints else None,
                                          ph.data_ptr() if self.npoints else None,
                                          ch.data_ptr() if ch is not None else None, float(epsilon),
-                                         _PREC[precision], 1 if self.grad_only else 0, st, ctypes.byref(prm))
+                                         _PREC[precision], (1 if self.grad_only else 0) | (2 if self.deterministic else 0),
+                                         st, ctypes.byref(prm))
             _native.check(rc)
         self._h = handle
         self.nalm = nalm(self.lmax, self.mmax)

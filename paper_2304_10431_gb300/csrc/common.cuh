@@ -83,6 +83,24 @@ __device__ __forceinline__ df32 df_sub_u(df32 a, df32 b)
 
 __device__ __forceinline__ df32 df_scale_pow2(df32 a, float p2) { return {a.h * p2, a.l * p2}; }
 
+// Fixed-point accumulation (deterministic plans): a sum whose terms are
+// bounded by `bound` in total is accumulated as integers in units of 2^-k,
+// with k the largest integer up to 122 such that bound 2^k <= 2^62 (so the
+// int64 sums cannot overflow); returns 2^k, 1 for a zero bound and NaN for a
+// bound that is not finite.
+__device__ __forceinline__ double fx_unit(double bound)
+{
+    if (!(bound <= 1.7976931348623157e308)) return __longlong_as_double(0x7ff8000000000000LL);
+    if (bound <= 0.0) return 1.0;
+    int e = ilogb(bound) + 1;  // bound < 2^e
+    if (e < -60) e = -60;
+    return ldexp(1.0, 62 - e);
+}
+// integer sum v in units of 1 / (inv) -> value, one rounding
+template <typename T> __device__ __forceinline__ T fx_value(long long v, double inv);
+template <> __device__ __forceinline__ float fx_value<float>(long long v, double inv) { return __ll2float_rn(v) * (float)inv; }
+template <> __device__ __forceinline__ double fx_value<double>(long long v, double inv) { return __ll2double_rn(v) * inv; }
+
 // Status flags written by kernels (bitwise OR).  No kernel traps.
 enum : unsigned {
     FLAG_DOMAIN = 1u,     // point coordinate not finite / theta outside [0, pi]

@@ -78,6 +78,13 @@ struct Plan {
     void *ring_batch = nullptr, *coef_batch = nullptr;
     bool group_maps = true;  // false: every map runs alone (lens_plan_set_grouping)
     bool grad = false;       // gradient-only spin s plan (C = 0): a_lm holds G alone
+    // deterministic plans (LENS_DETERMINISTIC): fixed-point accumulation
+    bool det = false;
+    void *fx_grid = nullptr;                  // FP32 plans: int64 spreading grid [R][pitch][ncomp]
+    void *fx_alm = nullptr;                   // FP32 plans: int64 adjoint a_lm sums [alm_ncomp][nalm][2]
+    double *fx_scale = nullptr;               // [0] spreading unit, [1 + m] adjoint Legendre unit of order m
+    unsigned long long *fx_maxbits = nullptr; // max |map value| of a call (bits of a double)
+    uint32_t *fx_kmax = nullptr;              // most points any grid cell receives
     int alm_ncomp() const { return spin && !grad ? 2 : 1; }
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;

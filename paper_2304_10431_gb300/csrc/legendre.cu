@@ -189,6 +189,11 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
     static __device__ __forceinline__ A shfl_xor(A v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
     // *dst += c v (c the monic-form scale of the degree)
     static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, v * (float)c); }
+    // deterministic plans: the same term in fixed point, units of 1 / unit (a power of two)
+    static __device__ __forceinline__ void atomic_add_fx(unsigned long long *dst, A v, double c, double unit)
+    {
+        atomicAdd(dst, (unsigned long long)__float2ll_rn(v * (float)c * (float)unit));
+    }
     // prepared coefficient (re, im) of entry idx, component comp
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
@@ -275,6 +280,10 @@ struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static __device__ __forceinline__ A ascale(A a, double f) { return a * f; }
     static __device__ __forceinline__ A shfl_xor(A v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
     static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, v * c); }
+    static __device__ __forceinline__ void atomic_add_fx(unsigned long long *dst, A v, double c, double unit)
+    {
+        atomicAdd(dst, (unsigned long long)__double2ll_rn(v * c * unit));
+    }
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
         const double2 v = __ldg((const double2 *)tab + comp * nalm + idx);
@@ -339,6 +348,10 @@ struct PolDD : PolDF {
         return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
     }
     static __device__ __forceinline__ void atomic_add(R *dst, A v, double c) { atomicAdd(dst, aout(v) * c); }
+    static __device__ __forceinline__ void atomic_add_fx(unsigned long long *dst, A v, double c, double unit)
+    {
+        atomicAdd(dst, (unsigned long long)__double2ll_rn(aout(v) * c * unit));
+    }
     // table entry: float4 (re_h, re_l, im_h, im_l)
     static __device__ __forceinline__ void coef(const void *tab, int64_t nalm, int comp, int64_t idx, K &re, K &im)
     {
@@ -808,11 +821,12 @@ template <class P, int RPT, bool SPIN, bool GRAD = false> struct AdjIn {
 
 // Adds the warp sums of the degrees lb + i (value index i * NCOMP + c),
 // times the monic scale c_l and the order weight wm, into a_lm (spin 0) or
-// G, C (spin s).
+// G, C (spin s); with fx (deterministic plans) into the fixed-point sums fx
+// (same layout, units of 1 / fxu) instead.
 template <class P, bool SPIN, int NV>
 __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *out, const double *__restrict__ sc,
                                       double wm, int64_t base, int64_t nalm, int m, int lb, int lmax,
-                                      decltype(P::fac(0)) sgs)
+                                      decltype(P::fac(0)) sgs, unsigned long long *fx, double fxu)
 {
     using A = typename P::A;
     using Sg = decltype(P::fac(0));
@@ -824,8 +838,11 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
     const int i = v / NCOMP, c = v % NCOMP;
     const int l = lb + i;
     if (!SPIN) {
-        if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1))
-            P::atomic_add(out + 2 * (base + l) + c, tot, __ldg(sc + l) * wm);
+        if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1)) {
+            const int64_t dst = 2 * (base + l) + c;
+            if (fx) P::atomic_add_fx(fx + dst, tot, __ldg(sc + l) * wm, fxu);
+            else P::atomic_add(out + dst, tot, __ldg(sc + l) * wm);
+        }
     } else {
         // lanes hold U.re, U.im, V.re, V.im of degree l at c = 0..3; the G/C
         // split is linear, so each warp adds its share directly:
@@ -840,7 +857,10 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
             else if (c == 1) { val = P::ascale(P::aadd(tot, P::ascale(other, -sgs)), -h); dst = 2 * (base + l) + 1; }
             else if (c == 2) { val = P::ascale(P::aadd(other, P::ascale(tot, -sgs)), h); dst = 2 * (nalm + base + l) + 1; }
             else { val = P::ascale(P::aadd(other, P::ascale(tot, sgs)), -h); dst = 2 * (nalm + base + l); }
-            if (!(m == 0 && (c == 1 || c == 2))) P::atomic_add(out + dst, val, __ldg(sc + l) * wm);
+            if (!(m == 0 && (c == 1 || c == 2))) {
+                if (fx) P::atomic_add_fx(fx + dst, val, __ldg(sc + l) * wm, fxu);
+                else P::atomic_add(out + dst, val, __ldg(sc + l) * wm);
+            }
         }
     }
 }
@@ -856,7 +876,8 @@ template <int NV> constexpr int kRowStride = NV + 4;
 
 template <bool SPIN, int NV>
 __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float *out, const double *__restrict__ sc,
-                                           double wm, int64_t base, int64_t nalm, int m, int lb, int lmax, float sgs)
+                                           double wm, int64_t base, int64_t nalm, int m, int lb, int lmax, float sgs,
+                                           unsigned long long *fx, double fxu)
 {
     static_assert(NV == 16 || NV == 32, "NV must be 16 or 32");
     constexpr int NCOMP = SPIN ? 4 : 2;
@@ -885,7 +906,11 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
     const int i = v / NCOMP, c = v % NCOMP;
     const int l = lb + i;
     if (!SPIN) {
-        if (lane < NV && l <= lmax && !(m == 0 && c == 1)) atomicAdd(out + 2 * (base + l) + c, tot * (float)(__ldg(sc + l) * wm));
+        if (lane < NV && l <= lmax && !(m == 0 && c == 1)) {
+            const int64_t dst = 2 * (base + l) + c;
+            if (fx) PolDF::atomic_add_fx(fx + dst, tot, __ldg(sc + l) * wm, fxu);
+            else atomicAdd(out + dst, tot * (float)(__ldg(sc + l) * wm));
+        }
     } else {
         const float other = __shfl_xor_sync(0xffffffffu, tot, 2);  // U <-> V of the same l
         if (lane < NV && l <= lmax) {
@@ -895,7 +920,10 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
             else if (c == 1) { val = -0.5f * (tot - sgs * other); dst = 2 * (base + l) + 1; }
             else if (c == 2) { val = 0.5f * (other - sgs * tot); dst = 2 * (nalm + base + l) + 1; }
             else { val = -0.5f * (other + sgs * tot); dst = 2 * (nalm + base + l); }
-            if (!(m == 0 && (c == 1 || c == 2))) atomicAdd(out + dst, val * (float)(__ldg(sc + l) * wm));
+            if (!(m == 0 && (c == 1 || c == 2))) {
+                if (fx) PolDF::atomic_add_fx(fx + dst, val, __ldg(sc + l) * wm, fxu);
+                else atomicAdd(out + dst, val * (float)(__ldg(sc + l) * wm));
+            }
         }
     }
 }
@@ -929,7 +957,8 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  const double *__restrict__ scale, RingTab rt,
                                                  typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
-                                                 int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos)
+                                                 int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos,
+                                                 unsigned long long *fx, const double *__restrict__ fxs)
 {
     using A = typename P::A;
     using R = typename P::R;
@@ -953,6 +982,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     R *out = reinterpret_cast<R *>(alm);
     const int lf = l0 + 1;
     const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
+    const double fxu = fx ? fxs[1 + m] : 0.0;  // deterministic plans: fixed-point unit of order m
 
     Rings<P, RPT, SPIN> st;
     st.init(rt, rp0, nnorth, m, s, lognorm[m]);
@@ -964,7 +994,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
         in.add_rt(st, true, p0);  // l0 = lf - 1
-        flush<P, FSPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs);
+        flush<P, FSPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs, fx, fxu);
     }
     int l = lf;
     A part[NV];
@@ -984,9 +1014,10 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
         if (reg == 0) adj_block<P, RPT, SPIN, 0, GRAD>(st, in, part, reca, rect, l);
         else adj_block<P, RPT, SPIN, 2, GRAD>(st, in, part, reca, rect, l);
         if constexpr (kSmemFlush)
-            flush_smem<FSPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, base, nalm, m, l, lmax, sgs);
+            flush_smem<FSPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, base, nalm, m, l, lmax, sgs, fx,
+                                  fxu);
         else
-            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
+            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs, fx, fxu);
     }
     if (l <= lmax) {  // tail: fewer than kBlk degrees, general path
 #pragma unroll
@@ -998,8 +1029,56 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                 in.add_rt(st, (j & 1) != 0, part + j * NCOMP);
             }
         }
-        flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs);
+        flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs, fx, fxu);
     }
+}
+
+// ---------------------------------------------- fixed point (deterministic plans)
+// Unit of order m: every a_lm of the adjoint is a sum over rings of ring
+// coefficients times lambda values, |lambda| <= sqrt((2 lmax + 1)/(4 pi)),
+// so |a_lm| <= S_m sqrt((2 lmax + 1)/(4 pi)) max(w_m, 1) with S_m the sum of
+// |Re| + |Im| over the ring coefficients of order m (columns +m and -m for
+// spin s); the same bounds every warp's partial sum.  One CTA per m, reduced
+// in a fixed order.  fxs[1 + m] = fx_unit(bound).
+template <typename C>
+__global__ void k_fx_units(const C *__restrict__ ring, int ntheta, int mmax, bool spin, double wlam,
+                           double *__restrict__ fxs)
+{
+    __shared__ double red[256];
+    const int m = blockIdx.x;
+    double a = 0.0;
+    const int64_t c0 = (int64_t)(spin ? mmax + m : m) * ntheta, c1 = (int64_t)(mmax - m) * ntheta;
+    for (int j = threadIdx.x; j < ntheta; j += blockDim.x) {
+        const C v = ring[c0 + j];
+        a += fabs((double)v.x) + fabs((double)v.y);
+        if (spin && m > 0) {
+            const C w = ring[c1 + j];
+            a += fabs((double)w.x) + fabs((double)w.y);
+        }
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) fxs[1 + m] = fx_unit(red[0] * wlam * (1.0 + 0x1p-20));
+}
+
+// a_lm = fixed-point sum / unit of its order (fx and alm may coincide)
+template <typename R>
+__global__ void k_fx_to_alm(const unsigned long long *fx, R *alm, int lmax, int64_t nalm, int ncomp,
+                            const double *__restrict__ fxs)
+{
+    const int m = blockIdx.y;
+    const double inv = 1.0 / fxs[1 + m];
+    const int64_t base = alm_base(lmax, m);
+    for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x)
+        for (int c = 0; c < ncomp; ++c)
+            for (int k = 0; k < 2; ++k) {
+                const int64_t i = 2 * (c * nalm + base + l) + k;
+                alm[i] = fx_value<R>((long long)fx[i], inv);
+            }
 }
 
 // ------------------------------------------------------- coefficient tables
@@ -1131,7 +1210,7 @@ template <class P, bool SPIN, bool GRAD = false> size_t adj_smem_bytes(int warps
 
 template <class P, int RPT, bool SPIN, bool GRAD = false>
 cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                       void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
+                       void *alm, int m_begin, int m_end, cudaStream_t st, double wpos, void *fx)
 {
     if (m_end <= m_begin) return cudaSuccess;
     dim3 grid(sh.chunks, m_end - m_begin);
@@ -1139,7 +1218,8 @@ cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring
     k_leg_adj<P, RPT, SPIN, GRAD><<<grid, block, adj_smem_bytes<P, SPIN, GRAD>(sh.warps), st>>>(
                                                     (const typename P::C *)ring, ta, tt, p.lognorm, p.scale, p.rings,
                                                     (typename P::C *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
-                                                    p.nalm, m_begin, wpos);
+                                                    p.nalm, m_begin, wpos, (unsigned long long *)fx,
+                                                    p.fx_scale);
     return cudaGetLastError();
 }
 
@@ -1153,10 +1233,10 @@ cudaError_t fwd_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, c
 
 template <class P, bool SPIN, bool GRAD = false>
 cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                    void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
+                    void *alm, int m_begin, int m_end, cudaStream_t st, double wpos, void *fx)
 {
-    if (sh.rpt == 1) return adj_launch<P, 1, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
-    return adj_launch<P, 2, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    if (sh.rpt == 1) return adj_launch<P, 1, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
+    return adj_launch<P, 2, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
 }
 
 template <class P>
@@ -1170,11 +1250,11 @@ cudaError_t fwd_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, 
 
 template <class P>
 cudaError_t adj_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, const void *ta, const void *tt,
-                     void *alm, int m_begin, int m_end, cudaStream_t st, double wpos)
+                     void *alm, int m_begin, int m_end, cudaStream_t st, double wpos, void *fx)
 {
-    if (!p.spin) return adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
-    return p.grad ? adj_rpt<P, true, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos)
-                  : adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos);
+    if (!p.spin) return adj_rpt<P, false>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
+    return p.grad ? adj_rpt<P, true, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx)
+                  : adj_rpt<P, true>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
 }
 
 // Kernel entry of one (arithmetic, spin, gradient-only, rings-per-thread,
@@ -1320,10 +1400,32 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
     const size_t ebytes = (p.prec == LENS_FP32 ? 8 : 16) * (size_t)p.nalm * p.alm_ncomp();
     cudaError_t e = cudaMemsetAsync(alm, 0, ebytes, st);  // the kernels add warp sums atomically
     if (e != cudaSuccess) return e;
-    if (p.prec == LENS_FP32)
-        return adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos);
-    if ((e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos)) != cudaSuccess) return e;
-    return adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos);
+    // deterministic plans: fixed-point sums (FP32 plans in their own buffer,
+    // FP64 plans in alm itself), units per order from the ring inputs
+    const bool f32 = p.prec == LENS_FP32;
+    void *fx = nullptr;
+    if (p.det) {
+        fx = f32 ? p.fx_alm : alm;
+        if (f32 && (e = cudaMemsetAsync(fx, 0, 16 * (size_t)p.nalm * p.alm_ncomp(), st)) != cudaSuccess) return e;
+        const double lam = sqrt((2.0 * p.lmax + 1.0) / (4.0 * 3.14159265358979323846));
+        const double wmax = (wpos > 1.0 ? wpos : 1.0) * lam;
+        if (f32) k_fx_units<float2><<<p.mmax + 1, 256, 0, st>>>((const float2 *)ring, p.ntheta, p.mmax, p.spin != 0, wmax, p.fx_scale);
+        else k_fx_units<double2><<<p.mmax + 1, 256, 0, st>>>((const double2 *)ring, p.ntheta, p.mmax, p.spin != 0, wmax, p.fx_scale);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (f32) {
+        e = adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos, fx);
+    } else {
+        e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos, fx);
+        if (e == cudaSuccess)
+            e = adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos, fx);
+    }
+    if (e != cudaSuccess || !p.det) return e;
+    const dim3 g(4, p.mmax + 1);
+    const int nc = p.alm_ncomp();
+    if (f32) k_fx_to_alm<float><<<g, 256, 0, st>>>((const unsigned long long *)fx, (float *)alm, p.lmax, p.nalm, nc, p.fx_scale);
+    else k_fx_to_alm<double><<<g, 256, 0, st>>>((const unsigned long long *)fx, (double *)alm, p.lmax, p.nalm, nc, p.fx_scale);
+    return cudaGetLastError();
 }
 
 }  // namespace gsl

@@ -24,6 +24,15 @@
 // plans spread with one global atomic per tap instead: the L2 adds doubles
 // natively, while double additions into shared memory measured 1.9x (spin s)
 // to 2.4x (spin 0) slower at lmax 4096.
+//
+// Deterministic plans (LENS_DETERMINISTIC) spread in 64-bit fixed point: every
+// tap value is scaled by a power of two 2^k and rounded to an integer, and the
+// shared-memory and global atomics add integers, exactly and so in any order.
+// k is chosen per call so that no cell can exceed 2^62: a cell receives at
+// most Kmax points (the largest point count of a tile and its left, upper and
+// upper-left neighbours, whose taps are the only ones that reach it), each
+// contributing |x| psi psi <= max |x|.  A conversion pass then writes the
+// grid in the plan's precision.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -134,6 +143,13 @@ template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta
     return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
 }
 
+// fixed-point term: v 2^k (exact, 2^k a power of two) rounded to an integer
+__device__ __forceinline__ unsigned long long to_fx(float v, float sc) { return (unsigned long long)__float2ll_rn(v * sc); }
+__device__ __forceinline__ unsigned long long to_fx(double v, double sc)
+{
+    return (unsigned long long)__double2ll_rn(v * sc);
+}
+
 // FP64 plans: the 2W weights of every (sorted) point, computed once.
 __global__ void k_weights(const double2 *__restrict__ frac, int64_t n, int W, double beta, double *__restrict__ wts)
 {
@@ -213,64 +229,84 @@ __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, c
     }
 }
 
-// one thread per sorted point, one global atomic per tap (FP64 plans)
-template <typename T, int W, bool SPIN, bool PRE>
+// one thread per sorted point, one global atomic per tap (FP64 plans); FX:
+// fixed-point integers into the same grid memory (scale *fxs)
+template <typename T, bool FX> struct Acc {
+    using type = T;
+};
+template <typename T> struct Acc<T, true> {
+    using type = unsigned long long;
+};
+template <typename T, bool FX>
+__device__ __forceinline__ void acc_add(typename Acc<T, FX>::type *dst, T v, T sc)
+{
+    if constexpr (FX) atomicAdd(dst, to_fx(v, sc));
+    else atomicAdd(dst, v);
+}
+
+template <typename T, int W, bool SPIN, bool PRE, bool FX>
 __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                        const cplx<T> *__restrict__ frac,
                                                        const int32_t *__restrict__ perm,
                                                        const cplx<T> *__restrict__ phase,
                                                        const double *__restrict__ wts, const T *__restrict__ map,
-                                                       int64_t n, int pitch, T beta)
+                                                       int64_t n, int pitch, T beta, const double *__restrict__ fxs)
 {
+    using G = typename Acc<T, FX>::type;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    const T sc = FX ? (T)fxs[0] : T(1);
     const uint32_t c0 = cell[p];
     T wa[W], wb[W];
     tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
     const int32_t src = perm[p];
     if (!SPIN) {
         const T x = map[src];
-        T *g = (T *)grid + c0;
+        G *g = (G *)grid + c0;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
             const T xa = wa[a] * x;
 #pragma unroll
-            for (int b = 0; b < W; ++b) atomicAdd(g + (int64_t)a * pitch + b, xa * wb[b]);
+            for (int b = 0; b < W; ++b) acc_add<T, FX>(g + (int64_t)a * pitch + b, xa * wb[b], sc);
         }
     } else {
         // e^{-i s chi} (Q + i U)
         const cplx<T> ph = phase[p];
         const T q = map[src], u = map[n + src];
         const T zx = ph.x * q + ph.y * u, zy = ph.x * u - ph.y * q;
-        T *g = (T *)grid + 2 * (int64_t)c0;
+        G *g = (G *)grid + 2 * (int64_t)c0;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
             const T xa = wa[a] * zx, ya = wa[a] * zy;
 #pragma unroll
             for (int b = 0; b < W; ++b) {
-                T *q2 = g + 2 * ((int64_t)a * pitch + b);
-                atomicAdd(q2, xa * wb[b]);
-                atomicAdd(q2 + 1, ya * wb[b]);
+                G *q2 = g + 2 * ((int64_t)a * pitch + b);
+                acc_add<T, FX>(q2, xa * wb[b], sc);
+                acc_add<T, FX>(q2 + 1, ya * wb[b], sc);
             }
         }
     }
 }
 
-template <typename T, int W, bool SPIN, bool PRE>
+// FX: fixed-point integers in shared memory and in the grid (scale *fxs)
+template <typename T, int W, bool SPIN, bool PRE, bool FX>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                            const cplx<T> *__restrict__ frac,
                                                            const int32_t *__restrict__ perm,
                                                            const cplx<T> *__restrict__ phase,
                                                            const double *__restrict__ wts, const T *__restrict__ map,
                                                            int64_t n, int pitch, int R, int ntc,
-                                                           const uint32_t *__restrict__ tile_start, T beta)
+                                                           const uint32_t *__restrict__ tile_start, T beta,
+                                                           const double *__restrict__ fxs)
 {
+    using G = typename Acc<T, FX>::type;
     constexpr int TR = kTileR + W - 1, TC = kTileC + W - 1, NC = SPIN ? 2 : 1;
-    __shared__ T buf[TR * TC * NC];
+    __shared__ G buf[TR * TC * NC];
     const int t = blockIdx.x;
     const uint32_t p0 = tile_start[t], p1 = tile_start[t + 1];
     if (p0 == p1) return;
-    for (int i = threadIdx.x; i < TR * TC * NC; i += blockDim.x) buf[i] = T(0);
+    const T sc = FX ? (T)fxs[0] : T(1);
+    for (int i = threadIdx.x; i < TR * TC * NC; i += blockDim.x) buf[i] = G(0);
     __syncthreads();
     const int r0 = (t / ntc) * kTileR, c0 = (t % ntc) * kTileC;
     for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -280,14 +316,14 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
         T wa[W], wb[W];
         tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
         const int32_t src = perm[p];
-        T *b0 = buf + (lr * TC + lc) * NC;
+        G *b0 = buf + (lr * TC + lc) * NC;
         if (!SPIN) {
             const T x = map[src];
 #pragma unroll
             for (int a = 0; a < W; ++a) {
                 const T xa = wa[a] * x;
 #pragma unroll
-                for (int b = 0; b < W; ++b) atomicAdd(b0 + a * TC + b, xa * wb[b]);
+                for (int b = 0; b < W; ++b) acc_add<T, FX>(b0 + a * TC + b, xa * wb[b], sc);
             }
         } else {
             // e^{-i s chi} (Q + i U)
@@ -299,28 +335,80 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
                 const T xa = wa[a] * zx, ya = wa[a] * zy;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    T *q2 = b0 + 2 * (a * TC + b);
-                    atomicAdd(q2, xa * wb[b]);
-                    atomicAdd(q2 + 1, ya * wb[b]);
+                    G *q2 = b0 + 2 * (a * TC + b);
+                    acc_add<T, FX>(q2, xa * wb[b], sc);
+                    acc_add<T, FX>(q2 + 1, ya * wb[b], sc);
                 }
             }
         }
     }
     __syncthreads();
-    T *g = (T *)grid;
+    G *g = (G *)grid;
     for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
         const int gr = r0 + i / TC, gc = c0 + i % TC;
         if (gr >= R || gc >= pitch) continue;
         const int64_t o = (int64_t)gr * pitch + gc;
         if (!SPIN) {
-            const T v = buf[i];
-            if (v != T(0)) atomicAdd(g + o, v);
+            const G v = buf[i];
+            if (v != G(0)) atomicAdd(g + o, v);
         } else {
-            const T vx = buf[2 * i], vy = buf[2 * i + 1];
-            if (vx != T(0)) atomicAdd(g + 2 * o, vx);
-            if (vy != T(0)) atomicAdd(g + 2 * o + 1, vy);
+            const G vx = buf[2 * i], vy = buf[2 * i + 1];
+            if (vx != G(0)) atomicAdd(g + 2 * o, vx);
+            if (vy != G(0)) atomicAdd(g + 2 * o + 1, vy);
         }
     }
+}
+
+// ---------------------------------------------- fixed point (deterministic plans)
+// Largest |x| (spin 0) or |Q| + |U| (spin s) of a map, as the bits of a
+// non-negative double, which order like unsigned integers (a NaN input gives
+// NaN bits, above those of infinity).
+template <typename T, bool SPIN>
+__global__ void k_fx_maxabs(const T *__restrict__ map, int64_t n, unsigned long long *__restrict__ out)
+{
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = SPIN ? fabs((double)map[i]) + fabs((double)map[n + i]) : fabs((double)map[i]);
+        a = (v > a || v != v) ? v : a;
+    }
+    unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+        b = o > b ? o : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, b);
+}
+
+// unit[0] = 2^k with k the largest integer (up to 122) such that
+// Kmax max|x| 2^k <= 2^62; NaN when the bound is not finite
+__global__ void k_fx_grid_unit(const unsigned long long *__restrict__ maxbits, const uint32_t *__restrict__ kmax,
+                               double *__restrict__ unit)
+{
+    unit[0] = fx_unit((double)*kmax * __longlong_as_double((long long)*maxbits));
+}
+
+// grid[i] = fx[i] / unit in the plan's precision (fx and grid may coincide)
+template <typename T>
+__global__ void k_fx_to_grid(const unsigned long long *fx, T *grid, int64_t n, const double *__restrict__ unit)
+{
+    const double inv = 1.0 / unit[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        grid[i] = fx_value<T>((long long)fx[i], inv);
+}
+
+// Kmax: the most points any cell can receive (a tile's count plus those of
+// its left, upper and upper-left neighbours); start as k_tile_bounds writes it
+__global__ void k_tile_kmax(const uint32_t *__restrict__ start, int ntr, int ntc, uint32_t *__restrict__ kmax)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntr * ntc) return;
+    const int tr = t / ntc, tc = t % ntc;
+    auto cnt = [&](int r, int c) -> uint32_t {
+        if (r < 0 || c < 0) return 0u;
+        const int u = r * ntc + c;
+        return start[u + 1] - start[u];
+    };
+    atomicMax(kmax, cnt(tr, tc) + cnt(tr, tc - 1) + cnt(tr - 1, tc) + cnt(tr - 1, tc - 1));
 }
 
 template <typename T, bool SPIN, int W>
@@ -347,20 +435,33 @@ template <typename T, bool SPIN, int W>
 cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st)
 {
     if (p.npts == 0) return cudaSuccess;
+    const double *fxs = p.fx_scale;
     if constexpr (std::is_same<T, double>::value) {
         const unsigned blocks = (unsigned)((p.npts + 255) / 256);
-        if (p.wts)
-            k_spread_direct<T, W, SPIN, true><<<blocks, 256, 0, st>>>(
-                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-                p.pitch, (T)p.beta);
-        else
-            k_spread_direct<T, W, SPIN, false><<<blocks, 256, 0, st>>>(
-                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-                p.pitch, (T)p.beta);
+        const cplx<T> *fr = (const cplx<T> *)p.frac, *ph = (const cplx<T> *)p.phase;
+        if (p.det) {
+            if (p.wts)
+                k_spread_direct<T, W, SPIN, true, true><<<blocks, 256, 0, st>>>(
+                    grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
+            else
+                k_spread_direct<T, W, SPIN, false, true><<<blocks, 256, 0, st>>>(
+                    grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
+        } else if (p.wts) {
+            k_spread_direct<T, W, SPIN, true, false><<<blocks, 256, 0, st>>>(
+                grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
+        } else {
+            k_spread_direct<T, W, SPIN, false, false><<<blocks, 256, 0, st>>>(
+                grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
+        }
     } else {
-        k_spread<T, W, SPIN, false><<<(unsigned)p.ntiles, kSpreadThreads, 0, st>>>(
-            grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-            p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta);
+        if (p.det)
+            k_spread<T, W, SPIN, false, true><<<(unsigned)p.ntiles, kSpreadThreads, 0, st>>>(
+                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
+                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs);
+        else
+            k_spread<T, W, SPIN, false, false><<<(unsigned)p.ntiles, kSpreadThreads, 0, st>>>(
+                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
+                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs);
     }
     return cudaGetLastError();
 }
@@ -419,11 +520,42 @@ cudaError_t launch_interp(const Plan &p, const void *grid, void *map, cudaStream
 cudaError_t launch_spread(const Plan &p, const void *map, void *grid, cudaStream_t st)
 {
     const size_t eb = (p.prec == LENS_FP32 ? 4 : 8) * (p.spin ? 2 : 1);
+    const size_t ncell = (size_t)p.R * p.pitch * (p.spin ? 2 : 1);
     cudaError_t e = cudaMemsetAsync(grid, 0, eb * (size_t)p.R * p.pitch, st);
     if (e != cudaSuccess) return e;
-    if (p.prec == LENS_FP32)
-        return p.spin ? spread_dispatch<float, true>(p, map, grid, st) : spread_dispatch<float, false>(p, map, grid, st);
-    return p.spin ? spread_dispatch<double, true>(p, map, grid, st) : spread_dispatch<double, false>(p, map, grid, st);
+    const bool f32 = p.prec == LENS_FP32;
+    if (!p.det) {
+        if (f32)
+            return p.spin ? spread_dispatch<float, true>(p, map, grid, st)
+                          : spread_dispatch<float, false>(p, map, grid, st);
+        return p.spin ? spread_dispatch<double, true>(p, map, grid, st)
+                      : spread_dispatch<double, false>(p, map, grid, st);
+    }
+    // fixed point: FP32 plans accumulate in their own int64 grid, FP64 plans in place
+    void *fxg = f32 ? p.fx_grid : grid;
+    if (f32 && (e = cudaMemsetAsync(fxg, 0, 8 * ncell, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.fx_maxbits, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    const unsigned mb = (unsigned)std::min<int64_t>((p.npts + 255) / 256, 152 * 8);
+    if (p.npts > 0) {
+        if (f32) {
+            if (p.spin) k_fx_maxabs<float, true><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.fx_maxbits);
+            else k_fx_maxabs<float, false><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.fx_maxbits);
+        } else {
+            if (p.spin) k_fx_maxabs<double, true><<<mb, 256, 0, st>>>((const double *)map, p.npts, p.fx_maxbits);
+            else k_fx_maxabs<double, false><<<mb, 256, 0, st>>>((const double *)map, p.npts, p.fx_maxbits);
+        }
+    }
+    k_fx_grid_unit<<<1, 1, 0, st>>>(p.fx_maxbits, p.fx_kmax, p.fx_scale);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (f32)
+        e = p.spin ? spread_dispatch<float, true>(p, map, fxg, st) : spread_dispatch<float, false>(p, map, fxg, st);
+    else
+        e = p.spin ? spread_dispatch<double, true>(p, map, fxg, st) : spread_dispatch<double, false>(p, map, fxg, st);
+    if (e != cudaSuccess) return e;
+    const unsigned cb = (unsigned)std::min<size_t>((ncell + 255) / 256, 152 * 16);
+    if (f32) k_fx_to_grid<float><<<cb, 256, 0, st>>>((const unsigned long long *)fxg, (float *)grid, ncell, p.fx_scale);
+    else k_fx_to_grid<double><<<cb, 256, 0, st>>>((const unsigned long long *)fxg, (double *)grid, ncell, p.fx_scale);
+    return cudaGetLastError();
 }
 
 // Point preparation: validate, compute cells/offsets/phases in user order,
@@ -481,6 +613,11 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
     if (nkeys != (uint64_t)p.ntiles) { cleanup(); err = "internal: tile count mismatch"; return cudaErrorInvalidValue; }
     k_tile_bounds<<<(unsigned)((n + 1 + thr - 1) / thr), thr, 0, st>>>(key2, n, p.ntiles, p.tile_start);
     GSL_TRY(cudaGetLastError());
+    if (p.det) {
+        GSL_TRY(cudaMemsetAsync(p.fx_kmax, 0, sizeof(uint32_t), st));
+        k_tile_kmax<<<(unsigned)((p.ntiles + thr - 1) / thr), thr, 0, st>>>(p.tile_start, p.ntiles / ntc, ntc, p.fx_kmax);
+        GSL_TRY(cudaGetLastError());
+    }
     if (p.wts) {
         k_weights<<<blocks, thr, 0, st>>>((const double2 *)p.frac, n, p.W, p.beta, p.wts);
         GSL_TRY(cudaGetLastError());

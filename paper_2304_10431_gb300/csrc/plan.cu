@@ -255,7 +255,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if (npoints < 0 || npoints > 0x7fffffffLL) return fail(LENS_ERR_INVALID, "npoints must be in [0, 2^31 - 1]");
     if (npoints > 0 && (!theta_d || !phi_d)) return fail(LENS_ERR_INVALID, "theta/phi pointers are NULL");
     if (prec != LENS_FP32 && prec != LENS_FP64) return fail(LENS_ERR_INVALID, "prec must be LENS_FP32 or LENS_FP64");
-    if (flags & ~(unsigned)LENS_GRAD_ONLY) return fail(LENS_ERR_INVALID, "unknown flag");
+    if (flags & ~(unsigned)(LENS_GRAD_ONLY | LENS_DETERMINISTIC)) return fail(LENS_ERR_INVALID, "unknown flag");
     if ((flags & LENS_GRAD_ONLY) && spin == 0) return fail(LENS_ERR_INVALID, "LENS_GRAD_ONLY needs spin > 0");
     if (!(epsilon > 0) || !(epsilon < 1)) return fail(LENS_ERR_INVALID, "epsilon must be in (0, 1)");
     // FP32 floor: at lmax 4096 an FP32 plan with the narrowest kernel setting
@@ -269,6 +269,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     p->lmax = lmax; p->mmax = mmax; p->spin = spin; p->prec = prec;
     p->npts = npoints; p->eps = epsilon;
     p->grad = (flags & LENS_GRAD_ONLY) != 0;
+    p->det = (flags & LENS_DETERMINISTIC) != 0;
     p->stream = (cudaStream_t)stream;
     cudaGetDevice(&p->device);
     p->nalm = lens_nalm(lmax, mmax);
@@ -408,6 +409,18 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if ((e = B.alloc(&p->X, esz * (size_t)p->R * p->ncol, true)) != cudaSuccess) return bailc(e, "alloc X");
     if ((e = B.alloc(&p->grid, (esz / 2) * ncomp * (size_t)p->R * p->pitch, true)) != cudaSuccess)
         return bailc(e, "alloc grid");
+    if (p->det) {  // fixed-point sums; the small scalars share one allocation
+        if ((e = B.alloc((void **)&p->fx_scale, sizeof(double) * ((size_t)mmax + 2), false)) != cudaSuccess ||
+            (e = B.alloc((void **)&p->fx_maxbits, 64, false)) != cudaSuccess)
+            return bailc(e, "alloc fixed-point units");
+        p->fx_kmax = reinterpret_cast<uint32_t *>(p->fx_maxbits + 1);
+        if ((e = cudaMemset(p->fx_maxbits, 0, 64)) != cudaSuccess) return bailc(e, "clear fixed-point units");
+        if (prec == LENS_FP32) {
+            if ((e = B.alloc(&p->fx_grid, 8 * (size_t)ncomp * p->R * p->pitch, true)) != cudaSuccess ||
+                (e = B.alloc(&p->fx_alm, 16 * (size_t)p->nalm * p->alm_ncomp(), true)) != cudaSuccess)
+                return bailc(e, "alloc fixed-point sums");
+        }
+    }
     if (npoints > 0) {
         if ((e = B.alloc((void **)&p->cell, sizeof(uint32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc cell");
         if ((e = B.alloc(&p->frac, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc frac");
@@ -534,7 +547,7 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
     info->W = p->W; info->beta = p->beta; info->sigma = p->sigma;
     info->rows_kept = p->R; info->row_pitch = p->pitch;
     info->workspace_bytes = p->work_bytes; info->plan_bytes = p->plan_bytes;
-    info->flags = p->grad ? (unsigned)LENS_GRAD_ONLY : 0u;
+    info->flags = (p->grad ? (unsigned)LENS_GRAD_ONLY : 0u) | (p->det ? (unsigned)LENS_DETERMINISTIC : 0u);
     info->alm_ncomp = p->alm_ncomp();
     return LENS_OK;
 }
