@@ -47,7 +47,7 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
 # source makes the entry stale and the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("legendre_adjoint/spin2/fp32", "3b189f72a88f"): 740843776,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
+    ("legendre_adjoint/spin2/fp32", "d846cc9777e2"): 741691904,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
 }
 
 
