@@ -113,6 +113,12 @@ typedef struct {
                                recursion (0 = choose, -1 = never) */
     int fft_cluster;        /* CTAs per FFT vector: 0 = choose (1, or a cluster of 2 or 4 when
                                the vector exceeds one CTA's shared memory), 1, 2 or 4 to force */
+    int legendre_tables;    /* FP32 plans: 1 = compute the Legendre values once at plan creation
+                               and keep them in device memory (about (2/pi) x n_rings/2 x nalm
+                               floats, twice that for spin s: 46 / 93 GB at lmax 4096); the
+                               Legendre steps then stream them instead of running the
+                               recursion.  0 = recursion (default).  LENS_ERR_NOMEM if the
+                               tables do not fit. */
 } lens_plan_params;
 
 typedef struct {
@@ -130,6 +136,7 @@ typedef struct {
     size_t plan_bytes;         /* point tables and coefficient tables */
     unsigned flags;            /* lens_flags the plan was created with */
     int alm_ncomp;             /* components of an a_lm buffer: 1 (spin 0, LENS_GRAD_ONLY) or 2 */
+    size_t legendre_table_bytes; /* Legendre tables held by the plan (0: recursion) */
 } lens_plan_info_t;
 
 /*

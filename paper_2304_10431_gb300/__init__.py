@@ -56,7 +56,8 @@ class LensPlan:
                  epsilon: float = 1e-5, precision: str = "fp32", sigma: float | None = None,
                  W: int | None = None, beta: float | None = None, ntheta: int | None = None,
                  legendre_rpt: tuple | None = None, legendre_df32_mmin: int = 0, fft_cluster: int = 0,
-                 grad_only: bool = False, deterministic: bool = False, device=None, stream=None):
+                 grad_only: bool = False, deterministic: bool = False, legendre_tables: bool = False,
+                 device=None, stream=None):
         lib = _native.load()
         if precision not in _PREC:
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -78,7 +79,7 @@ class LensPlan:
             self.npoints = int(th.numel())
             rf, ra = legendre_rpt if legendre_rpt else (0, 0)
             prm = PlanParams(float(sigma or 0.0), int(W or 0), float(beta or 0.0), int(ntheta or 0), int(rf), int(ra),
-                             int(legendre_df32_mmin), int(fft_cluster))
+                             int(legendre_df32_mmin), int(fft_cluster), 1 if legendre_tables else 0)
             handle = ctypes.c_void_p()
             st = _stream_handle(stream)
             rc = lib.lens_plan_create_ex(ctypes.byref(handle), self.lmax, self.mmax, self.spin, self.npoints,

@@ -57,7 +57,7 @@ EXPORTS = {
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("W", ctypes.c_int), ("beta", ctypes.c_double),
                 ("ntheta", ctypes.c_int), ("legendre_rpt_fwd", ctypes.c_int), ("legendre_rpt_adj", ctypes.c_int),
-                ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int)]
+                ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int), ("legendre_tables", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -66,7 +66,8 @@ class PlanInfo(ctypes.Structure):
                 ("ntheta_fft", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("W", ctypes.c_int),
                 ("beta", ctypes.c_double), ("sigma", ctypes.c_double), ("rows_kept", ctypes.c_int),
                 ("row_pitch", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
-                ("plan_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint), ("alm_ncomp", ctypes.c_int)]
+                ("plan_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint), ("alm_ncomp", ctypes.c_int),
+                ("legendre_table_bytes", ctypes.c_size_t)]
 
 
 def lib_path() -> str:

@@ -85,6 +85,15 @@ struct Plan {
     double *fx_scale = nullptr;               // [0] spreading unit, [1 + m] adjoint Legendre unit of order m
     unsigned long long *fx_maxbits = nullptr; // max |map value| of a call (bits of a double)
     uint32_t *fx_kmax = nullptr;              // most points any grid cell receives
+    // Legendre tables (FP32 plans, lens_plan_params.legendre_tables): values of
+    // the monic functions per (m, l, ring group), see legendre.cu
+    bool tab = false;
+    float *tab_v = nullptr;          // entries: float (spin 0) / float2 (+s, -s)
+    int64_t *tab_rowbase = nullptr;  // [nalm] row offset - first ring, in entries
+    int *tab_jlo = nullptr;          // [nalm] first ring of the row (nnp: empty)
+    int *tab_lstart = nullptr;       // [mmax+1][ng] first degree of each ring group
+    int tab_nnp = 0, tab_ng = 0, tab_chunks = 0, tab_threads = 0;
+    size_t tab_bytes = 0;
     int alm_ncomp() const { return spin && !grad ? 2 : 1; }
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
     RingTab rings;
@@ -119,6 +128,11 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);
+// Legendre tables: shape, first-entry degrees, rows, values (plan creation)
+void tab_shape(Plan &p);
+cudaError_t launch_tab_first(const Plan &p, int *first);
+cudaError_t launch_tab_rows(const Plan &p, const int *first, int *lstart, int *jlo, int64_t *rowlen);
+cudaError_t launch_tab_fill(const Plan &p);
 // wpos multiplies the orders m > 0 (1 for the transforms themselves; the
 // gradient entry points use 1/2 forward and 2 adjoint)
 cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st, double wpos = 1.0);

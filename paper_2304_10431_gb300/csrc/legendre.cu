@@ -540,6 +540,12 @@ template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false> struct Fwd
             vp[k] = st.template vplus<NW, SCALED>(k);
             if (SPIN) vm[k] = st.template vminus<NW, SCALED>(k);
         }
+        add_vals<ODD>(vp, vm, l);
+    }
+    // contribution of degree l given its values (+s in vp, -s in vm) on the rings
+    template <bool ODD>
+    __device__ __forceinline__ void add_vals(const typename P::V (&vp)[RPT], const typename P::V (&vm)[RPT], int l)
+    {
         const int64_t mstride = (SPIN ? 2 : 1) * nalm;
 #pragma unroll
         for (int b = 0; b < NM; ++b) {
@@ -785,18 +791,31 @@ template <class P, int RPT, bool SPIN, bool GRAD = false> struct AdjIn {
     template <int NW, bool SCALED, bool ODD>
     __device__ __forceinline__ void add(const Rings<P, RPT, SPIN> &st, A *part) const
     {
+        typename P::V vp[RPT], vm[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            const typename P::V vp = st.template vplus<NW, SCALED>(k);
+            vp[k] = st.template vplus<NW, SCALED>(k);
+            if (SPIN) vm[k] = st.template vminus<NW, SCALED>(k);
+        }
+        add_vals<ODD>(vp, vm, part);
+    }
+    // partial sums of one degree given its values (+s in vpv, -s in vmv) on the rings
+    template <bool ODD>
+    __device__ __forceinline__ void add_vals(const typename P::V (&vpv)[RPT], const typename P::V (&vmv)[RPT],
+                                             A *part) const
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const typename P::V vp = vpv[k];
             if (!SPIN) {
                 P::fma(part[0], ODD ? hsr[k] : hnr[k], vp);
                 P::fma(part[1], ODD ? hsi[k] : hni[k], vp);
             } else if (GRAD) {
-                const typename P::V vm = st.template vminus<NW, SCALED>(k);
+                const typename P::V vm = vmv[k];
                 P::fma2(part[0], ODD ? gnr[k] : hnr[k], vp, ODD ? gsr[k] : hsr[k], vm);
                 P::fma2(part[1], ODD ? gni[k] : hni[k], vp, ODD ? gsi[k] : hsi[k], vm);
             } else {
-                const typename P::V vm = st.template vminus<NW, SCALED>(k);
+                const typename P::V vm = vmv[k];
                 // U += lam+ H_m(N) + rel lam- s0 H_m(S) ; V += lam- H_-m(N) + rel lam+ s0 H_-m(S)
                 if (!ODD) {
                     P::fma2(part[0], hnr[k], vp, hsr[k], vm);
@@ -1273,6 +1292,309 @@ template <class P> const void *kernel_of(bool spin, bool grad, int rpt, bool adj
     return rpt == 1 ? (const void *)k_leg_fwd<P, 1, false> : (const void *)k_leg_fwd<P, 2, false>;
 }
 
+// ------------------------------------------------------------ Legendre tables
+// FP32 plans built with Legendre tables store, at plan creation, the value
+// mu_lm(theta_j) (monic form, true magnitude) of every (m, l, ring) that the
+// transforms need, and then read them instead of running the recursion: the
+// Legendre steps become HBM-bound streams (about 2/pi of the dense
+// (m, l, ring) triples are stored: a ring enters at the degree where its
+// value first reaches kTabT, and the evanescent region before it is skipped).
+//
+// Layout.  Rings are taken in groups of four (kTabG), nnp = nnorth rounded up
+// to a multiple of 4.  first(m, j) = the first degree at which ring j's value
+// (either spin) reaches kTabT; lstart(m, q) = max(l0, min over rings
+// j <= 4q + 3 of first(m, j)), which does not increase with q.  Row (m, l)
+// holds the groups q with lstart(m, q) <= l, a suffix [jlo(m, l) / 4, nnp / 4)
+// of the groups; its entry for ring j is at rowbase(m, l) + j (rowbase = row
+// offset - jlo, offsets in entries, multiples of 4).  An entry is a float
+// (spin 0) or a float2 (mu_{+s}, mu_{-s}).  Rings nnorth..nnp-1 hold zeros.
+constexpr float kTabT = 0x1p-40f;
+constexpr int kTabG = 4;
+
+// Shared recursion driver of the two table-building passes: visits every
+// degree l0..lmax with the values of the thread's two rings (word 1, scaled).
+// All threads of the CTA run the whole loop (the renormalisation votes).
+template <bool SPIN, class F>
+__device__ __forceinline__ void tab_walk(const void *rec_a, const void *rec_t, const double *lognorm, RingTab rt,
+                                         int lmax, int spin, int nnorth, int m, int rp0, F &&visit)
+{
+    using P = PolDF;
+    const int s = SPIN ? spin : 0;
+    const int l0 = m > s ? m : s;
+    if (l0 > lmax) return;
+    const int64_t base = alm_base(lmax, m);
+    const P::Tab *reca = SPIN ? reinterpret_cast<const P::Tab *>((const P::TabAT *)rec_a + base)
+                              : (const P::Tab *)rec_a + base;
+    const P::TTab *rect = SPIN ? (const P::TTab *)rec_t + base : nullptr;
+    Rings<P, 2, SPIN> st;
+    st.init(rt, rp0, nnorth, m, s, lognorm[m]);
+    if (!visit(st, l0)) return;
+    for (int l = l0 + 1; l <= lmax; ++l) {
+        if (((l - l0 - 1) & (kBlk - 1)) == 0) st.regime();  // df32 renormalisation
+        st.advance_moved(reca, rect, l);
+        if (!visit(st, l)) return;
+    }
+}
+
+template <bool SPIN>
+__global__ void __launch_bounds__(256) k_tab_first(const void *__restrict__ rec_a, const void *__restrict__ rec_t,
+                                                   const double *__restrict__ lognorm, RingTab rt, int lmax,
+                                                   int spin, int nnorth, int *__restrict__ first)
+{
+    const int m = blockIdx.y;
+    const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    int f[2] = {lmax + 1, lmax + 1};
+    tab_walk<SPIN>(rec_a, rec_t, lognorm, rt, lmax, spin, nnorth, m, rp0, [&](const Rings<PolDF, 2, SPIN> &st, int l) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float v = fabsf(st.template vplus<1, true>(k));
+            if (SPIN) v = fmaxf(v, fabsf(st.template vminus<1, true>(k)));
+            if (f[k] > lmax && v >= kTabT) f[k] = l;
+        }
+        // stop once every ring of the warp has entered (uniform per warp)
+        return !__all_sync(0xffffffffu, f[0] <= lmax && f[1] <= lmax);
+    });
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (rp0 + k < nnorth) first[(int64_t)m * nnorth + rp0 + k] = f[k];
+}
+
+// One thread per order m: lstart (prefix minimum of first) and, per degree,
+// the row's first ring jlo (nnp for an empty row) and its length.
+__global__ void k_tab_rows(const int *__restrict__ first, int lmax, int mmax, int spin, int nnorth, int nnp,
+                           int *__restrict__ lstart, int *__restrict__ jlo, int64_t *__restrict__ rowlen)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > mmax) return;
+    const int l0 = m > spin ? m : spin;
+    const int ng = nnp / kTabG;
+    const int *f = first + (int64_t)m * nnorth;
+    int *ls = lstart + (int64_t)m * ng;
+    int g = lmax + 1;
+    for (int q = 0; q < ng; ++q) {
+        for (int r = 0; r < kTabG; ++r) {
+            const int j = kTabG * q + r;
+            if (j < nnorth && f[j] < g) g = f[j];
+        }
+        ls[q] = g > l0 ? g : l0;
+    }
+    const int64_t base = alm_base(lmax, m);
+    int qlo = ng;
+    for (int l = m; l <= lmax; ++l) {
+        while (qlo > 0 && ls[qlo - 1] <= l && l >= l0) --qlo;
+        jlo[base + l] = kTabG * qlo;
+        rowlen[base + l] = (int64_t)kTabG * (ng - qlo);
+    }
+}
+
+template <bool SPIN>
+__global__ void __launch_bounds__(256) k_tab_fill(const void *__restrict__ rec_a, const void *__restrict__ rec_t,
+                                                  const double *__restrict__ lognorm, RingTab rt, int lmax, int spin,
+                                                  int nnorth, int nnp, const int *__restrict__ jlo,
+                                                  const int64_t *__restrict__ rowbase, float *__restrict__ tab)
+{
+    const int m = blockIdx.y;
+    const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const int64_t base = alm_base(lmax, m);
+    tab_walk<SPIN>(rec_a, rec_t, lognorm, rt, lmax, spin, nnorth, m, rp0, [&](const Rings<PolDF, 2, SPIN> &st, int l) {
+        if (rp0 < nnp && rp0 >= __ldg(jlo + base + l)) {
+            const int64_t e = __ldg(rowbase + base + l) + rp0;  // even: 8-byte (spin 0) / 16-byte (spin s) aligned
+            if (!SPIN) {
+                reinterpret_cast<float2 *>(tab)[e >> 1] = make_float2(st.template vplus<1, true>(0),
+                                                                      st.template vplus<1, true>(1));
+            } else {
+                reinterpret_cast<float4 *>(tab)[e >> 1] =
+                    make_float4(st.template vplus<1, true>(0), st.template vminus<1, true>(0),
+                                st.template vplus<1, true>(1), st.template vminus<1, true>(1));
+            }
+        }
+        return true;
+    });
+}
+
+// Table synthesis: one thread per group of four rings, one order m per
+// grid row.  The lanes of a warp step through the degrees together from the
+// warp's smallest lstart (so that a degree's loads cover one contiguous
+// stretch of its row); a lane before its own lstart loads nothing and adds
+// zeros.  Each iteration first issues the row bases, then kTabU degrees'
+// values, then the sums.
+template <bool SPIN> struct TabU {
+    static constexpr int value = SPIN ? 4 : 8;
+};
+
+template <bool SPIN>
+__device__ __forceinline__ void tab_load(const float *__restrict__ tab, int64_t e, bool on, float (&vp)[kTabG],
+                                         float (&vm)[kTabG])
+{
+    if (!SPIN) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (on) v = __ldg(reinterpret_cast<const float4 *>(tab + e));
+        vp[0] = v.x; vp[1] = v.y; vp[2] = v.z; vp[3] = v.w;
+        vm[0] = vm[1] = vm[2] = vm[3] = 0.f;
+    } else {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (on) {
+            a = __ldg(reinterpret_cast<const float4 *>(tab) + (e >> 1));
+            b = __ldg(reinterpret_cast<const float4 *>(tab) + (e >> 1) + 1);
+        }
+        vp[0] = a.x; vm[0] = a.y; vp[1] = a.z; vm[1] = a.w;
+        vp[2] = b.x; vm[2] = b.y; vp[3] = b.z; vm[3] = b.w;
+    }
+}
+
+template <bool SPIN, bool GRAD>
+__global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, const float *__restrict__ tab,
+                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ lstart,
+                                                 float2 *__restrict__ ring, int lmax, int mmax, int spin, int ntheta,
+                                                 int nnorth, int ng, int64_t nalm)
+{
+    using P = PolDF;
+    using Sg = float;
+    constexpr int U = TabU<SPIN>::value;
+    const int m = blockIdx.y;
+    const int s = SPIN ? spin : 0;
+    const int l0 = m > s ? m : s;
+    if (l0 > lmax) return;  // uniform per CTA
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t base = alm_base(lmax, m);
+    const int j0 = kTabG * q;
+    const int lf = l0 + 1;
+    const int ls = q < ng ? __ldg(lstart + (int64_t)m * ng + q) : lmax + 1;
+    const int lw = __reduce_min_sync(0xffffffffu, ls);
+    FwdAcc<P, kTabG, SPIN, 1, GRAD> acc;
+    acc.init(coef, nalm, base);
+    float vp[kTabG], vm[kTabG];
+    int l = lw;
+    if (l <= lmax && ((l - lf) & 1)) {  // peel one odd degree
+        tab_load<SPIN>(tab, __ldg(rowbase + base + l) + j0, l >= ls, vp, vm);
+        acc.template add_vals<true>(vp, vm, l);
+        ++l;
+    }
+    for (; l + U - 1 <= lmax; l += U) {
+        int64_t rb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) rb[u] = __ldg(rowbase + base + l + u);
+        float up[U][kTabG], um[U][kTabG];
+#pragma unroll
+        for (int u = 0; u < U; ++u) tab_load<SPIN>(tab, rb[u] + j0, l + u >= ls, up[u], um[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u & 1) acc.template add_vals<true>(up[u], um[u], l + u);
+            else acc.template add_vals<false>(up[u], um[u], l + u);
+        }
+    }
+    for (; l <= lmax; ++l) {
+        tab_load<SPIN>(tab, __ldg(rowbase + base + l) + j0, l >= ls, vp, vm);
+        if ((l - lf) & 1) acc.template add_vals<true>(vp, vm, l);
+        else acc.template add_vals<false>(vp, vm, l);
+    }
+    // write-out as k_leg_fwd (s0 = (-1)^(lf - m))
+    const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);
+#pragma unroll
+    for (int k = 0; k < kTabG; ++k) {
+        const int jn = j0 + k;
+        if (jn >= nnorth) continue;
+        const int js = ntheta - 1 - jn;
+        if (!SPIN) {
+            float2 *col = ring + (int64_t)m * ntheta;
+            col[jn] = P::cout(acc.r0[0][k] + acc.r1[0][k], acc.i0[0][k] + acc.i1[0][k]);
+            if (js != jn) col[js] = P::cout(s0 * (acc.r0[0][k] - acc.r1[0][k]), s0 * (acc.i0[0][k] - acc.i1[0][k]));
+        } else if (GRAD) {
+            const Sg ms0 = -s0, sgs = (s & 1) ? Sg(-1) : Sg(1);
+            const float pr = acc.r0[0][k] + acc.r1[0][k], pi = acc.i0[0][k] + acc.i1[0][k];
+            const float qr = acc.r2[0][k] - acc.r3[0][k], qi = acc.i2[0][k] - acc.i3[0][k];
+            float2 *colp = ring + (int64_t)(mmax + m) * ntheta;
+            colp[jn] = P::cout(-pr, -pi);
+            if (js != jn) colp[js] = P::cout(ms0 * qr, ms0 * qi);
+            if (m > 0) {
+                const float ur = acc.r2[0][k] + acc.r3[0][k], ui = acc.i2[0][k] + acc.i3[0][k];
+                const float wr = acc.r0[0][k] - acc.r1[0][k], wi = acc.i0[0][k] - acc.i1[0][k];
+                float2 *colq = ring + (int64_t)(mmax - m) * ntheta;
+                colq[jn] = P::cout(-sgs * ur, sgs * ui);
+                if (js != jn) colq[js] = P::cout(sgs * ms0 * wr, -(sgs * ms0) * wi);
+            }
+        } else {
+            const Sg ms0 = -s0;
+            float2 *colp = ring + (int64_t)(mmax + m) * ntheta;
+            colp[jn] = P::cout(-acc.r0[0][k], -acc.i0[0][k]);
+            if (js != jn) colp[js] = P::cout(ms0 * acc.r1[0][k], ms0 * acc.i1[0][k]);
+            if (m > 0) {
+                float2 *colq = ring + (int64_t)(mmax - m) * ntheta;
+                colq[jn] = P::cout(-acc.r2[0][k], -acc.i2[0][k]);
+                if (js != jn) colq[js] = P::cout(ms0 * acc.r3[0][k], ms0 * acc.i3[0][k]);
+            }
+        }
+    }
+}
+
+// Table adjoint: one thread per group of four rings; degrees in blocks of
+// kBlk starting at l0 (degree lb + i has rel = -1 for even i), each block
+// reduced over the warp like k_leg_adj (a block no lane of the warp has
+// reached is skipped).  Within a block the row bases, then the values of
+// U degrees at a time are loaded before they are summed.
+template <bool SPIN, bool GRAD>
+__global__ void __launch_bounds__(256) k_tab_adj(const float2 *__restrict__ ring, const float *__restrict__ tab,
+                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ lstart,
+                                                 const double *__restrict__ scale, float2 *__restrict__ alm, int lmax,
+                                                 int mmax, int spin, int ntheta, int nnorth, int ng, int64_t nalm,
+                                                 double wpos, unsigned long long *fx, const double *__restrict__ fxs)
+{
+    using P = PolDF;
+    using A = float;
+    constexpr int NCOMP = (SPIN && !GRAD) ? 4 : 2;
+    constexpr bool FSPIN = SPIN && !GRAD;
+    constexpr int NV = kBlk * NCOMP;
+    constexpr int U = TabU<SPIN>::value;
+    const int m = blockIdx.y;
+    const int s = SPIN ? spin : 0;
+    const int l0 = m > s ? m : s;
+    if (l0 > lmax) return;  // uniform per CTA
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = q < ng;
+    const int64_t base = alm_base(lmax, m);
+    const double *sc = scale + base;
+    const int j0 = kTabG * q;
+    const float sgs = (s & 1) ? -1.f : 1.f;
+    const int lf = l0 + 1;
+    const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
+    const double fxu = fx ? fxs[1 + m] : 0.0;
+    float *out = reinterpret_cast<float *>(alm);
+    AdjIn<P, kTabG, SPIN, GRAD> in;
+    in.init(ring, has ? j0 : nnorth, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
+    const int ls = has ? __ldg(lstart + (int64_t)m * ng + q) : lmax + 1;
+    constexpr bool kSmemFlush = FSPIN;
+    extern __shared__ __align__(16) float adj_smem[];
+    float *wbuf = adj_smem + (threadIdx.x >> 5) * (adj_smem_per_warp<FSPIN>() / sizeof(float));
+    A part[NV];
+    for (int lb = l0; lb <= lmax; lb += kBlk) {
+        if (!__any_sync(0xffffffffu, ls <= lb + kBlk - 1)) continue;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[i] = 0.f;
+        int64_t rb[kBlk];
+#pragma unroll
+        for (int i = 0; i < kBlk; ++i) rb[i] = lb + i <= lmax ? __ldg(rowbase + base + lb + i) : 0;
+#pragma unroll
+        for (int h = 0; h < kBlk; h += U) {
+            float up[U][kTabG], um[U][kTabG];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int l = lb + h + u;
+                tab_load<SPIN>(tab, rb[h + u] + j0, l >= ls && l <= lmax, up[u], um[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = h + u;
+                if (i & 1) in.template add_vals<false>(up[u], um[u], part + i * NCOMP);
+                else in.template add_vals<true>(up[u], um[u], part + i * NCOMP);
+            }
+        }
+        if constexpr (kSmemFlush)
+            flush_smem<FSPIN, NV>(part, wbuf, out, sc, wm, base, nalm, m, lb, lmax, sgs, fx, fxu);
+        else
+            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, lb, lmax, sgs, fx, fxu);
+    }
+}
+
 // FP32 forward kernel sharing the recursion among nm = 2 or 4 maps
 const void *kernel_of_batch(bool spin, int rpt, int nm)
 {
@@ -1356,6 +1678,17 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef, p.lmax, p.spin,
                                                                p.nalm, p.mmax + 1, wpos, p.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (p.tab) {
+            const dim3 tg(p.tab_chunks, p.mmax + 1);
+            const auto args = [&](auto kern) {
+                kern<<<tg, p.tab_threads, 0, st>>>(p.coef, p.tab_v, p.tab_rowbase, p.tab_lstart, (float2 *)ring,
+                                                   p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth, p.tab_ng, p.nalm);
+            };
+            if (!p.spin) args(k_tab_fwd<false, false>);
+            else if (p.grad) args(k_tab_fwd<true, true>);
+            else args(k_tab_fwd<true, false>);
+            return cudaGetLastError();
+        }
         return fwd_spin<PolDF>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
     }
     k_coef_prep<double2, double2, float4><<<g, 256, 0, st>>>((const double2 *)alm, p.scale, p.coef, p.lmax, p.spin,
@@ -1413,7 +1746,19 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
         else k_fx_units<double2><<<p.mmax + 1, 256, 0, st>>>((const double2 *)ring, p.ntheta, p.mmax, p.spin != 0, wmax, p.fx_scale);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (f32) {
+    if (f32 && p.tab) {
+        const dim3 tg(p.tab_chunks, p.mmax + 1);
+        const int warps = p.tab_threads / 32;
+        const auto args = [&](auto kern, size_t smem) {
+            kern<<<tg, p.tab_threads, smem, st>>>((const float2 *)ring, p.tab_v, p.tab_rowbase, p.tab_lstart,
+                                                  p.scale, (float2 *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
+                                                  p.tab_ng, p.nalm, wpos, (unsigned long long *)fx, p.fx_scale);
+        };
+        if (!p.spin) args(k_tab_adj<false, false>, 0);
+        else if (p.grad) args(k_tab_adj<true, true>, 0);
+        else args(k_tab_adj<true, false>, (size_t)warps * adj_smem_per_warp<true>());
+        e = cudaGetLastError();
+    } else if (f32) {
         e = adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos, fx);
     } else {
         e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos, fx);
@@ -1425,6 +1770,43 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
     const int nc = p.alm_ncomp();
     if (f32) k_fx_to_alm<float><<<g, 256, 0, st>>>((const unsigned long long *)fx, (float *)alm, p.lmax, p.nalm, nc, p.fx_scale);
     else k_fx_to_alm<double><<<g, 256, 0, st>>>((const unsigned long long *)fx, (double *)alm, p.lmax, p.nalm, nc, p.fx_scale);
+    return cudaGetLastError();
+}
+
+// ---- Legendre tables (plan creation)
+void tab_shape(Plan &p)
+{
+    p.tab_nnp = (p.nnorth + kTabG - 1) / kTabG * kTabG;
+    p.tab_ng = p.tab_nnp / kTabG;
+    p.tab_chunks = (p.tab_ng + 255) / 256;
+    const int per = (p.tab_ng + p.tab_chunks - 1) / p.tab_chunks;
+    p.tab_threads = (per + 31) / 32 * 32;
+}
+
+cudaError_t launch_tab_first(const Plan &p, int *first)
+{
+    const dim3 g((p.tab_nnp + 511) / 512, p.mmax + 1);
+    if (p.spin) k_tab_first<true><<<g, 256, 0, p.stream>>>(p.rec_a, p.rec_t, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth, first);
+    else k_tab_first<false><<<g, 256, 0, p.stream>>>(p.rec_a, p.rec_t, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth, first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_rows(const Plan &p, const int *first, int *lstart, int *jlo, int64_t *rowlen)
+{
+    k_tab_rows<<<(p.mmax + 1 + 127) / 128, 128, 0, p.stream>>>(first, p.lmax, p.mmax, p.spin, p.nnorth, p.tab_nnp,
+                                                              lstart, jlo, rowlen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tab_fill(const Plan &p)
+{
+    const dim3 g((p.tab_nnp + 511) / 512, p.mmax + 1);
+    if (p.spin)
+        k_tab_fill<true><<<g, 256, 0, p.stream>>>(p.rec_a, p.rec_t, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
+                                                  p.tab_nnp, p.tab_jlo, p.tab_rowbase, p.tab_v);
+    else
+        k_tab_fill<false><<<g, 256, 0, p.stream>>>(p.rec_a, p.rec_t, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
+                                                   p.tab_nnp, p.tab_jlo, p.tab_rowbase, p.tab_v);
     return cudaGetLastError();
 }
 

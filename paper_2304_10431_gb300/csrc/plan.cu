@@ -137,6 +137,7 @@ struct Builder {
     {
         *ptr = nullptr;
         if (bytes == 0) bytes = 16;
+        if (p.nallocs >= (int)(sizeof(p.allocs) / sizeof(p.allocs[0]))) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(ptr, bytes);
         if (e != cudaSuccess) return e;
         p.allocs[p.nallocs++] = *ptr;
@@ -230,6 +231,60 @@ int lens_get_last_error(void) { return g_last_status; }
 const char *lens_last_error_message(void) { return g_last_msg; }
 int lens_version(void) { return 100; }
 
+}  // extern "C"
+
+// Legendre tables of an FP32 plan (lens_plan_params.legendre_tables): the
+// degree at which each ring's monic values become non-negligible, the row
+// layout (prefix sums on the host, once per plan), then the values.  Returns
+// a lens_status (the caller destroys the plan on failure).
+static int build_legendre_tables(Plan &p, Builder &B)
+{
+    tab_shape(p);
+    cudaStream_t st = p.stream;
+    int *first = nullptr;
+    int64_t *rowlen = nullptr;
+    cudaError_t e;
+    auto done = [&](cudaError_t err, const char *what) {
+        cudaFree(first);
+        cudaFree(rowlen);
+        return err == cudaSuccess ? LENS_OK : cuda_fail(err, what);
+    };
+    if ((e = cudaMalloc(&first, sizeof(int) * (size_t)(p.mmax + 1) * p.nnorth)) != cudaSuccess) return done(e, "table scratch");
+    if ((e = cudaMalloc(&rowlen, sizeof(int64_t) * (size_t)p.nalm)) != cudaSuccess) return done(e, "table scratch");
+    if ((e = B.alloc((void **)&p.tab_lstart, sizeof(int) * (size_t)(p.mmax + 1) * p.tab_ng, false)) != cudaSuccess ||
+        (e = B.alloc((void **)&p.tab_jlo, sizeof(int) * (size_t)p.nalm, false)) != cudaSuccess)
+        return done(e, "table index");
+    if ((e = launch_tab_first(p, first)) != cudaSuccess) return done(e, "table degrees");
+    if ((e = launch_tab_rows(p, first, p.tab_lstart, p.tab_jlo, rowlen)) != cudaSuccess) return done(e, "table rows");
+    std::vector<int64_t> base(p.nalm);
+    std::vector<int> jlo(p.nalm);
+    if ((e = cudaMemcpyAsync(base.data(), rowlen, sizeof(int64_t) * p.nalm, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(jlo.data(), p.tab_jlo, sizeof(int) * p.nalm, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return done(e, "table rows");
+    int64_t off = 0;
+    for (int64_t i = 0; i < p.nalm; ++i) {
+        const int64_t len = base[i];
+        base[i] = off - jlo[i];
+        off += len;
+    }
+    void *d = nullptr;
+    if ((e = B.upload(&d, base)) != cudaSuccess) return done(e, "table rows");
+    p.tab_rowbase = (int64_t *)d;
+    const size_t esz = p.spin ? 8 : 4;
+    p.tab_bytes = (size_t)off * esz;
+    if ((e = B.alloc((void **)&p.tab_v, p.tab_bytes, false)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(first);
+        cudaFree(rowlen);
+        return fail(LENS_ERR_NOMEM, "Legendre tables: " + std::to_string(p.tab_bytes >> 20) + " MiB not available");
+    }
+    if ((e = launch_tab_fill(p)) != cudaSuccess) return done(e, "table values");
+    return done(cudaStreamSynchronize(st), "table values");
+}
+
+extern "C" {
+
 int lens_plan_destroy(lens_plan pl)
 {
     if (!pl) return LENS_OK;
@@ -301,6 +356,11 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // one CTA holds fft_one elements; a cluster of two or four CTAs 2x or 4x that
     const size_t fft_one = kSmemLimit / esz, fft_max = 4 * fft_one;
     const int force_cl = prm ? prm->fft_cluster : 0;
+    if (prm && prm->legendre_tables != 0) {
+        if (prm->legendre_tables != 1) return bail(LENS_ERR_INVALID, "legendre_tables must be 0 or 1");
+        if (prec != LENS_FP32) return bail(LENS_ERR_INVALID, "Legendre tables are built for FP32 plans only");
+        p->tab = true;
+    }
     if (force_cl != 0 && force_cl != 1 && force_cl != 2 && force_cl != 4)
         return bail(LENS_ERR_INVALID, "fft_cluster must be 0, 1, 2 or 4");
     const double eps_nufft = (prec == LENS_FP32 ? 0.25 : 0.5) * epsilon;
@@ -517,6 +577,13 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if ((e = B.fft(p->fN2, p->N2)) != cudaSuccess) return bailc(e, "fft tables");
 
     if ((e = launch_rec_tables(*p)) != cudaSuccess) return bailc(e, "recursion tables");
+    if (p->tab) {
+        const int rc = build_legendre_tables(*p, B);
+        if (rc != LENS_OK) {
+            lens_plan_destroy(reinterpret_cast<lens_plan>(p));
+            return rc;
+        }
+    }
     {
         std::string err;
         e = launch_prep_points(*p, theta_d, phi_d, spin ? chi_d : nullptr, p->stream, err);
@@ -549,6 +616,7 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
     info->workspace_bytes = p->work_bytes; info->plan_bytes = p->plan_bytes;
     info->flags = (p->grad ? (unsigned)LENS_GRAD_ONLY : 0u) | (p->det ? (unsigned)LENS_DETERMINISTIC : 0u);
     info->alm_ncomp = p->alm_ncomp();
+    info->legendre_table_bytes = p->tab_bytes;
     return LENS_OK;
 }
 
@@ -727,7 +795,7 @@ static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, v
     const size_t ib = fwd ? alm_bytes(p) : map_bytes(p), ob = fwd ? map_bytes(p) : alm_bytes(p);
     int i = 0;
     // FP32 synthesis of several maps: groups of 4, then 2, share the recursion
-    if (fwd && p.prec == LENS_FP32 && !p.grad && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
+    if (fwd && p.prec == LENS_FP32 && !p.grad && !p.tab && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
         for (int nm = 4; nm >= 2; nm /= 2)
             for (; nmaps - i >= nm; i += nm) {
                 const int r = forward_group(p, (const char *)in_d + i * ib, (char *)out_d + i * ob, nm, st, wpos);

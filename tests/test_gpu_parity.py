@@ -395,3 +395,61 @@ def test_deterministic_adjoint_is_bit_reproducible(spin, grad, prec, eps):
     assert np.all(np.isnan(det.adjoint(gpu_map(det, y)).cpu().numpy()))
     det.close()
     ref.close()
+
+
+@pytest.mark.parametrize("spin,grad,det", [(0, False, False), (1, False, False), (2, False, False), (2, True, False),
+                                           (2, False, True), (0, False, True)])
+def test_legendre_tables_match_recursion(spin, grad, det):
+    """FP32 plans with Legendre tables (values of the monic functions computed
+    once at plan creation, non-negligible entries only) give the recursion's
+    results: the stored values are the recursion's own, so the synthesis agrees
+    to ~1e-7 and the adjoint to FP32 reduction order; both meet epsilon against
+    the oracle.  lmax 300 has long evanescent stretches near the poles."""
+    L, n = 300, 30000
+    th, ph, chi = W.random_points(n, 410 + spin)
+    kw = dict(spin=spin, epsilon=1e-5, precision="fp32", grad_only=grad, deterministic=det, device=DEV)
+    tab = LensPlan(L, th, ph, chi if spin else None, legendre_tables=True, **kw)
+    rec = LensPlan(L, th, ph, chi if spin else None, **kw)
+    inf = tab.info()
+    nnp = (inf["ntheta"] + 1) // 2
+    dense = ((nnp + 3) // 4 * 4) * tab.nalm * (8 if spin else 4)
+    assert 0.3 * dense < inf["legendre_table_bytes"] < dense and rec.info()["legendre_table_bytes"] == 0
+    a = make_alm(L, spin, 91)[: tab.alm_ncomp]
+    mt = tab.synthesis(gpu_alm(tab, a)).cpu().numpy()
+    mr = rec.synthesis(gpu_alm(rec, a)).cpu().numpy()
+    assert rel(mt, mr) <= 1e-6
+    s = np.arange(0, n, 113)
+    full = a if not grad else np.stack([a[0], 0 * a[0]])
+    assert rel(mt[:, s], O.synthesis(L, L, spin, th[s], ph[s], full, chi[s] if spin else None)) <= 1e-5
+    nc = 1 if spin == 0 else 2
+    y = np.random.default_rng(12).standard_normal((nc, n))
+    at = tab.adjoint(gpu_map(tab, y)).cpu().numpy()
+    ar = rec.adjoint(gpu_map(rec, y)).cpu().numpy()
+    assert rel(at, ar) <= 1e-6
+    if det:
+        assert np.array_equal(at, tab.adjoint(gpu_map(tab, y)).cpu().numpy())
+    k = np.arange(0, n, 293)
+    ys = np.zeros_like(y)
+    ys[:, k] = y[:, k]
+    orc = O.adjoint(L, L, spin, th[k], ph[k], y[:, k], chi[k] if spin else None)
+    assert rel(tab.adjoint(gpu_map(tab, ys)).cpu().numpy(), orc[:1] if grad else orc) <= 1e-5
+    tab.close()
+    rec.close()
+
+
+def test_legendre_tables_edge_cases():
+    """Tables at tiny band limits, mmax < lmax, spin = lmax; FP64 plans refuse them."""
+    for L, mmax, spin in [(1, 1, 0), (2, 2, 2), (7, 3, 1), (40, 10, 2), (33, 33, 0)]:
+        th, ph, chi = W.random_points(500, L)
+        tab = LensPlan(L, th, ph, chi if spin else None, spin=spin, mmax=mmax, legendre_tables=True, device=DEV)
+        rec = LensPlan(L, th, ph, chi if spin else None, spin=spin, mmax=mmax, device=DEV)
+        a = make_alm(L, spin, 5, mmax=mmax)
+        assert rel(tab.synthesis(gpu_alm(tab, a)).cpu().numpy(), rec.synthesis(gpu_alm(rec, a)).cpu().numpy()) <= 1e-6
+        y = np.random.default_rng(L).standard_normal((1 if spin == 0 else 2, 500))
+        assert rel(tab.adjoint(gpu_map(tab, y)).cpu().numpy(), rec.adjoint(gpu_map(rec, y)).cpu().numpy()) <= 1e-6
+        tab.close()
+        rec.close()
+    th, ph, _ = W.random_points(10, 1)
+    with pytest.raises(LensError) as ex:
+        LensPlan(16, th, ph, precision="fp64", epsilon=1e-10, legendre_tables=True, device=DEV)
+    assert ex.value.status == 1
