@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--lmax", type=int, default=4096)
     ap.add_argument("--nside", type=int, default=2048)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-tables", action="store_true",
+                    help="FP32 plans run the Legendre recursion instead of reading plan-time tables")
+    ap.add_argument("--no-recursion-compare", action="store_true",
+                    help="skip the extra measurement of the FP32 step with recursion plans")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -178,7 +182,8 @@ def legendre_triples(lmax, spin, nnorth):
 
 
 def stage_units(info, npts, spin, prec):
-    """Algorithmic work per launch of each stage (flops for Legendre, bytes otherwise)."""
+    """Algorithmic work per launch of each stage (flops for the Legendre recursion, bytes otherwise;
+    a plan with Legendre tables streams table + coefficients + ring coefficients)."""
     esz = 8 if prec == "fp32" else 16  # complex element
     rsz = esz // 2
     L, nt, ncol = info["lmax"], info["ntheta"], (2 * info["mmax"] + 1 if spin else info["mmax"] + 1)
@@ -190,9 +195,13 @@ def stage_units(info, npts, spin, prec):
     x_b = R * ncol * esz
     grid_b = R * N2 * gsz
     pt_b = npts * (4 + esz + 4 + (esz if spin else 0) + rsz * (2 if spin else 1))
+    nalm = (info["mmax"] + 1) * (2 * L + 2 - info["mmax"]) // 2
+    alm_b = info["alm_ncomp"] * esz * nalm
+    tab_b = info.get("legendre_table_bytes", 0)
+    leg = ("hbm", tab_b + alm_b + ring_b, "GB/s") if tab_b else ("alu", leg_flops, "TFLOP/s")
     return {
-        "legendre_synthesis": ("alu", leg_flops, "TFLOP/s"),
-        "legendre_adjoint": ("alu", leg_flops, "TFLOP/s"),
+        "legendre_synthesis": leg,
+        "legendre_adjoint": leg,
         "theta_fwd": ("hbm", ring_b + x_b, "GB/s"),
         "theta_adj": ("hbm", ring_b + x_b, "GB/s"),
         "phi_fwd": ("hbm", x_b + grid_b, "GB/s"),
@@ -229,9 +238,13 @@ def run_gpu(args):
     th, ph, chi = deflect_on_gpu(th0, ph0, phi_lm, lmax, dev)
     del th0, ph0
 
-    def make(prec, eps):
-        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, device=dev)
-        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, device=dev)
+    def make(prec, eps, tables=False):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, legendre_tables=tables, device=dev)
+        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, legendre_tables=tables, device=dev)
+        torch.cuda.synchronize()
+        make.plan_s = time.perf_counter() - t0
         ct = pT.complex_dtype
         a_T = torch.as_tensor(aT, dtype=ct, device=dev)
         a_P = torch.as_tensor(aEB, dtype=ct, device=dev)
@@ -289,8 +302,10 @@ def run_gpu(args):
             out[name] = npts / (e0.elapsed_time(e1) / reps * 1e-3)
         return out
 
-    # ---------------- FP32 headline
-    pT, pP, b = make("fp32", 1e-5)
+    # ---------------- FP32 headline (plans with Legendre tables unless --no-tables)
+    tables = not args.no_tables
+    pT, pP, b = make("fp32", 1e-5, tables)
+    plan_s = make.plan_s
     info_T, info_P = pT.info(), pP.info()
     clk = ClockSampler(local)
     clk.start()
@@ -325,7 +340,7 @@ def run_gpu(args):
         peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
         achieved = work / (avg * 1e-3) / 1e9
         peak_note = "HBM copy bandwidth (%s)" % peak_src
-    key = ("%s/spin%d/fp32" % (name, 2 if sp else 0), src_hash(KERNEL_FILES[name]))
+    key = ("%s%s/spin%d/fp32" % (name, "_tables" if tables else "", 2 if sp else 0), src_hash(KERNEL_FILES[name]))
     traffic = NCU_TRAFFIC.get(key)
     roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -376,6 +391,19 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3),
                "statistic": "median of %d steps" % len(times), "ms_mean": round(float(np.mean(times)), 3),
                "ms_min": round(float(np.min(times)), 3), "ms_max": round(float(np.max(times)), 3)}
+
+    # ---------------- the same FP32 step with recursion plans (no tables), for comparison
+    recursion = None
+    if tables and not args.no_recursion_compare:
+        rT, rP, rb = make("fp32", 1e-5, False)
+        kr = max(1, min(args.steps, 3))
+        msr = timed(rT, rP, rb, kr, 1, profile=False, nvtx_name="timed_fp32_recursion")
+        recursion = {"value": round(world * npts / (msr * 1e-3), 1), "unit": "lensed points/s",
+                     "ms_per_step": round(msr, 3), "steps": kr,
+                     "what": "same step, FP32 plans without Legendre tables (df32 recursion per call)"}
+        del rb
+        rT.close(); rP.close()
+        torch.cuda.empty_cache()
 
     # ---------------- FP64 plans (epsilon 1e-10), same geometry
     fp64 = None
@@ -432,7 +460,7 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (df32 Legendre recursion)",
+        "dtype": "f32 (Legendre values from plan-time df32 recursion tables)" if tables else "f32 (df32 Legendre recursion)",
         "data": "synthetic: seeded CMB/phi a_lm, HEALPix centres lensed on the GPU",
         "config": {"workload": "T + E/B lensing, lmax 4096, HEALPix Nside %d (%d points), phi lmax %d, "
                                "2.5 arcmin rms deflection, l_damp %.0f" % (nside, npts, lmax, ld),
@@ -441,6 +469,10 @@ def run_gpu(args):
                    "plan_T": {k: info_T[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
                    "plan_EB": {k: info_P[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
                    "l2": "per-step inputs 0.8 GB > 129 MB L2 (no flush)",
+                   "legendre": ({"mode": "tables", "T_bytes": info_T["legendre_table_bytes"],
+                                 "EB_bytes": info_P["legendre_table_bytes"],
+                                 "plan_creation_s": round(plan_s, 3)} if tables else
+                                {"mode": "recursion", "plan_creation_s": round(plan_s, 3)}),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "per_transform": {k: round(v, 1) for k, v in pt.items()},
         "roofline": roofline,
@@ -449,6 +481,7 @@ def run_gpu(args):
         "library": os.path.relpath(lib_path(), ROOT),
         "clocks": clocks,
         "e2e": e2e,
+        "recursion": recursion,
         "fp64": fp64,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
