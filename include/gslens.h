@@ -187,6 +187,12 @@ int lens_plan_info(lens_plan p, lens_plan_info_t *info);
  */
 int lens_synthesis(lens_plan p, const void *alm_d, void *map_d, int nmaps, void *stream);
 
+/* Synchronises `stream` (NULL: the plan's) and reports whether a kernel of
+ * an earlier call on this plan gave up a bounded device-side wait (the bulk
+ * copies of the Legendre-table kernels wait at most ~2 s): LENS_ERR_TIMEOUT,
+ * and the flag is cleared; else LENS_OK. */
+int lens_plan_status(lens_plan p, void *stream);
+
 /* Turns the grouped multi-map synthesis above on (on != 0, the default) or off
  * for this plan.  Returns LENS_ERR_INVALID for a NULL plan. */
 int lens_plan_set_grouping(lens_plan p, int on);

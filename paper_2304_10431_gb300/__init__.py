@@ -103,6 +103,10 @@ class LensPlan:
         _native.check(_native.load().lens_plan_info(self._h, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
 
+    def status(self, stream=None):
+        """Raise LensError (LENS_ERR_TIMEOUT) if a device-side wait of an earlier call gave up."""
+        _native.check(_native.load().lens_plan_status(self._h, _stream_handle(stream)))
+
     def set_grouping(self, on: bool):
         """FP32 plans: synthesise several maps per call with a shared Legendre
         recursion (default on); off runs every map alone."""

@@ -101,10 +101,56 @@ template <typename T> __device__ __forceinline__ T fx_value(long long v, double 
 template <> __device__ __forceinline__ float fx_value<float>(long long v, double inv) { return __ll2float_rn(v) * (float)inv; }
 template <> __device__ __forceinline__ double fx_value<double>(long long v, double inv) { return __ll2double_rn(v) * inv; }
 
+// ---- bulk copies (TMA, non-tensor form) into shared memory, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes barrier initialisation and earlier generic-proxy accesses of shared
+// memory visible to the async proxy (bulk copies)
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16) from a 16-byte aligned global address to a 16-byte
+// aligned shared address; completes `bytes` of the barrier's transaction count
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Whole-warp wait for phase `parity` of bar: every lane observes the
+// completion itself; gives up (uniformly, returning false) after about
+// kWaitCycles clock cycles.
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        const bool done = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        const bool late = clock64() - t0 > kWaitCycles;
+        if (__shfl_sync(0xffffffffu, late, 0)) return false;
+    }
+}
+
 // Status flags written by kernels (bitwise OR).  No kernel traps.
 enum : unsigned {
     FLAG_DOMAIN = 1u,     // point coordinate not finite / theta outside [0, pi]
     FLAG_OOB = 2u,        // an index check failed; the access was skipped
+    FLAG_TIMEOUT = 4u,    // a bounded wait on a bulk copy gave up; the result is incomplete
 };
 
 }  // namespace gsl

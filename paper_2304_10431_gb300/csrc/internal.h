@@ -92,7 +92,8 @@ struct Plan {
     int64_t *tab_rowbase = nullptr;  // [nalm] row offset - first ring, in entries
     int *tab_jlo = nullptr;          // [nalm] first ring of the row (nnp: empty)
     int *tab_lstart = nullptr;       // [mmax+1][ng] first degree of each ring group
-    int tab_nnp = 0, tab_ng = 0, tab_chunks = 0, tab_threads = 0;
+    int tab_nnp = 0, tab_ng = 0;
+    int tab_fchunks = 0, tab_fthreads = 0, tab_achunks = 0, tab_athreads = 0;  // launch shapes
     size_t tab_bytes = 0;
     int alm_ncomp() const { return spin && !grad ? 2 : 1; }
     double *lognorm = nullptr;  // per m: log2 of the start-value normalisation
@@ -129,7 +130,7 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);
 // Legendre tables: shape, first-entry degrees, rows, values (plan creation)
-void tab_shape(Plan &p);
+cudaError_t tab_shape(Plan &p);
 cudaError_t launch_tab_first(const Plan &p, int *first);
 cudaError_t launch_tab_rows(const Plan &p, const int *first, int *lstart, int *jlo, int64_t *rowlen);
 cudaError_t launch_tab_fill(const Plan &p);

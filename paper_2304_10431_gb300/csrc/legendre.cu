@@ -1412,50 +1412,113 @@ __global__ void __launch_bounds__(256) k_tab_fill(const void *__restrict__ rec_a
     });
 }
 
-// Table synthesis: one thread per group of four rings, one order m per
-// grid row.  The lanes of a warp step through the degrees together from the
-// warp's smallest lstart (so that a degree's loads cover one contiguous
-// stretch of its row); a lane before its own lstart loads nothing and adds
-// zeros.  Each iteration first issues the row bases, then kTabU degrees'
-// values, then the sums.
-template <bool SPIN> struct TabU {
-    static constexpr int value = SPIN ? 4 : 8;
+// Staging of one warp's table values through shared memory.  The warp
+// covers 32 ring groups q0 .. q0 + 31; for each degree of a unit of kTabS
+// degrees, the row's stretch [max(jlo, 4 q0), min(4 q0 + 128, nnp)) is brought
+// in by a bulk copy (issued by lane i for degree lb + i) into the degree's
+// slot at the offset of its first ring, so lane t finds its group at
+// slot + t * 4 entries.  Two buffers alternate: while one unit is summed the
+// next is in flight.  Lanes 0..kTabS-1 hold the row base and first ring of
+// the unit to issue next in registers (loaded one unit ahead).  A unit is
+// 4 KB per warp: 8 degrees of spin-0 entries, 4 of spin-s entries.
+template <int ESZ> struct TabStage {
+    static constexpr int kTabS = ESZ == 4 ? 8 : 4;  // degrees per unit
+    static constexpr int SLOT = 32 * kTabG * ESZ;   // bytes per degree
+    static constexpr int BYTES = 2 * kTabS * SLOT;   // both buffers
+    unsigned char *buf;
+    uint64_t *bar;
+    uint32_t ph = 0;  // bit b: parity of buffer b's next phase
+    int64_t nrb = 0;
+    int njlo = 0;
+    bool nok = false;
+    __device__ __forceinline__ void fetch(const int64_t *__restrict__ rowbase, const int *__restrict__ jlo,
+                                          int64_t base, int lb, int l0, int lmax, int lane)
+    {
+        const int l = lb + lane;
+        nok = lane < kTabS && l >= l0 && l <= lmax;
+        if (nok) {
+            nrb = __ldg(rowbase + base + l);
+            njlo = __ldg(jlo + base + l);
+        }
+    }
+    __device__ __forceinline__ void issue(int b, const float *__restrict__ tab, int q0, int nnp, int lane)
+    {
+        int start = 0, bytes = 0;
+        if (nok) {
+            const int lo = max(njlo, kTabG * q0), hi = min(kTabG * (q0 + 32), nnp);
+            if (lo < hi) {
+                start = lo;
+                bytes = (hi - lo) * ESZ;
+            }
+        }
+        const int total = __reduce_add_sync(0xffffffffu, bytes);
+        __syncwarp();          // the buffer's previous contents have been read
+        fence_async_shared();  // ... before the bulk copies overwrite it
+        if (lane == 0) mbar_expect_tx(bar + b, (uint32_t)total);
+        __syncwarp();
+        if (bytes > 0)
+            bulk_copy_g2s(buf + (b * kTabS + lane) * SLOT + (start - kTabG * q0) * ESZ,
+                          reinterpret_cast<const unsigned char *>(tab) + (nrb + start) * ESZ, (uint32_t)bytes,
+                          bar + b);
+    }
+    __device__ __forceinline__ bool wait(int b)
+    {
+        const bool ok = mbar_wait_warp(bar + b, (ph >> b) & 1u);
+        ph ^= 1u << b;
+        return ok;
+    }
+    __device__ __forceinline__ const unsigned char *slot(int b, int i) const { return buf + (b * kTabS + i) * SLOT; }
 };
 
+// A lane's four rings from a staged slot.  Spin s: the group's 32 bytes are
+// read as two 16-byte halves; lanes with bit 2 set read the second half
+// first, so that the eight lanes of each quarter-warp access hit 32
+// distinct banks.
 template <bool SPIN>
-__device__ __forceinline__ void tab_load(const float *__restrict__ tab, int64_t e, bool on, float (&vp)[kTabG],
-                                         float (&vm)[kTabG])
+__device__ __forceinline__ void tab_read(const unsigned char *slot, int lane, float (&vp)[kTabG], float (&vm)[kTabG])
 {
     if (!SPIN) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (on) v = __ldg(reinterpret_cast<const float4 *>(tab + e));
+        const float4 v = reinterpret_cast<const float4 *>(slot)[lane];
         vp[0] = v.x; vp[1] = v.y; vp[2] = v.z; vp[3] = v.w;
         vm[0] = vm[1] = vm[2] = vm[3] = 0.f;
     } else {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (on) {
-            a = __ldg(reinterpret_cast<const float4 *>(tab) + (e >> 1));
-            b = __ldg(reinterpret_cast<const float4 *>(tab) + (e >> 1) + 1);
-        }
+        const int h = (lane >> 2) & 1;
+        const float4 x = reinterpret_cast<const float4 *>(slot)[2 * lane + h];
+        const float4 y = reinterpret_cast<const float4 *>(slot)[2 * lane + 1 - h];
+        const float4 a = h ? y : x, b = h ? x : y;
         vp[0] = a.x; vm[0] = a.y; vp[1] = a.z; vm[1] = a.w;
         vp[2] = b.x; vm[2] = b.y; vp[3] = b.z; vm[3] = b.w;
     }
 }
 
+// shared memory per warp of the table kernels: staging, two barriers, and
+// (adjoint, spin s) the rows of the block reduction
+template <bool SPIN, bool ADJ_FLUSH> __host__ __device__ constexpr int tab_smem_per_warp()
+{
+    return TabStage<SPIN ? 8 : 4>::BYTES + 16 + (ADJ_FLUSH ? (int)adj_smem_per_warp<true>() : 0);
+}
+
+// Table synthesis: one thread per group of four rings, one order m per grid
+// row; the warp's lanes step through the degrees together from the warp's
+// smallest lstart (units start on a degree of even parity rel), reading the
+// staged values; a lane before its own lstart adds nothing.
 template <bool SPIN, bool GRAD>
 __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, const float *__restrict__ tab,
-                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ lstart,
-                                                 float2 *__restrict__ ring, int lmax, int mmax, int spin, int ntheta,
-                                                 int nnorth, int ng, int64_t nalm)
+                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ jlo,
+                                                 const int *__restrict__ lstart, float2 *__restrict__ ring, int lmax,
+                                                 int mmax, int spin, int ntheta, int nnorth, int nnp, int ng,
+                                                 int64_t nalm, unsigned *__restrict__ status)
 {
     using P = PolDF;
     using Sg = float;
-    constexpr int U = TabU<SPIN>::value;
+    constexpr int ESZ = SPIN ? 8 : 4;
     const int m = blockIdx.y;
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
     if (l0 > lmax) return;  // uniform per CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = q - lane;
     const int64_t base = alm_base(lmax, m);
     const int j0 = kTabG * q;
     const int lf = l0 + 1;
@@ -1463,30 +1526,44 @@ __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, 
     const int lw = __reduce_min_sync(0xffffffffu, ls);
     FwdAcc<P, kTabG, SPIN, 1, GRAD> acc;
     acc.init(coef, nalm, base);
-    float vp[kTabG], vm[kTabG];
-    int l = lw;
-    if (l <= lmax && ((l - lf) & 1)) {  // peel one odd degree
-        tab_load<SPIN>(tab, __ldg(rowbase + base + l) + j0, l >= ls, vp, vm);
-        acc.template add_vals<true>(vp, vm, l);
-        ++l;
-    }
-    for (; l + U - 1 <= lmax; l += U) {
-        int64_t rb[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) rb[u] = __ldg(rowbase + base + l + u);
-        float up[U][kTabG], um[U][kTabG];
-#pragma unroll
-        for (int u = 0; u < U; ++u) tab_load<SPIN>(tab, rb[u] + j0, l + u >= ls, up[u], um[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (u & 1) acc.template add_vals<true>(up[u], um[u], l + u);
-            else acc.template add_vals<false>(up[u], um[u], l + u);
+    extern __shared__ __align__(128) unsigned char tab_smem[];
+    if (lw <= lmax) {
+        TabStage<ESZ> stg;
+        stg.buf = tab_smem + warp * tab_smem_per_warp<SPIN, false>();
+        stg.bar = reinterpret_cast<uint64_t *>(stg.buf + TabStage<ESZ>::BYTES);
+        if (lane == 0) {
+            mbar_init(stg.bar, 1);
+            mbar_init(stg.bar + 1, 1);
         }
-    }
-    for (; l <= lmax; ++l) {
-        tab_load<SPIN>(tab, __ldg(rowbase + base + l) + j0, l >= ls, vp, vm);
-        if ((l - lf) & 1) acc.template add_vals<true>(vp, vm, l);
-        else acc.template add_vals<false>(vp, vm, l);
+        fence_async_shared();
+        __syncwarp();
+        constexpr int kTabS = TabStage<ESZ>::kTabS;
+        int lb = lw - ((lw - lf) & 1);  // degree lb + i has rel (-1)^i
+        stg.fetch(rowbase, jlo, base, lb, l0, lmax, lane);
+        stg.issue(0, tab, q0, nnp, lane);
+        stg.fetch(rowbase, jlo, base, lb + kTabS, l0, lmax, lane);
+        float vp[kTabG], vm[kTabG];
+        for (int b = 0; lb <= lmax; lb += kTabS, b ^= 1) {
+            const bool more = lb + kTabS <= lmax;
+            if (more) {
+                stg.issue(b ^ 1, tab, q0, nnp, lane);
+                stg.fetch(rowbase, jlo, base, lb + 2 * kTabS, l0, lmax, lane);
+            }
+            if (!stg.wait(b)) {
+                if (lane == 0) atomicOr(status, FLAG_TIMEOUT);
+                if (more) stg.wait(b ^ 1);
+                return;
+            }
+#pragma unroll
+            for (int i = 0; i < kTabS; ++i) {
+                const int l = lb + i;
+                if (l >= ls && l <= lmax) {
+                    tab_read<SPIN>(stg.slot(b, i), lane, vp, vm);
+                    if (i & 1) acc.template add_vals<true>(vp, vm, l);
+                    else acc.template add_vals<false>(vp, vm, l);
+                }
+            }
+        }
     }
     // write-out as k_leg_fwd (s0 = (-1)^(lf - m))
     const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);
@@ -1528,70 +1605,101 @@ __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, 
 }
 
 // Table adjoint: one thread per group of four rings; degrees in blocks of
-// kBlk starting at l0 (degree lb + i has rel = -1 for even i), each block
-// reduced over the warp like k_leg_adj (a block no lane of the warp has
-// reached is skipped).  Within a block the row bases, then the values of
-// U degrees at a time are loaded before they are summed.
+// kBlk starting at l0 + kBlk k (degree lb + i has rel = -1 for even i), from
+// the warp's first block on; each block arrives as two staged units of
+// kTabS degrees and is reduced over the warp like k_leg_adj.
 template <bool SPIN, bool GRAD>
 __global__ void __launch_bounds__(256) k_tab_adj(const float2 *__restrict__ ring, const float *__restrict__ tab,
-                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ lstart,
-                                                 const double *__restrict__ scale, float2 *__restrict__ alm, int lmax,
-                                                 int mmax, int spin, int ntheta, int nnorth, int ng, int64_t nalm,
-                                                 double wpos, unsigned long long *fx, const double *__restrict__ fxs)
+                                                 const int64_t *__restrict__ rowbase, const int *__restrict__ jlo,
+                                                 const int *__restrict__ lstart, const double *__restrict__ scale,
+                                                 float2 *__restrict__ alm, int lmax, int mmax, int spin, int ntheta,
+                                                 int nnorth, int nnp, int ng, int64_t nalm, double wpos,
+                                                 unsigned long long *fx, const double *__restrict__ fxs,
+                                                 unsigned *__restrict__ status)
 {
     using P = PolDF;
     using A = float;
+    constexpr int ESZ = SPIN ? 8 : 4;
     constexpr int NCOMP = (SPIN && !GRAD) ? 4 : 2;
     constexpr bool FSPIN = SPIN && !GRAD;
     constexpr int NV = kBlk * NCOMP;
-    constexpr int U = TabU<SPIN>::value;
+    constexpr int kTabS = TabStage<ESZ>::kTabS;
+    constexpr int UPB = kBlk / kTabS;  // staged units per block
+    static_assert(UPB * kTabS == kBlk, "a block is a whole number of staged units");
     const int m = blockIdx.y;
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
     if (l0 > lmax) return;  // uniform per CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = q - lane;
     const bool has = q < ng;
+    const int ls = has ? __ldg(lstart + (int64_t)m * ng + q) : lmax + 1;
+    const int lw = __reduce_min_sync(0xffffffffu, ls);
+    if (lw > lmax) return;  // uniform per warp: nothing to add
     const int64_t base = alm_base(lmax, m);
     const double *sc = scale + base;
-    const int j0 = kTabG * q;
     const float sgs = (s & 1) ? -1.f : 1.f;
     const int lf = l0 + 1;
     const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
     const double fxu = fx ? fxs[1 + m] : 0.0;
     float *out = reinterpret_cast<float *>(alm);
     AdjIn<P, kTabG, SPIN, GRAD> in;
-    in.init(ring, has ? j0 : nnorth, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
-    const int ls = has ? __ldg(lstart + (int64_t)m * ng + q) : lmax + 1;
-    constexpr bool kSmemFlush = FSPIN;
-    extern __shared__ __align__(16) float adj_smem[];
-    float *wbuf = adj_smem + (threadIdx.x >> 5) * (adj_smem_per_warp<FSPIN>() / sizeof(float));
+    in.init(ring, has ? kTabG * q : nnorth, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
+    extern __shared__ __align__(128) unsigned char tab_smem[];
+    TabStage<ESZ> stg;
+    stg.buf = tab_smem + warp * tab_smem_per_warp<SPIN, FSPIN>();
+    stg.bar = reinterpret_cast<uint64_t *>(stg.buf + TabStage<ESZ>::BYTES);
+    float *wbuf = reinterpret_cast<float *>(stg.buf + TabStage<ESZ>::BYTES + 16);
+    if (lane == 0) {
+        mbar_init(stg.bar, 1);
+        mbar_init(stg.bar + 1, 1);
+    }
+    fence_async_shared();
+    __syncwarp();
+    int lb = l0 + (lw - l0) / kBlk * kBlk;  // first block; units lb, lb + kTabS, ...
+    stg.fetch(rowbase, jlo, base, lb, l0, lmax, lane);
+    stg.issue(0, tab, q0, nnp, lane);
+    stg.fetch(rowbase, jlo, base, lb + kTabS, l0, lmax, lane);
     A part[NV];
-    for (int lb = l0; lb <= lmax; lb += kBlk) {
-        if (!__any_sync(0xffffffffu, ls <= lb + kBlk - 1)) continue;
+    float vp[kTabG], vm[kTabG];
+    for (int b = 0; lb <= lmax; lb += kTabS, b ^= 1) {
+        const bool more = lb + kTabS <= lmax;
+        if (more) {
+            stg.issue(b ^ 1, tab, q0, nnp, lane);
+            stg.fetch(rowbase, jlo, base, lb + 2 * kTabS, l0, lmax, lane);
+        }
+        if (!stg.wait(b)) {
+            if (lane == 0) atomicOr(status, FLAG_TIMEOUT);
+            if (more) stg.wait(b ^ 1);
+            return;
+        }
+        const int unit = ((lb - l0) / kTabS) % UPB;  // position of the unit in its block
+        if (unit == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) part[i] = 0.f;
-        int64_t rb[kBlk];
+            for (int i = 0; i < NV; ++i) part[i] = 0.f;
+        }
 #pragma unroll
-        for (int i = 0; i < kBlk; ++i) rb[i] = lb + i <= lmax ? __ldg(rowbase + base + lb + i) : 0;
+        for (int w = 0; w < UPB; ++w) {
+            if (w != unit) continue;
 #pragma unroll
-        for (int h = 0; h < kBlk; h += U) {
-            float up[U][kTabG], um[U][kTabG];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int l = lb + h + u;
-                tab_load<SPIN>(tab, rb[h + u] + j0, l >= ls && l <= lmax, up[u], um[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = h + u;
-                if (i & 1) in.template add_vals<false>(up[u], um[u], part + i * NCOMP);
-                else in.template add_vals<true>(up[u], um[u], part + i * NCOMP);
+            for (int u = 0; u < kTabS; ++u) {
+                const int l = lb + u;
+                if (l >= ls && l <= lmax) {
+                    tab_read<SPIN>(stg.slot(b, u), lane, vp, vm);
+                    // block index i = w kTabS + u: rel = -1 for even i
+                    if (u & 1) in.template add_vals<false>(vp, vm, part + (w * kTabS + u) * NCOMP);
+                    else in.template add_vals<true>(vp, vm, part + (w * kTabS + u) * NCOMP);
+                }
             }
         }
-        if constexpr (kSmemFlush)
-            flush_smem<FSPIN, NV>(part, wbuf, out, sc, wm, base, nalm, m, lb, lmax, sgs, fx, fxu);
-        else
-            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, lb, lmax, sgs, fx, fxu);
+        if (unit == UPB - 1 || !more) {
+            const int blk = lb - unit * kTabS;
+            if constexpr (FSPIN)
+                flush_smem<FSPIN, NV>(part, wbuf, out, sc, wm, base, nalm, m, blk, lmax, sgs, fx, fxu);
+            else
+                flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, blk, lmax, sgs, fx, fxu);
+        }
     }
 }
 
@@ -1679,10 +1787,13 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
                                                                p.nalm, p.mmax + 1, wpos, p.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (p.tab) {
-            const dim3 tg(p.tab_chunks, p.mmax + 1);
+            const dim3 tg(p.tab_fchunks, p.mmax + 1);
+            const size_t smem = (size_t)(p.tab_fthreads / 32) *
+                                (p.spin ? tab_smem_per_warp<true, false>() : tab_smem_per_warp<false, false>());
             const auto args = [&](auto kern) {
-                kern<<<tg, p.tab_threads, 0, st>>>(p.coef, p.tab_v, p.tab_rowbase, p.tab_lstart, (float2 *)ring,
-                                                   p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth, p.tab_ng, p.nalm);
+                kern<<<tg, p.tab_fthreads, smem, st>>>(p.coef, p.tab_v, p.tab_rowbase, p.tab_jlo, p.tab_lstart,
+                                                       (float2 *)ring, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
+                                                       p.tab_nnp, p.tab_ng, p.nalm, p.flags + 1);
             };
             if (!p.spin) args(k_tab_fwd<false, false>);
             else if (p.grad) args(k_tab_fwd<true, true>);
@@ -1747,16 +1858,17 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (f32 && p.tab) {
-        const dim3 tg(p.tab_chunks, p.mmax + 1);
-        const int warps = p.tab_threads / 32;
+        const dim3 tg(p.tab_achunks, p.mmax + 1);
+        const size_t warps = (size_t)(p.tab_athreads / 32);
         const auto args = [&](auto kern, size_t smem) {
-            kern<<<tg, p.tab_threads, smem, st>>>((const float2 *)ring, p.tab_v, p.tab_rowbase, p.tab_lstart,
-                                                  p.scale, (float2 *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
-                                                  p.tab_ng, p.nalm, wpos, (unsigned long long *)fx, p.fx_scale);
+            kern<<<tg, p.tab_athreads, smem, st>>>((const float2 *)ring, p.tab_v, p.tab_rowbase, p.tab_jlo,
+                                                   p.tab_lstart, p.scale, (float2 *)alm, p.lmax, p.mmax, p.spin,
+                                                   p.ntheta, p.nnorth, p.tab_nnp, p.tab_ng, p.nalm, wpos,
+                                                   (unsigned long long *)fx, p.fx_scale, p.flags + 1);
         };
-        if (!p.spin) args(k_tab_adj<false, false>, 0);
-        else if (p.grad) args(k_tab_adj<true, true>, 0);
-        else args(k_tab_adj<true, false>, (size_t)warps * adj_smem_per_warp<true>());
+        if (!p.spin) args(k_tab_adj<false, false>, warps * tab_smem_per_warp<false, false>());
+        else if (p.grad) args(k_tab_adj<true, true>, warps * tab_smem_per_warp<true, false>());
+        else args(k_tab_adj<true, false>, warps * tab_smem_per_warp<true, true>());
         e = cudaGetLastError();
     } else if (f32) {
         e = adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos, fx);
@@ -1774,13 +1886,41 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
 }
 
 // ---- Legendre tables (plan creation)
-void tab_shape(Plan &p)
+// Launch shapes of the table kernels: warps of 32 ring groups, at most wmax
+// warps per CTA (shared memory: 8 KB of staging per warp, plus the spin-s
+// adjoint's reduction rows), as few idle warps as possible.
+// Opts the kernels into the dynamic shared memory they need.
+cudaError_t tab_shape(Plan &p)
 {
     p.tab_nnp = (p.nnorth + kTabG - 1) / kTabG * kTabG;
     p.tab_ng = p.tab_nnp / kTabG;
-    p.tab_chunks = (p.tab_ng + 255) / 256;
-    const int per = (p.tab_ng + p.tab_chunks - 1) / p.tab_chunks;
-    p.tab_threads = (per + 31) / 32 * 32;
+    const int nw = (p.tab_ng + 31) / 32;
+    auto shape = [&](int wmax, int &chunks, int &threads) {
+        chunks = (nw + wmax - 1) / wmax;
+        threads = 32 * ((nw + chunks - 1) / chunks);
+    };
+    const int fw = 8, aw = p.spin ? 4 : 8;  // the attributes below allow the largest shape
+    shape(fw, p.tab_fchunks, p.tab_fthreads);
+    shape(aw, p.tab_achunks, p.tab_athreads);
+    cudaError_t e;
+    if (p.spin) {
+        if ((e = cudaFuncSetAttribute(k_tab_fwd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<true, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_fwd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<true, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_adj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      aw * tab_smem_per_warp<true, true>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_adj<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      aw * tab_smem_per_warp<true, false>())) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(k_tab_fwd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<false, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_adj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      aw * tab_smem_per_warp<false, false>())) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_tab_first(const Plan &p, int *first)

@@ -239,8 +239,8 @@ int lens_version(void) { return 100; }
 // a lens_status (the caller destroys the plan on failure).
 static int build_legendre_tables(Plan &p, Builder &B)
 {
-    tab_shape(p);
     cudaStream_t st = p.stream;
+    if (cudaError_t e0 = tab_shape(p); e0 != cudaSuccess) return cuda_fail(e0, "table kernel attributes");
     int *first = nullptr;
     int64_t *rowlen = nullptr;
     cudaError_t e;
@@ -454,6 +454,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     cudaError_t e;
     // ---- device buffers
     if ((e = B.alloc((void **)&p->flags, sizeof(unsigned) * 4, false)) != cudaSuccess) return bailc(e, "alloc flags");
+    if ((e = cudaMemset(p->flags, 0, sizeof(unsigned) * 4)) != cudaSuccess) return bailc(e, "clear flags");
     // FP32 spin plans interleave alpha and tau in rec_a (16 bytes per entry)
     const size_t ra_b = (prec == LENS_FP32 && spin) ? 16 : 8;
     if ((e = B.alloc(&p->rec_a, (size_t)p->nalm * ra_b, false)) != cudaSuccess) return bailc(e, "alloc rec_a");
@@ -809,6 +810,22 @@ static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, v
         if (r != LENS_OK) return r;
     }
     return LENS_OK;
+}
+
+int lens_plan_status(lens_plan pl, void *stream)
+{
+    if (!pl) return fail(LENS_ERR_INVALID, "bad plan");
+    Plan &p = *reinterpret_cast<Plan *>(pl);
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    unsigned f = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&f, p.flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if (f == 0) return LENS_OK;
+    if ((e = cudaMemsetAsync(p.flags + 1, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(e, "status reset");
+    return fail(LENS_ERR_TIMEOUT, "a device-side wait gave up: the results of earlier calls are incomplete");
 }
 
 int lens_plan_set_grouping(lens_plan pl, int on)

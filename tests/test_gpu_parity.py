@@ -453,3 +453,15 @@ def test_legendre_tables_edge_cases():
     with pytest.raises(LensError) as ex:
         LensPlan(16, th, ph, precision="fp64", epsilon=1e-10, legendre_tables=True, device=DEV)
     assert ex.value.status == 1
+
+
+def test_legendre_tables_status_clean():
+    """The table kernels' bounded waits never give up on a healthy device."""
+    th, ph, chi = W.random_points(5000, 3)
+    plan = LensPlan(500, th, ph, chi, spin=2, legendre_tables=True, device=DEV)
+    a = make_alm(500, 2, 1)
+    for _ in range(3):
+        m = plan.synthesis(gpu_alm(plan, a))
+        plan.adjoint(m)
+    plan.status()
+    plan.close()
