@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-tables", action="store_true",
                     help="FP32 plans run the Legendre recursion instead of reading plan-time tables")
+    ap.add_argument("--sigma", type=float, default=None,
+                    help="force the NUFFT oversampling factor of the FP32 plans (small profiling cases)")
     ap.add_argument("--no-recursion-compare", action="store_true",
                     help="skip the extra measurement of the FP32 step with recursion plans")
     ap.add_argument("--no-e2e", action="store_true")
@@ -244,8 +246,10 @@ def run_gpu(args):
     def make(prec, eps, tables=False):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, legendre_tables=tables, device=dev)
-        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, legendre_tables=tables, device=dev)
+        sg = args.sigma if prec == "fp32" else None
+        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg, device=dev)
+        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg,
+                      device=dev)
         torch.cuda.synchronize()
         make.plan_s = time.perf_counter() - t0
         ct = pT.complex_dtype

@@ -173,6 +173,9 @@ inline size_t plan_map_bytes(const Plan &p) { return (size_t)p.npts * (p.spin ? 
 // (lens_get_last_error / lens_last_error_message) and returns the status.
 int record_failure(int status, const char *msg);
 
+// shared-memory elements of a one-CTA FFT vector of n elements of esz bytes
+// (FP32 vectors: one padding element after every 16, see fft.cuh)
+inline constexpr size_t fft_smem_elems(size_t n, size_t esz) { return esz == 8 ? n + n / 16 + 1 : n; }
 size_t theta_smem_bytes(const Plan &p);
 size_t phi_smem_bytes(const Plan &p);
 

@@ -354,7 +354,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // the FFTs takes ~1e-6 at lmax ~ 4096.  sigma is then picked by a cost model.
     const size_t esz = prec == LENS_FP32 ? 8 : 16;
     // one CTA holds fft_one elements; a cluster of two or four CTAs 2x or 4x that
-    const size_t fft_one = kSmemLimit / esz, fft_max = 4 * fft_one;
+    // (FP32 single-CTA vectors carry one padding element per 16: fft_smem_elems)
+    size_t fft_one = kSmemLimit / esz;
+    while (fft_smem_elems(fft_one, esz) * esz > kSmemLimit) --fft_one;
+    const size_t fft_max = 4 * fft_one;
     const int force_cl = prm ? prm->fft_cluster : 0;
     if (prm && prm->legendre_tables != 0) {
         if (prm->legendre_tables != 1) return bail(LENS_ERR_INVALID, "legendre_tables must be 0 or 1");

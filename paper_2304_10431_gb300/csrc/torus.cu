@@ -35,6 +35,15 @@ __device__ __forceinline__ int pmod(int a, int n)
 }
 
 template <typename C, int CL> __device__ __forceinline__ Buf<C, CL> make_buf(C *local, int chunk);
+// theta transforms: FP32 single-CTA vectors use the padded layout
+template <typename C, int CL> struct ThetaBuf {
+    using type = Buf<C, CL>;
+    static __device__ __forceinline__ type make(C *l, int chunk) { return make_buf<C, CL>(l, chunk); }
+};
+template <> struct ThetaBuf<float2, 1> {
+    using type = PadBuf<float2>;
+    static __device__ __forceinline__ type make(float2 *l, int) { return PadBuf<float2>(l); }
+};
 template <> __device__ __forceinline__ Buf<float2, 1> make_buf<float2, 1>(float2 *l, int) { return Buf<float2, 1>(l); }
 template <> __device__ __forceinline__ Buf<double2, 1> make_buf<double2, 1>(double2 *l, int)
 {
@@ -74,7 +83,7 @@ __global__ void __launch_bounds__(512) k_theta_fwd(const cplx<T> *__restrict__ r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Team<CL> tm;
     if (CL > 1) tm.sync();
-    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
+    const auto buf = ThetaBuf<C, CL>::make(reinterpret_cast<C *>(smem_raw), chunk);
     const int c = tm.vec();
     const int mc = spin == 0 ? c : c - mmax;
     const T par = ((mc + spin) & 1) ? T(-1) : T(1);
@@ -123,7 +132,7 @@ __global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Team<CL> tm;
     if (CL > 1) tm.sync();
-    const Buf<C, CL> buf = make_buf<C, CL>(reinterpret_cast<C *>(smem_raw), chunk);
+    const auto buf = ThetaBuf<C, CL>::make(reinterpret_cast<C *>(smem_raw), chunk);
     const int c = tm.vec();
     const int mc = spin == 0 ? c : c - mmax;
     const T par = ((mc + spin) & 1) ? T(-1) : T(1);
@@ -276,8 +285,9 @@ __global__ void __launch_bounds__(512) k_phi_adj(const void *__restrict__ grid, 
 // Per-CTA shared memory: the vector's elements divided over the team.
 size_t theta_smem_bytes(const Plan &p)
 {
-    const size_t n = (size_t)(p.N1 > p.M ? p.N1 : p.M);
-    return (n + p.cl_theta - 1) / p.cl_theta * (p.prec == LENS_FP32 ? 8 : 16);
+    const size_t n = (size_t)(p.N1 > p.M ? p.N1 : p.M), esz = p.prec == LENS_FP32 ? 8 : 16;
+    if (p.cl_theta == 1) return fft_smem_elems(n, esz) * esz;
+    return (n + p.cl_theta - 1) / p.cl_theta * esz;
 }
 size_t phi_smem_bytes(const Plan &p)
 {
