@@ -48,7 +48,7 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kPi = 3.141592653589793238462643383280;
-constexpr int kSpreadThreads = 128;
+constexpr int kSpreadThreads = 64;
 
 // Grid coordinate u = t c with c = N / (2 pi) held as a double-double (c.x +
 // c.y): the product's rounding error, ~1e-16 of u (up to N/2 ~ 10^4 cells),
