@@ -1501,13 +1501,15 @@ template <bool SPIN, bool ADJ_FLUSH> __host__ __device__ constexpr int tab_smem_
 // Table synthesis: one thread per group of four rings, one order m per grid
 // row; the warp's lanes step through the degrees together from the warp's
 // smallest lstart (units start on a degree of even parity rel), reading the
-// staged values; a lane before its own lstart adds nothing.
-template <bool SPIN, bool GRAD>
+// staged values; a lane before its own lstart adds nothing.  NM maps share
+// each table read (prepared coefficients of map b at coef + b ncomp nalm).
+template <bool SPIN, bool GRAD, int NM = 1>
 __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, const float *__restrict__ tab,
                                                  const int64_t *__restrict__ rowbase, const int *__restrict__ jlo,
                                                  const int *__restrict__ lstart, float2 *__restrict__ ring, int lmax,
                                                  int mmax, int spin, int ntheta, int nnorth, int nnp, int ng,
-                                                 int64_t nalm, unsigned *__restrict__ status)
+                                                 int64_t nalm, unsigned *__restrict__ status,
+                                                 int64_t ring_stride = 0)
 {
     using P = PolDF;
     using Sg = float;
@@ -1524,7 +1526,7 @@ __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, 
     const int lf = l0 + 1;
     const int ls = q < ng ? __ldg(lstart + (int64_t)m * ng + q) : lmax + 1;
     const int lw = __reduce_min_sync(0xffffffffu, ls);
-    FwdAcc<P, kTabG, SPIN, 1, GRAD> acc;
+    FwdAcc<P, kTabG, SPIN, NM, GRAD> acc;
     acc.init(coef, nalm, base);
     extern __shared__ __align__(128) unsigned char tab_smem[];
     if (lw <= lmax) {
@@ -1565,40 +1567,43 @@ __global__ void __launch_bounds__(256) k_tab_fwd(const void *__restrict__ coef, 
             }
         }
     }
-    // write-out as k_leg_fwd (s0 = (-1)^(lf - m))
+    // write-out as k_leg_fwd (s0 = (-1)^(lf - m)); map b at ring + b ring_stride
     const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);
 #pragma unroll
+    for (int b = 0; b < NM; ++b)
+#pragma unroll
     for (int k = 0; k < kTabG; ++k) {
+        float2 *const rb = ring + b * ring_stride;
         const int jn = j0 + k;
         if (jn >= nnorth) continue;
         const int js = ntheta - 1 - jn;
         if (!SPIN) {
-            float2 *col = ring + (int64_t)m * ntheta;
-            col[jn] = P::cout(acc.r0[0][k] + acc.r1[0][k], acc.i0[0][k] + acc.i1[0][k]);
-            if (js != jn) col[js] = P::cout(s0 * (acc.r0[0][k] - acc.r1[0][k]), s0 * (acc.i0[0][k] - acc.i1[0][k]));
+            float2 *col = rb + (int64_t)m * ntheta;
+            col[jn] = P::cout(acc.r0[b][k] + acc.r1[b][k], acc.i0[b][k] + acc.i1[b][k]);
+            if (js != jn) col[js] = P::cout(s0 * (acc.r0[b][k] - acc.r1[b][k]), s0 * (acc.i0[b][k] - acc.i1[b][k]));
         } else if (GRAD) {
             const Sg ms0 = -s0, sgs = (s & 1) ? Sg(-1) : Sg(1);
-            const float pr = acc.r0[0][k] + acc.r1[0][k], pi = acc.i0[0][k] + acc.i1[0][k];
-            const float qr = acc.r2[0][k] - acc.r3[0][k], qi = acc.i2[0][k] - acc.i3[0][k];
-            float2 *colp = ring + (int64_t)(mmax + m) * ntheta;
+            const float pr = acc.r0[b][k] + acc.r1[b][k], pi = acc.i0[b][k] + acc.i1[b][k];
+            const float qr = acc.r2[b][k] - acc.r3[b][k], qi = acc.i2[b][k] - acc.i3[b][k];
+            float2 *colp = rb + (int64_t)(mmax + m) * ntheta;
             colp[jn] = P::cout(-pr, -pi);
             if (js != jn) colp[js] = P::cout(ms0 * qr, ms0 * qi);
             if (m > 0) {
-                const float ur = acc.r2[0][k] + acc.r3[0][k], ui = acc.i2[0][k] + acc.i3[0][k];
-                const float wr = acc.r0[0][k] - acc.r1[0][k], wi = acc.i0[0][k] - acc.i1[0][k];
-                float2 *colq = ring + (int64_t)(mmax - m) * ntheta;
+                const float ur = acc.r2[b][k] + acc.r3[b][k], ui = acc.i2[b][k] + acc.i3[b][k];
+                const float wr = acc.r0[b][k] - acc.r1[b][k], wi = acc.i0[b][k] - acc.i1[b][k];
+                float2 *colq = rb + (int64_t)(mmax - m) * ntheta;
                 colq[jn] = P::cout(-sgs * ur, sgs * ui);
                 if (js != jn) colq[js] = P::cout(sgs * ms0 * wr, -(sgs * ms0) * wi);
             }
         } else {
             const Sg ms0 = -s0;
-            float2 *colp = ring + (int64_t)(mmax + m) * ntheta;
-            colp[jn] = P::cout(-acc.r0[0][k], -acc.i0[0][k]);
-            if (js != jn) colp[js] = P::cout(ms0 * acc.r1[0][k], ms0 * acc.i1[0][k]);
+            float2 *colp = rb + (int64_t)(mmax + m) * ntheta;
+            colp[jn] = P::cout(-acc.r0[b][k], -acc.i0[b][k]);
+            if (js != jn) colp[js] = P::cout(ms0 * acc.r1[b][k], ms0 * acc.i1[b][k]);
             if (m > 0) {
-                float2 *colq = ring + (int64_t)(mmax - m) * ntheta;
-                colq[jn] = P::cout(-acc.r2[0][k], -acc.i2[0][k]);
-                if (js != jn) colq[js] = P::cout(ms0 * acc.r3[0][k], ms0 * acc.i3[0][k]);
+                float2 *colq = rb + (int64_t)(mmax - m) * ntheta;
+                colq[jn] = P::cout(-acc.r2[b][k], -acc.i2[b][k]);
+                if (js != jn) colq[js] = P::cout(ms0 * acc.r3[b][k], ms0 * acc.i3[b][k]);
             }
         }
     }
@@ -1793,7 +1798,7 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
             const auto args = [&](auto kern) {
                 kern<<<tg, p.tab_fthreads, smem, st>>>(p.coef, p.tab_v, p.tab_rowbase, p.tab_jlo, p.tab_lstart,
                                                        (float2 *)ring, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
-                                                       p.tab_nnp, p.tab_ng, p.nalm, p.flags + 1);
+                                                       p.tab_nnp, p.tab_ng, p.nalm, p.flags + 1, (int64_t)0);
             };
             if (!p.spin) args(k_tab_fwd<false, false>);
             else if (p.grad) args(k_tab_fwd<true, true>);
@@ -1823,6 +1828,26 @@ cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring
                                                                p.scale, (float2 *)coef + (size_t)b * ncomp * p.nalm,
                                                                p.lmax, p.spin, p.nalm, p.mmax + 1, wpos, false);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (p.tab) {  // one table read serves the nm maps
+        const dim3 tg(p.tab_fchunks, p.mmax + 1);
+        const size_t smem = (size_t)(p.tab_fthreads / 32) *
+                            (p.spin ? tab_smem_per_warp<true, false>() : tab_smem_per_warp<false, false>());
+        const int64_t rs = (int64_t)p.ncol * p.ntheta;
+        const auto args = [&](auto kern) {
+            kern<<<tg, p.tab_fthreads, smem, st>>>(coef, p.tab_v, p.tab_rowbase, p.tab_jlo, p.tab_lstart,
+                                                   (float2 *)ring, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
+                                                   p.tab_nnp, p.tab_ng, p.nalm, p.flags + 1, rs);
+        };
+        if (p.spin) {
+            if (nm != 2) return cudaErrorInvalidValue;
+            args(k_tab_fwd<true, false, 2>);
+        } else if (nm == 2) {
+            args(k_tab_fwd<false, false, 2>);
+        } else {
+            args(k_tab_fwd<false, false, 4>);
+        }
+        return cudaGetLastError();
     }
     const Plan::LegShape &sh = p.leg_fb[nm == 2 ? 0 : 1];
     if (p.spin) {
@@ -1906,6 +1931,8 @@ cudaError_t tab_shape(Plan &p)
     if (p.spin) {
         if ((e = cudaFuncSetAttribute(k_tab_fwd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       fw * tab_smem_per_warp<true, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_fwd<true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<true, false>())) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_tab_fwd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       fw * tab_smem_per_warp<true, false>())) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_tab_adj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1915,6 +1942,10 @@ cudaError_t tab_shape(Plan &p)
             return e;
     } else {
         if ((e = cudaFuncSetAttribute(k_tab_fwd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<false, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_fwd<false, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      fw * tab_smem_per_warp<false, false>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_tab_fwd<false, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       fw * tab_smem_per_warp<false, false>())) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_tab_adj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       aw * tab_smem_per_warp<false, false>())) != cudaSuccess)

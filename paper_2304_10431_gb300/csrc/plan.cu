@@ -799,8 +799,9 @@ static int device_call(lens_plan pl, const void *in_d, void *out_d, int nmaps, v
     const size_t ib = fwd ? alm_bytes(p) : map_bytes(p), ob = fwd ? map_bytes(p) : alm_bytes(p);
     int i = 0;
     // FP32 synthesis of several maps: groups of 4, then 2, share the recursion
-    if (fwd && p.prec == LENS_FP32 && !p.grad && !p.tab && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
-        for (int nm = 4; nm >= 2; nm /= 2)
+    // (plans with Legendre tables: one table read serves the group; spin s groups of 2)
+    if (fwd && p.prec == LENS_FP32 && !p.grad && nmaps >= 2 && p.group_maps && group_workspace(p, st)) {
+        for (int nm = (p.tab && p.spin) ? 2 : 4; nm >= 2; nm /= 2)
             for (; nmaps - i >= nm; i += nm) {
                 const int r = forward_group(p, (const char *)in_d + i * ib, (char *)out_d + i * ob, nm, st, wpos);
                 if (r != LENS_OK) return r;

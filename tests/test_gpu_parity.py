@@ -298,15 +298,17 @@ def test_cluster_fft_matches_single_cta(spin, prec, eps, cl):
     assert rel(out[cl][0][:, s], ref) <= eps
 
 
+@pytest.mark.parametrize("tables", [False, True])
 @pytest.mark.parametrize("spin", [0, 1, 2])
-def test_grouped_synthesis_matches_per_map(spin):
+def test_grouped_synthesis_matches_per_map(spin, tables):
     """FP32 plans synthesise several maps per call with one Legendre recursion
     shared by four (then two) maps; every map equals its own call (the same
     arithmetic per map: bit-identical where the rings-per-thread setting is the
     same, else up to which negligible degrees a warp skips) and the oracle."""
     L, n = 200, 30000
     th, ph, chi = W.random_points(n, 77 + spin)
-    plan = LensPlan(L, th, ph, chi if spin else None, spin=spin, epsilon=1e-5, precision="fp32", device=DEV)
+    plan = LensPlan(L, th, ph, chi if spin else None, spin=spin, epsilon=1e-5, precision="fp32",
+                    legendre_tables=tables, device=DEV)
     a = np.stack([make_alm(L, spin, 500 + 3 * i) for i in range(7)])
     single = np.stack([plan.synthesis(gpu_alm(plan, a[i])).cpu().numpy() for i in range(7)])
     for nm in (2, 3, 4, 5, 7):
