@@ -372,6 +372,18 @@ int lens_synthesis_host(lens_plan p, const void *alm_h, void *map_h, int nmaps, 
 int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream);
 
 /*
+ * As lens_synthesis_host / lens_adjoint_host, but only enqueued on `stream`:
+ * they return once the copies and kernels are queued.  The host buffers must
+ * stay valid and unmodified until the stream has been synchronised, and should
+ * be page-locked (cudaHostAlloc / pinned): copies from pageable memory are
+ * staged by the driver and do not overlap other work.  Calls on one plan share
+ * its staging buffers, so they must use one stream; plans on different streams
+ * overlap their copies with each other's kernels.
+ */
+int lens_synthesis_host_async(lens_plan p, const void *alm_h, void *map_h, int nmaps, void *stream);
+int lens_adjoint_host_async(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream);
+
+/*
  * Forward lensing that allocates nothing (no counterpart in the paper).
  * Callers whose device memory belongs to someone else once they are running
  * (a host framework that owns every device allocation, a service with a

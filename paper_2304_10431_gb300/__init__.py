@@ -188,25 +188,28 @@ class LensPlan:
                                                       _stream_handle(stream)))
         return out
 
-    def synthesis_host(self, alm_h, out_h=None, stream=None):
-        """Forward on host (CPU) tensors: copies in, transform, copies out (synchronous)."""
+    def synthesis_host(self, alm_h, out_h=None, stream=None, sync: bool = True):
+        """Forward on host (CPU) tensors: copies in, transform, copies out.  sync=False only
+        enqueues on `stream` (lens_synthesis_host_async): pinned tensors, kept alive and
+        untouched until the stream is synchronised."""
         alm_h = torch.as_tensor(alm_h).to(self.complex_dtype).contiguous()
         nmaps = 1 if alm_h.dim() <= 2 else int(np.prod(alm_h.shape[:-2]))
         lead = alm_h.shape[:-2] if alm_h.dim() > 2 else ()
         if out_h is None:
-            out_h = torch.empty(*lead, self.ncomp, self.npoints, dtype=self.real_dtype)
-        _native.check(_native.load().lens_synthesis_host(self._h, alm_h.data_ptr(), out_h.data_ptr(), nmaps,
-                                                         _stream_handle(stream)))
+            out_h = torch.empty(*lead, self.ncomp, self.npoints, dtype=self.real_dtype, pin_memory=not sync)
+        fn = _native.load().lens_synthesis_host if sync else _native.load().lens_synthesis_host_async
+        _native.check(fn(self._h, alm_h.data_ptr(), out_h.data_ptr(), nmaps, _stream_handle(stream)))
         return out_h
 
-    def adjoint_host(self, m_h, out_h=None, stream=None):
+    def adjoint_host(self, m_h, out_h=None, stream=None, sync: bool = True):
+        """Adjoint on host tensors (see synthesis_host for sync=False)."""
         m_h = torch.as_tensor(m_h).to(self.real_dtype).contiguous()
         nmaps = 1 if m_h.dim() <= 2 else int(np.prod(m_h.shape[:-2]))
         lead = m_h.shape[:-2] if m_h.dim() > 2 else ()
         if out_h is None:
-            out_h = torch.empty(*lead, self.alm_ncomp, self.nalm, dtype=self.complex_dtype)
-        _native.check(_native.load().lens_adjoint_host(self._h, m_h.data_ptr(), out_h.data_ptr(), nmaps,
-                                                       _stream_handle(stream)))
+            out_h = torch.empty(*lead, self.alm_ncomp, self.nalm, dtype=self.complex_dtype, pin_memory=not sync)
+        fn = _native.load().lens_adjoint_host if sync else _native.load().lens_adjoint_host_async
+        _native.check(fn(self._h, m_h.data_ptr(), out_h.data_ptr(), nmaps, _stream_handle(stream)))
         return out_h
 
     def ring_synthesis(self, alm: torch.Tensor, stream=None) -> torch.Tensor:

@@ -40,6 +40,8 @@ EXPORTS = {
     "lens_magnification": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "lens_synthesis_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_synthesis_host_async": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "lens_adjoint_host_async": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_synthesis": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_adjoint": (_i32, [_vp, _vp, _vp, _vp]),

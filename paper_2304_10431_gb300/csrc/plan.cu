@@ -862,7 +862,8 @@ int lens_adjoint_vjp(lens_plan pl, const void *grad_alm_d, void *grad_map_d, int
     return device_call(pl, grad_alm_d, grad_map_d, nmaps, stream, true, 0.5);
 }
 
-static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, void *stream, bool fwd)
+static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, void *stream, bool fwd,
+                     bool sync = true)
 {
     if (!pl || nmaps < 0) return fail(LENS_ERR_INVALID, "bad plan or nmaps");
     Plan &p = *reinterpret_cast<Plan *>(pl);
@@ -898,6 +899,7 @@ static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, voi
             break;
         }
     }
+    if (!sync) return rc;
     e = cudaStreamSynchronize(st);
     if (rc == LENS_OK && e != cudaSuccess) rc = cuda_fail(e, "stream sync");
     return rc;
@@ -911,6 +913,16 @@ int lens_synthesis_host(lens_plan p, const void *alm_h, void *map_h, int nmaps, 
 int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream)
 {
     return host_call(p, map_h, alm_h, nmaps, stream, false);
+}
+
+int lens_synthesis_host_async(lens_plan p, const void *alm_h, void *map_h, int nmaps, void *stream)
+{
+    return host_call(p, alm_h, map_h, nmaps, stream, true, false);
+}
+
+int lens_adjoint_host_async(lens_plan p, const void *map_h, void *alm_h, int nmaps, void *stream)
+{
+    return host_call(p, map_h, alm_h, nmaps, stream, false, false);
 }
 
 int lens_ring_synthesis(lens_plan pl, const void *alm_d, void *ring_d, void *stream)

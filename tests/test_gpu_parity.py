@@ -467,3 +467,26 @@ def test_legendre_tables_status_clean():
         plan.adjoint(m)
     plan.status()
     plan.close()
+
+
+def test_async_host_entry_points_on_two_streams():
+    """lens_*_host_async: enqueued on a stream, results equal to the synchronous host
+    calls once the stream is synchronised; two plans on two streams overlap."""
+    L, n = 64, 20000
+    th, ph, chi = W.random_points(n, 8)
+    p0 = LensPlan(L, th, ph, spin=0, epsilon=1e-5, precision="fp32", device=DEV)
+    p2 = LensPlan(L, th, ph, chi, spin=2, epsilon=1e-5, precision="fp32", device=DEV)
+    a0 = torch.as_tensor(make_alm(L, 0, 3), dtype=torch.complex64).pin_memory()
+    a2 = torch.as_tensor(make_alm(L, 2, 4), dtype=torch.complex64).pin_memory()
+    y2 = torch.as_tensor(np.random.default_rng(1).standard_normal((2, n)), dtype=torch.float32).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    m0 = p0.synthesis_host(a0, stream=s1, sync=False)
+    b2 = p2.adjoint_host(y2, stream=s2, sync=False)
+    m2 = p2.synthesis_host(a2, stream=s2, sync=False)
+    s1.synchronize()
+    s2.synchronize()
+    assert np.array_equal(m0.numpy(), p0.synthesis_host(a0).numpy())
+    assert np.array_equal(m2.numpy(), p2.synthesis_host(a2).numpy())
+    assert rel(b2.numpy(), p2.adjoint_host(y2).numpy()) <= 1e-6
+    p0.close()
+    p2.close()
