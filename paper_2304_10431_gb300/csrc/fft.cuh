@@ -7,7 +7,9 @@
 // twiddles W_{L_k}^{j q}; the output comes out in natural order.  Within a
 // stage the butterflies touch disjoint positions, so one barrier per stage
 // suffices.  Radices 2, 3, 4, 5, 7, 8; odd radices use the symmetric-pair
-// form y_k = x_0 + sum_q (x_q + x_{p-q}) cos(2 pi qk/p) -+ i (x_q - x_{p-q}) sin(2 pi qk/p).
+// form y_k = x_0 + sum_q (x_q + x_{p-q}) cos(2 pi qk/p) -+ i (x_q - x_{p-q}) sin(2 pi qk/p);
+// FP32 transforms also use the composite radices 6, 9, 14 and 21 (two small
+// DFTs in registers per stage, fewer shared-memory passes).
 //
 // DIR = -1: forward, sum x_n e^{-2 pi i nk/N};  DIR = +1: inverse (unnormalised).
 //
@@ -239,6 +241,80 @@ template <int DIR, typename T> struct SmallDft<7, DIR, T> {
     static __device__ __forceinline__ void run(cplx<T> *x) { OddDft<7, DIR, T>::run(x); }
 };
 
+// cos (sine = false) or sin of 2 pi t / R, t < R, for the composite radices
+template <int R> __host__ __device__ constexpr double root_cs(int t, bool sine)
+{
+    if (R == 6) {
+        constexpr double c[6] = {1.00000000000000000000, 0.50000000000000011102, -0.49999999999999977796, -1.00000000000000000000, -0.50000000000000044409, 0.50000000000000011102};
+        constexpr double s[6] = {0.00000000000000000000, 0.86602540378443859659, 0.86602540378443870761, 0.00000000000000012246, -0.86602540378443837454, -0.86602540378443859659};
+        return sine ? s[t] : c[t];
+    }
+    if (R == 9) {
+        constexpr double c[9] = {1.00000000000000000000, 0.76604444311897801345, 0.17364817766693041445, -0.49999999999999977796, -0.93969262078590831688, -0.93969262078590842791, -0.50000000000000044409, 0.17364817766692997036, 0.76604444311897779141};
+        constexpr double s[9] = {0.00000000000000000000, 0.64278760968653925190, 0.98480775301220802032, 0.86602540378443870761, 0.34202014332566887944, -0.34202014332566865740, -0.86602540378443837454, -0.98480775301220813134, -0.64278760968653958496};
+        return sine ? s[t] : c[t];
+    }
+    if (R == 14) {
+        constexpr double c[14] = {1.00000000000000000000, 0.90096886790241914600, 0.62348980185873359439, 0.22252093395631444839, -0.22252093395631433737, -0.62348980185873348336, -0.90096886790241903498, -1.00000000000000000000, -0.90096886790241914600, -0.62348980185873370541, -0.22252093395631458717, 0.22252093395631333816, 0.62348980185873337234, 0.90096886790241936804};
+        constexpr double s[14] = {0.00000000000000000000, 0.43388373911755812040, 0.78183148246802980363, 0.97492791218182361934, 0.97492791218182361934, 0.78183148246802991466, 0.43388373911755823142, 0.00000000000000012246, -0.43388373911755800938, -0.78183148246802969261, -0.97492791218182361934, -0.97492791218182384139, -0.78183148246802991466, -0.43388373911755750978};
+        return sine ? s[t] : c[t];
+    }
+    if (R == 21) {
+        constexpr double c[21] = {1.00000000000000000000, 0.95557280578614067768, 0.82623877431599490606, 0.62348980185873359439, 0.36534102436639498412, 0.07473009358642439259, -0.22252093395631433737, -0.49999999999999977796, -0.73305187182982634031, -0.90096886790241903498, -0.98883082622512852300, -0.98883082622512863402, -0.90096886790241914600, -0.73305187182982622929, -0.50000000000000044409, -0.22252093395631458717, 0.07473009358642436484, 0.36534102436639537270, 0.62348980185873337234, 0.82623877431599446197, 0.95557280578614056665};
+        constexpr double s[21] = {0.00000000000000000000, 0.29475517441090420823, 0.56332005806362206446, 0.78183148246802980363, 0.93087374864420424636, 0.99720379718118012935, 0.97492791218182361934, 0.86602540378443870761, 0.68017273777091935560, 0.43388373911755823142, 0.14904226617617472028, -0.14904226617617402639, -0.43388373911755800938, -0.68017273777091946663, -0.86602540378443837454, -0.97492791218182361934, -0.99720379718118012935, -0.93087374864420413534, -0.78183148246802991466, -0.56332005806362273059, -0.29475517441090470783};
+        return sine ? s[t] : c[t];
+    }
+    return 0.0;
+}
+
+// Composite radix R = P Q in registers (Cooley-Tukey with n = Q n1 + n2,
+// k = k1 + P k2): Q DFTs of length P, twiddles W_R^(n2 k1), P DFTs of length
+// Q.  One shared-memory pass instead of two.
+template <int P, int Q, int DIR, typename T> struct CompositeDft {
+    static __device__ __forceinline__ void run(cplx<T> *x)
+    {
+        constexpr int R = P * Q;
+        cplx<T> y[Q][P];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) {
+            cplx<T> t[P];
+#pragma unroll
+            for (int n1 = 0; n1 < P; ++n1) t[n1] = x[Q * n1 + n2];
+            SmallDft<P, DIR, T>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) {
+                if (n2 > 0 && k1 > 0) {
+                    const int e = (n2 * k1) % R;
+                    const T c = (T)root_cs<R>(e, false), s = (T)(DIR * root_cs<R>(e, true));
+                    t[k1] = mkc(t[k1].x * c - t[k1].y * s, t[k1].x * s + t[k1].y * c);
+                }
+                y[n2][k1] = t[k1];
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            cplx<T> u[Q];
+#pragma unroll
+            for (int n2 = 0; n2 < Q; ++n2) u[n2] = y[n2][k1];
+            SmallDft<Q, DIR, T>::run(u);
+#pragma unroll
+            for (int k2 = 0; k2 < Q; ++k2) x[k1 + P * k2] = u[k2];
+        }
+    }
+};
+template <int DIR, typename T> struct SmallDft<6, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { CompositeDft<2, 3, DIR, T>::run(x); }
+};
+template <int DIR, typename T> struct SmallDft<9, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { CompositeDft<3, 3, DIR, T>::run(x); }
+};
+template <int DIR, typename T> struct SmallDft<14, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { CompositeDft<2, 7, DIR, T>::run(x); }
+};
+template <int DIR, typename T> struct SmallDft<21, DIR, T> {
+    static __device__ __forceinline__ void run(cplx<T> *x) { CompositeDft<3, 7, DIR, T>::run(x); }
+};
+
 // x[q] *= w^q (DIR = -1) or conj(w)^q (DIR = +1) for q = 1 .. R-1, w = W_L^j
 // = tw[e] with e = j N / L.  FP32: w read once and its powers formed by
 // multiplication (q - 1 products, a few ulp; measured 5-8% faster torus
@@ -300,6 +376,18 @@ __device__ void fft_smem(const B &buf, const FftDesc &d, const Team<CL> &tm)
         case 4: fft_stage<4, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         case 5: fft_stage<5, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         case 7: fft_stage<7, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 6:
+            if constexpr (std::is_same<T, float>::value) fft_stage<6, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 9:
+            if constexpr (std::is_same<T, float>::value) fft_stage<9, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 14:
+            if constexpr (std::is_same<T, float>::value) fft_stage<14, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 21:
+            if constexpr (std::is_same<T, float>::value) fft_stage<21, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
         default: fft_stage<8, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         }
         Lp *= r;
@@ -350,6 +438,18 @@ __device__ void fft_smem_dif(const B &buf, const FftDesc &d, const Team<CL> &tm)
         case 4: fft_stage_dif<4, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         case 5: fft_stage_dif<5, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         case 7: fft_stage_dif<7, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
+        case 6:
+            if constexpr (std::is_same<T, float>::value) fft_stage_dif<6, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 9:
+            if constexpr (std::is_same<T, float>::value) fft_stage_dif<9, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 14:
+            if constexpr (std::is_same<T, float>::value) fft_stage_dif<14, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
+        case 21:
+            if constexpr (std::is_same<T, float>::value) fft_stage_dif<21, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr);
+            break;
         default: fft_stage_dif<8, DIR, T>(buf, d.n, Lp, tw, tm.tid, tm.nthr); break;
         }
         tm.sync();

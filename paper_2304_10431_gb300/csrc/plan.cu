@@ -119,14 +119,29 @@ int support_for(double eps, double sigma)
     return std::max(W, 4);
 }
 
-std::vector<int> factorize(int n)
+// Radices of an FFT stage sequence.  composite (FP32): pairs of small primes
+// are fused into radices 21, 14, 9 and 6 where possible (one shared-memory
+// pass each; fft.cuh), measured on the 7-smooth lengths of lmax 4096.
+std::vector<int> factorize(int n, bool composite)
 {
     std::vector<int> f;
     while (n % 8 == 0) { f.push_back(8); n /= 8; }
     if (n % 4 == 0) { f.push_back(4); n /= 4; }
-    if (n % 2 == 0) { f.push_back(2); n /= 2; }
-    for (int p : {3, 5, 7})
-        while (n % p == 0) { f.push_back(p); n /= p; }
+    int a2 = 0, a3 = 0, a5 = 0, a7 = 0;
+    if (n % 2 == 0) { a2 = 1; n /= 2; }
+    while (n % 3 == 0) { ++a3; n /= 3; }
+    while (n % 5 == 0) { ++a5; n /= 5; }
+    while (n % 7 == 0) { ++a7; n /= 7; }
+    if (composite) {
+        for (; a3 > 0 && a7 > 0; --a3, --a7) f.push_back(21);
+        for (; a2 > 0 && a7 > 0; --a2, --a7) f.push_back(14);
+        for (; a3 > 1; a3 -= 2) f.push_back(9);
+        for (; a2 > 0 && a3 > 0; --a2, --a3) f.push_back(6);
+    }
+    for (; a2 > 0; --a2) f.push_back(2);
+    for (; a3 > 0; --a3) f.push_back(3);
+    for (; a5 > 0; --a5) f.push_back(5);
+    for (; a7 > 0; --a7) f.push_back(7);
     return f;
 }
 
@@ -153,7 +168,7 @@ struct Builder {
     cudaError_t fft(FftDesc &d, int n)
     {
         d.n = n;
-        std::vector<int> f = factorize(n);
+        std::vector<int> f = factorize(n, p.prec == LENS_FP32);
         d.nst = (int)f.size();
         for (int i = 0; i < d.nst; ++i) d.radix[i] = f[i];
         std::vector<int> perm(n);
