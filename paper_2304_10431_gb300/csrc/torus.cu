@@ -99,15 +99,22 @@ __global__ void __launch_bounds__(512) k_theta_fwd(const cplx<T> *__restrict__ r
     fft_smem<-1, T, CL>(buf, fM, tm);  // natural order c_k * M
 
     // move k < 0 from M + k to N1 + k (top first: never overwrites an unread
-    // source, since N1 >= M), scaling every kept k by w1(k) w2(m)
+    // source, since N1 >= M), scaling every kept k by w1(k) w2(m); when the two
+    // ranges are disjoint (N1 - lmax >= M) in one pass and one barrier (the
+    // zeroing below covers the source range)
     const T wm = w2[c];
-    for (int k0 = -1; k0 >= -lmax; k0 -= nthr) {
-        const int k = k0 - tid;
-        C v = mkc(T(0), T(0));
-        if (k >= -lmax) v = cscale(buf[M + k], w1[k + lmax] * wm);
+    if (N1 - lmax >= M) {
+        for (int k = -1 - tid; k >= -lmax; k -= nthr) buf[N1 + k] = cscale(buf[M + k], w1[k + lmax] * wm);
         tm.sync();
-        if (k >= -lmax) buf[N1 + k] = v;
-        tm.sync();
+    } else {
+        for (int k0 = -1; k0 >= -lmax; k0 -= nthr) {
+            const int k = k0 - tid;
+            C v = mkc(T(0), T(0));
+            if (k >= -lmax) v = cscale(buf[M + k], w1[k + lmax] * wm);
+            tm.sync();
+            if (k >= -lmax) buf[N1 + k] = v;
+            tm.sync();
+        }
     }
     for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
     for (int i = lmax + 1 + tid; i < N1 - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
@@ -148,15 +155,20 @@ __global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X
     tm.sync();
     fft_smem<-1, T, CL>(buf, fN1, tm);  // natural order
 
-    // move k < 0 from N1 + k down to M + k (lowest first), scale by w1 w2
+    // move k < 0 from N1 + k down to M + k (lowest first), scale by w1 w2; in
+    // one pass without barriers when the ranges are disjoint (N1 - lmax >= M)
     const T wm = w2[c];
-    for (int k0 = -lmax; k0 <= -1; k0 += nthr) {
-        const int k = k0 + tid;
-        C v = mkc(T(0), T(0));
-        if (k <= -1) v = cscale(buf[N1 + k], w1[k + lmax] * wm);
-        tm.sync();
-        if (k <= -1) buf[M + k] = v;
-        tm.sync();
+    if (N1 - lmax >= M) {
+        for (int k = -lmax + tid; k <= -1; k += nthr) buf[M + k] = cscale(buf[N1 + k], w1[k + lmax] * wm);
+    } else {
+        for (int k0 = -lmax; k0 <= -1; k0 += nthr) {
+            const int k = k0 + tid;
+            C v = mkc(T(0), T(0));
+            if (k <= -1) v = cscale(buf[N1 + k], w1[k + lmax] * wm);
+            tm.sync();
+            if (k <= -1) buf[M + k] = v;
+            tm.sync();
+        }
     }
     for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
     for (int i = lmax + 1 + tid; i < M - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
