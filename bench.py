@@ -48,9 +48,9 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # source makes the entry stale and the bench reports traffic null.
 NCU_TRAFFIC = {
     ("legendre_adjoint/spin2/fp32", "d846cc9777e2"): 741691904,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
-    # table adjoint: lmax 2048 capture (12.754 GB for 11.977 GB of table + a_lm + ring bytes, ratio 1.065)
+    # table adjoint: lmax 2048 capture (12.756 GB for 11.977 GB of table + a_lm + ring bytes, ratio 1.065)
     # scaled to lmax 4096's 92.75 GB; profiles/legendre_tables_adjoint_spin2_fp32.md
-    ("legendre_adjoint_tables/spin2/fp32", "c9531c5947d6"): 98760346148,
+    ("legendre_adjoint_tables/spin2/fp32", "4df24e5ff172"): 98778851588,
 }
 
 

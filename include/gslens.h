@@ -193,6 +193,12 @@ int lens_synthesis(lens_plan p, const void *alm_d, void *map_d, int nmaps, void 
  * and the flag is cleared; else LENS_OK. */
 int lens_plan_status(lens_plan p, void *stream);
 
+/* Diagnostic: runs one warp that waits, with a ~10 ms limit, on an mbarrier
+ * that no copy completes (nothing else is in flight), through the same
+ * bounded wait as the Legendre-table kernels.  LENS_OK when the wait gave up
+ * and reported it as those kernels do; LENS_ERR_CUDA otherwise. */
+int lens_selftest_bounded_wait(void *stream);
+
 /* Turns the grouped multi-map synthesis above on (on != 0, the default) or off
  * for this plan.  Returns LENS_ERR_INVALID for a NULL plan. */
 int lens_plan_set_grouping(lens_plan p, int on);

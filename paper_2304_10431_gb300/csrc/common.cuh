@@ -135,13 +135,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // completion itself; gives up (uniformly, returning false) after about
 // kWaitCycles clock cycles.
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, long long limit = kWaitCycles)
 {
     const long long t0 = clock64();
     for (;;) {
         const bool done = mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, done)) return true;
-        const bool late = clock64() - t0 > kWaitCycles;
+        const bool late = clock64() - t0 > limit;
         if (__shfl_sync(0xffffffffu, late, 0)) return false;
     }
 }

@@ -131,6 +131,8 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
 cudaError_t launch_rec_tables(Plan &p);
 // Legendre tables: shape, first-entry degrees, rows, values (plan creation)
 cudaError_t tab_shape(Plan &p);
+// bounded-wait self-test kernel (one warp, an mbarrier that never completes)
+cudaError_t launch_wait_selftest(unsigned *status, long long limit, cudaStream_t st);
 cudaError_t launch_tab_first(const Plan &p, int *first);
 cudaError_t launch_tab_rows(const Plan &p, const int *first, int *lstart, int *jlo, int64_t *rowlen);
 cudaError_t launch_tab_fill(const Plan &p);

@@ -1708,6 +1708,20 @@ __global__ void __launch_bounds__(256) k_tab_adj(const float2 *__restrict__ ring
     }
 }
 
+// Self-test of the bounded wait: one warp arms an mbarrier for 16 bytes that
+// no copy delivers, waits with a short limit, and reports the timeout the
+// way the table kernels do (a status bit).  Nothing is in flight.
+__global__ void k_wait_selftest(unsigned *status, long long limit)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    fence_async_shared();
+    __syncwarp();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncwarp();
+    if (!mbar_wait_warp(&bar, 0, limit) && threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
+}
+
 // FP32 forward kernel sharing the recursion among nm = 2 or 4 maps
 const void *kernel_of_batch(bool spin, int rpt, int nm)
 {
@@ -1907,6 +1921,12 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
     const int nc = p.alm_ncomp();
     if (f32) k_fx_to_alm<float><<<g, 256, 0, st>>>((const unsigned long long *)fx, (float *)alm, p.lmax, p.nalm, nc, p.fx_scale);
     else k_fx_to_alm<double><<<g, 256, 0, st>>>((const unsigned long long *)fx, (double *)alm, p.lmax, p.nalm, nc, p.fx_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned *status, long long limit, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(status, limit);
     return cudaGetLastError();
 }
 

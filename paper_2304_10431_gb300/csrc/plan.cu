@@ -847,6 +847,22 @@ int lens_plan_status(lens_plan pl, void *stream)
     return fail(LENS_ERR_TIMEOUT, "a device-side wait gave up: the results of earlier calls are incomplete");
 }
 
+int lens_selftest_bounded_wait(void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned *d = nullptr, h = 0;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "selftest alloc");
+    if ((e = cudaMemsetAsync(d, 0, sizeof(unsigned), st)) == cudaSuccess &&
+        (e = launch_wait_selftest(d, 20000000LL, st)) == cudaSuccess &&  // ~10 ms
+        (e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    if (!(h & FLAG_TIMEOUT)) return fail(LENS_ERR_CUDA, "bounded wait did not report its timeout");
+    return LENS_OK;
+}
+
 int lens_plan_set_grouping(lens_plan pl, int on)
 {
     if (!pl) return fail(LENS_ERR_INVALID, "bad plan");

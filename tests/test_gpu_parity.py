@@ -490,3 +490,19 @@ def test_async_host_entry_points_on_two_streams():
     assert rel(b2.numpy(), p2.adjoint_host(y2).numpy()) <= 1e-6
     p0.close()
     p2.close()
+
+
+def test_bounded_wait_reports_timeout():
+    """The bulk-copy waits of the table kernels are bounded: a wait on an
+    mbarrier that no copy completes gives up (~10 ms limit here) and sets the
+    status bit instead of hanging; the device stays usable afterwards."""
+    import time
+    from paper_2304_10431_gb300 import _native
+    t0 = time.perf_counter()
+    assert _native.load().lens_selftest_bounded_wait(None) == 0
+    assert time.perf_counter() - t0 < 10.0
+    th, ph, _ = W.random_points(100, 2)
+    plan = LensPlan(16, th, ph, legendre_tables=True, device=DEV)
+    plan.synthesis(gpu_alm(plan, make_alm(16, 0, 1)))
+    plan.status()
+    plan.close()
