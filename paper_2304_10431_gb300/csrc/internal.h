@@ -12,7 +12,7 @@ namespace gsl {
 
 constexpr int kMaxFftStages = 24;
 constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
-constexpr int kTileR = 16, kTileC = 32;  // grid tile of the point sort (rows x columns)
+constexpr int kTileR = 32, kTileC = 32;  // grid tile of the point sort (rows x columns)
 
 // One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
 // and the digit-reversal table (input element i is stored at position perm[i]).
