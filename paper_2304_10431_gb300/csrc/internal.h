@@ -106,7 +106,7 @@ struct Plan {
     uint32_t *cell = nullptr;  // row * pitch + col of the first tap
     void *frac = nullptr;      // float2 / double2 (u - i0, v - j0)
     int32_t *perm = nullptr;   // sorted -> user index
-    uint32_t *tile_start = nullptr;  // [ntiles + 1] first sorted point of each 16 x 32 grid tile
+    uint32_t *tile_start = nullptr;  // [ntiles + 1] first sorted point of each 32 x 32 grid tile
     int ntile_c = 0, ntiles = 0;     // tiles per grid row band, total tiles
     void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
     double *wts = nullptr;     // FP64 plans: [npts][2W] kernel weights (theta taps, then phi taps)

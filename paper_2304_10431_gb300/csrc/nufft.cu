@@ -12,13 +12,13 @@
 // Points are prepared once per plan (Sect. 4: the geometry is reused): cell
 // offset into the row-padded grid, fractional offsets (u - i0, v - j0) from
 // FP64 coordinates, the spin phase e^{i s chi}, a permutation that sorts
-// points by 16 x 32 grid tiles (of the first tap) so that neighbouring
+// points by 32 x 32 grid tiles (of the first tap) so that neighbouring
 // threads share grid rows, and the first sorted point of every tile.
 // Interpolation runs one thread per sorted point and reads its W x W taps
 // through L1: sorted neighbours share rows, so the tile stays cached (staging
 // the tile and its halo in shared memory first measured 1.36x slower for
 // spin 0 at lmax 4096).  Spreading in FP32 runs one CTA per tile: its points
-// add their W x W taps into the tile and its halo, (16 + W - 1) x (32 + W - 1)
+// add their W x W taps into the tile and its halo, (32 + W - 1) x (32 + W - 1)
 // cells held in shared memory, and the CTA then adds the non-zero cells into
 // the grid with one global atomic each.  FP64
 // plans spread with one global atomic per tap instead: the L2 adds doubles
