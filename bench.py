@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="oracle time budget of the whole --impl reference run")
     ap.add_argument("--scan", default=None,
                     help="N_side x lmax scan (the paper's Fig. 4): comma list of NSIDE:LMAX pairs; prints one JSON "
                          "line per pair and precision instead of the benchmark line")
@@ -217,15 +219,39 @@ def stage_units(info, npts, spin, prec):
     }
 
 
+# ------------------------------------------------------------------ ranks
+# One process per GPU (torchrun); the transform does not shard, so ranks are
+# independent replicas: they meet only at the barriers around the timed region
+# and in the max over ranks of each time.
+def rank_env():
+    """(world, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world, device):
+    """Largest `value` over the ranks (the slowest replica's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units all ranks processed per second, from the slowest rank's time per step."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
     import torch.distributed as dist
     from paper_2304_10431_gb300 import LensPlan, _native, lib_path
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -286,12 +312,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         lib.lens_profile_enable(0)
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
 
     def per_transform(pT, pP, b, reps=3):
         out = {}
@@ -395,13 +416,9 @@ def run_gpu(args):
             hstep()
             barrier()
             times.append((time.perf_counter() - t0) * 1e3)
-        ems = float(np.median(times))
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(float(np.median(times)), world, dev)
         h2d = sum(x.numel() * x.element_size() for x in (hT, hP, hmT, hmP))
-        e2e = {"value": round(world * npts / (ems * 1e-3), 1), "unit": "lensed points/s",
+        e2e = {"value": round(whole_job_rate(world, npts, ems), 1), "unit": "lensed points/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3),
                "statistic": "median of %d steps" % len(times), "ms_mean": round(float(np.mean(times)), 3),
                "api": "lens_synthesis_host_async / lens_adjoint_host_async, T and E/B on two streams",
@@ -413,7 +430,7 @@ def run_gpu(args):
         rT, rP, rb = make("fp32", 1e-5, False)
         kr = max(1, min(args.steps, 3))
         msr = timed(rT, rP, rb, kr, 1, profile=False, nvtx_name="timed_fp32_recursion")
-        recursion = {"value": round(world * npts / (msr * 1e-3), 1), "unit": "lensed points/s",
+        recursion = {"value": round(whole_job_rate(world, npts, msr), 1), "unit": "lensed points/s",
                      "ms_per_step": round(msr, 3), "steps": kr,
                      "what": "same step, FP32 plans without Legendre tables (df32 recursion per call)"}
         del rb
@@ -462,7 +479,7 @@ def run_gpu(args):
                   "frac": round(top64["achieved"] / peak64, 4), "traffic": None,
                   "kernel": "%s (spin %d, fp64)" % (top64["stage"], top64["spin"]),
                   "avg_launch_ms": top64["avg_launch_ms"], "peak_source": note64}
-        fp64 = {"value": round(world * npts / (ms64 * 1e-3), 1), "unit": "lensed points/s", "epsilon": 1e-10,
+        fp64 = {"value": round(whole_job_rate(world, npts, ms64), 1), "unit": "lensed points/s", "epsilon": 1e-10,
                 "ms_per_step": round(ms64, 3), "steps": k64, "per_transform": per_transform(qT, qP, c, reps=1),
                 "plan": {k: qT.info()[k] for k in ("n1", "W", "sigma")} | {"W_spin2": qP.info()["W"]},
                 "roofline": roof64, "stages": rows64}
@@ -470,7 +487,7 @@ def run_gpu(args):
 
     result = {
         "metric": "lensed points/sec (synthesis and adjoint), lmax 4096, eps 1e-5 FP32 vs 1e-10 FP64",
-        "value": round(world * npts / (ms * 1e-3), 1),
+        "value": round(whole_job_rate(world, npts, ms), 1),
         "unit": "lensed points/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms, 3),
@@ -557,11 +574,11 @@ def cpu_baseline(lmax, nside, seconds, steps=1, warmup=0, return_times=False):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = rank_env()
+    if rank != 0:  # under torchrun only rank 0 times the oracle; the others exit without work
         return
     steps, warmup = args.steps, max(args.warmup, 0)
-    per_step = max(2.0, 150.0 / max(steps + warmup, 1))
+    per_step = max(min(2.0, args.ref_seconds), args.ref_seconds / max(steps + warmup, 1))
     cb, t = cpu_baseline(args.lmax, args.nside, per_step, steps=steps, warmup=warmup, return_times=True)
     out = {"metric": "lensed points/sec (synthesis and adjoint), lmax 4096, eps 1e-5 FP32 vs 1e-10 FP64",
            "value": cb["value"], "unit": "lensed points/s", "n_gpus": args.gpus, "steps": steps,
