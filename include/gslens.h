@@ -381,8 +381,8 @@ int lens_adjoint_host(lens_plan p, const void *map_h, void *alm_h, int nmaps, vo
  * As lens_synthesis_host / lens_adjoint_host, but only enqueued on `stream`:
  * they return once the copies and kernels are queued.  The host buffers must
  * stay valid and unmodified until the stream has been synchronised, and should
- * be page-locked (cudaHostAlloc / pinned): copies from pageable memory are
- * staged by the driver and do not overlap other work.  Calls on one plan share
+ * be page-locked (cudaHostAlloc / pinned): copies from pageable memory go
+ * through a CUDA-internal bounce buffer and do not overlap other work.  Calls on one plan share
  * its staging buffers, so they must use one stream; plans on different streams
  * overlap their copies with each other's kernels.
  */
