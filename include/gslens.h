@@ -418,6 +418,20 @@ int lens_synthesis_static(lens_plan p, const void *alm_d, void *map_d, void *str
  */
 int lens_ring_synthesis(lens_plan p, const void *alm_d, void *ring_d, void *stream);
 
+/*
+ * Doubling and theta transform alone (Sect. 3 "doubling"): the Fourier
+ * coefficients in theta of the doubled ring functions, before the kernel
+ * deconvolution and the oversampling.
+ *   coef_d  device complex [ncol][2 lmax + 1] (ncol as lens_ring_synthesis;
+ *           entry k + lmax is c_k, |k| <= lmax), such that the ring function
+ *           of lens_ring_synthesis is F(theta) = sum_k c_k e^{i k theta} at
+ *           every theta in [0, pi], not only on the rings (the doubled
+ *           function is band-limited to |k| <= lmax).
+ * LENS_ERR_UNSUPPORTED when the plan's theta vectors need a CTA cluster.
+ * Uses the plan's workspace; stream-ordered like lens_synthesis.
+ */
+int lens_torus_coefficients(lens_plan p, const void *alm_d, void *coef_d, void *stream);
+
 /* Transpose of lens_ring_synthesis: a_lm (spin 0) or G, C (spin s, with the
  * G/C decomposition of Sect. 2) from ring coefficients of the same layout. */
 int lens_ring_adjoint(lens_plan p, const void *ring_d, void *alm_d, void *stream);

@@ -222,6 +222,15 @@ class LensPlan:
                                                          _stream_handle(stream)))
         return out
 
+    def torus_coefficients(self, alm: torch.Tensor, stream=None) -> torch.Tensor:
+        """Doubling + theta transform alone: c[ncol, 2 lmax + 1] with F(theta) = sum_k c_k e^{ik theta}."""
+        alm, _ = self._alm_arg(alm)
+        ncol = self.mmax + 1 if self.spin == 0 else 2 * self.mmax + 1
+        out = torch.empty(ncol, 2 * self.lmax + 1, dtype=self.complex_dtype, device=self.device)
+        _native.check(_native.load().lens_torus_coefficients(self._h, alm.data_ptr(), out.data_ptr(),
+                                                             _stream_handle(stream)))
+        return out
+
     def ring_adjoint(self, ring: torch.Tensor, stream=None) -> torch.Tensor:
         ring = ring.contiguous()
         out = torch.empty(self.alm_ncomp, self.nalm, dtype=self.complex_dtype, device=self.device)

@@ -179,6 +179,8 @@ int record_failure(int status, const char *msg);
 // (FP32 vectors: one padding element after every 16, see fft.cuh)
 inline constexpr size_t fft_smem_elems(size_t n, size_t esz) { return esz == 8 ? n + n / 16 + 1 : n; }
 size_t theta_smem_bytes(const Plan &p);
+// torus coefficients c_k (|k| <= lmax) of every m column from ring coefficients
+cudaError_t launch_theta_coeffs(const Plan &p, const void *ring, void *out, cudaStream_t st);
 size_t phi_smem_bytes(const Plan &p);
 
 }  // namespace gsl

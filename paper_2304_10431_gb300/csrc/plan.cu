@@ -966,6 +966,18 @@ int lens_ring_synthesis(lens_plan pl, const void *alm_d, void *ring_d, void *str
     return e == cudaSuccess ? LENS_OK : cuda_fail(e, "legendre synthesis");
 }
 
+int lens_torus_coefficients(lens_plan pl, const void *alm_d, void *coef_d, void *stream)
+{
+    if (!pl || !alm_d || !coef_d) return fail(LENS_ERR_INVALID, "NULL argument");
+    const Plan &p = *reinterpret_cast<const Plan *>(pl);
+    if (p.cl_theta != 1) return fail(LENS_ERR_UNSUPPORTED, "torus coefficients of cluster-sized theta vectors");
+    DeviceGuard g(p.device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : p.stream;
+    cudaError_t e = launch_legendre_fwd(p, alm_d, p.ring, st);
+    if (e == cudaSuccess) e = launch_theta_coeffs(p, p.ring, coef_d, st);
+    return e == cudaSuccess ? LENS_OK : cuda_fail(e, "torus coefficients");
+}
+
 int lens_ring_adjoint(lens_plan pl, const void *ring_d, void *alm_d, void *stream)
 {
     if (!pl || !alm_d || !ring_d) return fail(LENS_ERR_INVALID, "NULL argument");

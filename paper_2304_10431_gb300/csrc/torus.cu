@@ -128,6 +128,32 @@ __global__ void __launch_bounds__(512) k_theta_fwd(const cplx<T> *__restrict__ r
     if (CL > 1) tm.sync();
 }
 
+// Torus coefficients of one m column (diagnostic entry point): the doubled
+// sequence and its length-M transform as in k_theta_fwd, written unscaled by
+// the kernel deconvolution: out[c][k + lmax] = c_k = (1/M) sum_j G_j
+// e^{-2 pi i jk/M}, |k| <= lmax, so that F_m(theta) = sum_k c_k e^{ik theta}
+// for every theta (one CTA per column).
+template <typename T>
+__global__ void __launch_bounds__(512) k_theta_coeffs(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ out,
+                                                       FftDesc fM, int ntheta, int lmax, int mmax, int spin)
+{
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Team<1> tm;
+    const auto buf = ThetaBuf<C, 1>::make(reinterpret_cast<C *>(smem_raw), 0);
+    const int c = tm.vec();
+    const int mc = spin == 0 ? c : c - mmax;
+    const T par = ((mc + spin) & 1) ? T(-1) : T(1);
+    const int M = fM.n;
+    const C *F = ring + (int64_t)c * ntheta;
+    for (int i = tm.tid; i < M; i += tm.nthr) buf[__ldg(fM.perm + i)] = i < ntheta ? F[i] : cscale(F[M - i], par);
+    tm.sync();
+    fft_smem<-1, T, 1>(buf, fM, tm);
+    const T inv = T(1) / T(M);
+    for (int k = -lmax + tm.tid; k <= lmax; k += tm.nthr)
+        out[(int64_t)c * (2 * lmax + 1) + (k + lmax)] = cscale(buf[k < 0 ? M + k : k], inv);
+}
+
 // ----------------------------------------------------------------- theta adj
 template <typename T, int CL>
 __global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
@@ -398,6 +424,24 @@ cudaError_t phi_adj_t(const Plan &p, const void *grid, void *X, cudaStream_t st)
 cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st)
 {
     return p.prec == LENS_FP32 ? theta_fwd_t<float>(p, ring, X, st) : theta_fwd_t<double>(p, ring, X, st);
+}
+
+cudaError_t launch_theta_coeffs(const Plan &p, const void *ring, void *out, cudaStream_t st)
+{
+    if (p.cl_theta != 1) return cudaErrorNotSupported;
+    const size_t sm = theta_smem_bytes(p);
+    if (p.prec == LENS_FP32) {
+        cudaError_t e = cudaFuncSetAttribute(k_theta_coeffs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_theta_coeffs<float><<<p.ncol, kThetaThreads, sm, st>>>((const float2 *)ring, (float2 *)out, p.fM, p.ntheta,
+                                                                p.lmax, p.mmax, p.spin);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_theta_coeffs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_theta_coeffs<double><<<p.ncol, kThetaThreads, sm, st>>>((const double2 *)ring, (double2 *)out, p.fM,
+                                                                 p.ntheta, p.lmax, p.mmax, p.spin);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st)

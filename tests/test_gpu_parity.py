@@ -506,3 +506,22 @@ def test_bounded_wait_reports_timeout():
     plan.synthesis(gpu_alm(plan, make_alm(16, 0, 1)))
     plan.status()
     plan.close()
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_doubling_and_theta_transform_are_exact(spin):
+    """Sect. 3: only the NUFFT is approximate.  The torus coefficients c_k of the
+    doubled ring functions (FP64 plan) reproduce the ring functions at arbitrary
+    theta in [0, pi] -- off the equiangular rings -- to rounding, against the
+    oracle's direct sums sum_l a_lm lambda_lm(theta)."""
+    L = 60
+    th, ph, chi = W.random_points(10, 4)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-12, precision="fp64", device=DEV)
+    a = make_alm(L, spin, 31)
+    c = plan.torus_coefficients(gpu_alm(plan, a)).cpu().numpy()
+    t = np.random.default_rng(9).uniform(0.0, math.pi, 41)
+    k = np.arange(-L, L + 1)
+    F = c @ np.exp(1j * np.outer(k, t))  # [ncol, ntheta']
+    ref = O.ring_coeffs(L, L, spin, t, a).T
+    assert rel(F, ref) <= 1e-13
+    plan.close()
