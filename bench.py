@@ -378,6 +378,14 @@ def run_gpu(args):
     stages = [{"stage": r[1], "spin": 2 if r[2] else 0, "ms_per_step": round(r[0], 4), "avg_launch_ms": round(r[3], 4),
                "bound": r[4], "achieved": round(r[5] / (r[3] * 1e-3) / (1e12 if r[4] == "alu" else 1e9), 2),
                "unit": r[6]} for r in stage_rows]
+    # whole-step roofline: each stage's algorithmic work at its bound's peak (HBM bytes at the
+    # measured copy bandwidth, ALU flops at the FP32 FMA peak), summed, against the step time
+    hbm_bs = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)) * 1e9
+    alu_fs = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6
+    t_roof = 1e3 * sum(r[5] / (alu_fs if r[4] == "alu" else hbm_bs) * r[7] / args.steps for r in stage_rows)
+    step_roofline = {"t_roof_ms": round(t_roof, 3), "t_measured_ms": round(ms, 3), "frac": round(t_roof / ms, 4),
+                     "rule": "sum over stages of work / peak of the stage's bound (HBM bytes at %.1f GB/s, %s; "
+                             "FP32 FMA flops at %.1f TFLOP/s)" % (hbm_bs / 1e9, peak_src, alu_fs / 1e12)}
     # our kernel launches per step: Legendre 1, theta 1, phi 1, interp 1 (fwd); spread 1, phi 1, theta 1,
     # Legendre 1 (adj) -> 8 per spin, 16 per step (memsets excluded)
     gpu_launches = 16 * args.steps
@@ -509,6 +517,7 @@ def run_gpu(args):
         "per_transform": {k: round(v, 1) for k, v in pt.items()},
         "roofline": roofline,
         "stages": stages,
+        "step_roofline": step_roofline,
         "gpu_launches": gpu_launches,
         "library": os.path.relpath(lib_path(), ROOT),
         "clocks": clocks,
