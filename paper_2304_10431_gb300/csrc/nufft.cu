@@ -316,7 +316,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
         T wa[W], wb[W];
         tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
         const int32_t src = perm[p];
-        G *b0 = buf + (lr * TC + lc) * NC;
+        // spin s: two planes (real parts, then imaginary parts), so that the lanes'
+        // atomics of one plane spread over all 32 banks
+        G *b0 = buf + (lr * TC + lc);
         if (!SPIN) {
             const T x = map[src];
 #pragma unroll
@@ -335,9 +337,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
                 const T xa = wa[a] * zx, ya = wa[a] * zy;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    G *q2 = b0 + 2 * (a * TC + b);
+                    G *q2 = b0 + (a * TC + b);
                     acc_add<T, FX>(q2, xa * wb[b], sc);
-                    acc_add<T, FX>(q2 + 1, ya * wb[b], sc);
+                    acc_add<T, FX>(q2 + TR * TC, ya * wb[b], sc);
                 }
             }
         }
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
             const G v = buf[i];
             if (v != G(0)) atomicAdd(g + o, v);
         } else {
-            const G vx = buf[2 * i], vy = buf[2 * i + 1];
+            const G vx = buf[i], vy = buf[TR * TC + i];
             if (vx != G(0)) atomicAdd(g + 2 * o, vx);
             if (vy != G(0)) atomicAdd(g + 2 * o + 1, vy);
         }
