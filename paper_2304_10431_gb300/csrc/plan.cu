@@ -904,6 +904,8 @@ static int host_call(lens_plan pl, const void *in_h, void *out_h, int nmaps, voi
     const size_t ab = alm_bytes(p), mb = map_bytes(p);
     cudaError_t e;
     if (!p.stage_in) {  // one alm-sized and one map-sized buffer, kept by the plan
+        if (p.nallocs + 2 > (int)(sizeof(p.allocs) / sizeof(p.allocs[0])))
+            return fail(LENS_ERR_NOMEM, "plan allocation table full");
         const size_t big = std::max(ab, mb) > 0 ? std::max(ab, mb) : 16;
         if ((e = cudaMalloc(&p.stage_in, big)) != cudaSuccess) { p.stage_in = nullptr; return cuda_fail(e, "staging alloc"); }
         if ((e = cudaMalloc(&p.stage_out, big)) != cudaSuccess) {
