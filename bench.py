@@ -333,7 +333,17 @@ def run_gpu(args):
 
     # ---------------- FP32 headline (plans with Legendre tables unless --no-tables)
     tables = not args.no_tables
-    pT, pP, b = make("fp32", 1e-5, tables)
+    tables_note = None
+    try:
+        pT, pP, b = make("fp32", 1e-5, tables)
+    except _native.LensError as err:
+        if not tables or err.status != 4:  # LENS_ERR_NOMEM: the tables (138 GB) did not fit
+            raise
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+        tables, tables_note = False, "tables did not fit in free device memory: %s" % err
+        pT, pP, b = make("fp32", 1e-5, False)
     plan_s = make.plan_s
     info_T, info_P = pT.info(), pP.info()
     clk = ClockSampler(local)
@@ -512,7 +522,8 @@ def run_gpu(args):
                    "legendre": ({"mode": "tables", "T_bytes": info_T["legendre_table_bytes"],
                                  "EB_bytes": info_P["legendre_table_bytes"],
                                  "plan_creation_s": round(plan_s, 3)} if tables else
-                                {"mode": "recursion", "plan_creation_s": round(plan_s, 3)}),
+                                {"mode": "recursion", "plan_creation_s": round(plan_s, 3),
+                                 "note": tables_note}),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "per_transform": {k: round(v, 1) for k, v in pt.items()},
         "roofline": roofline,
