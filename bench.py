@@ -396,9 +396,10 @@ def run_gpu(args):
     step_roofline = {"t_roof_ms": round(t_roof, 3), "t_measured_ms": round(ms, 3), "frac": round(t_roof / ms, 4),
                      "rule": "sum over stages of work / peak of the stage's bound (HBM bytes at %.1f GB/s, %s; "
                              "FP32 FMA flops at %.1f TFLOP/s)" % (hbm_bs / 1e9, peak_src, alu_fs / 1e12)}
-    # our kernel launches per step: Legendre 1, theta 1, phi 1, interp 1 (fwd); spread 1, phi 1, theta 1,
-    # Legendre 1 (adj) -> 8 per spin, 16 per step (memsets excluded)
-    gpu_launches = 16 * args.steps
+    # our kernel launches per step, per spin: coefficient preparation, Legendre, theta, phi,
+    # interpolation (synthesis); spreading, phi, theta, Legendre (adjoint) -> 9 per spin, 18 per
+    # step (memsets excluded; the ncu launch list of the timed region shows the same count)
+    gpu_launches = 18 * args.steps
 
     # ---------------- e2e through the host-buffer entry points (pinned memory)
     e2e = None
