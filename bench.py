@@ -6,8 +6,10 @@ deflected along the gradient of a lensing potential (phi lmax 4096,
 C_L^phiphi ~ (L+1)^-4 rescaled to 2.5 arcmin rms), CMB a_lm drawn from
 C_l = (l+10)^-2 exp(-(l/2990)^2).  One step = the whole hot path on that
 geometry: spin-0 T synthesis + adjoint, spin-2 E/B -> Q/U synthesis + adjoint.
-value = points / step time (FP32 plans, epsilon 1e-5); the FP64 plans
-(epsilon 1e-10) are measured in the same run and reported under "fp64".
+value = points / step time (FP32 plans, epsilon 1e-5, Legendre functions by the
+restarted FP32 recursion); the same step with plan-time Legendre tables
+("tables"), the FP64 plans (epsilon 1e-10, "fp64") and the lmax 5120 workload
+of the paper's Fig. 2 ("lmax5120") are measured in the same run.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gslens|reference]
 
@@ -48,9 +50,10 @@ KERNEL_FILES = {"legendre_synthesis": "legendre.cu", "legendre_adjoint": "legend
 # keyed by (slot name, sha1 of the kernel's source file at capture time).  A changed
 # source makes the entry stale and the bench reports traffic null.
 NCU_TRAFFIC = {
-    ("legendre_adjoint/spin2/fp32", "d846cc9777e2"): 741691904,  # profiles/legendre_adjoint_spin2_fp32_lmax4096.md
+    # df32-recursion adjoint, spin 2, lmax 4096 (capture of the kernel alone on a small point set)
+    ("legendre_adjoint/spin2/fp32", "d846cc9777e2"): 741691904,
     # table adjoint: lmax 2048 capture (12.756 GB for 11.977 GB of table + a_lm + ring bytes, ratio 1.065)
-    # scaled to lmax 4096's 92.75 GB; profiles/legendre_tables_adjoint_spin2_fp32.md
+    # scaled to lmax 4096's 92.75 GB of table + a_lm + ring bytes
     ("legendre_adjoint_tables/spin2/fp32", "4df24e5ff172"): 98778851588,
 }
 
@@ -64,12 +67,14 @@ def parse():
     ap.add_argument("--lmax", type=int, default=4096)
     ap.add_argument("--nside", type=int, default=2048)
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-tables", action="store_true",
-                    help="FP32 plans run the Legendre recursion instead of reading plan-time tables")
     ap.add_argument("--sigma", type=float, default=None,
                     help="force the NUFFT oversampling factor of the FP32 plans (small profiling cases)")
-    ap.add_argument("--no-recursion-compare", action="store_true",
-                    help="skip the extra measurement of the FP32 step with recursion plans")
+    ap.add_argument("--no-tables-compare", action="store_true",
+                    help="skip the extra measurement of the FP32 step with Legendre-table plans")
+    ap.add_argument("--tables", action="store_true",
+                    help="headline FP32 plans read plan-time Legendre tables instead of running the recursion")
+    ap.add_argument("--no-lmax5120", action="store_true",
+                    help="skip the lmax 5120 workload (paper's Fig. 2 configuration)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -182,6 +187,7 @@ def deflect_on_gpu(th0, ph0, phi_lm, lmax, dev):
 
 
 def legendre_triples(lmax, spin, nnorth):
+    """Dense (ring pair, l, m) triple count of one Legendre step."""
     tot = 0
     for m in range(lmax + 1):
         l0 = max(m, spin)
@@ -190,15 +196,18 @@ def legendre_triples(lmax, spin, nnorth):
 
 
 def stage_units(info, npts, spin, prec):
-    """Algorithmic work per launch of each stage (flops for the Legendre recursion, bytes otherwise;
-    a plan with Legendre tables streams table + coefficients + ring coefficients)."""
+    """Algorithmic work per launch of each stage: flops for the Legendre recursion (8 per spin-0
+    triple, 24 per spin-s triple, non-negligible triples as the plan counted them, else the dense
+    count), bytes otherwise; a plan with Legendre tables streams table + coefficients + ring
+    coefficients."""
     esz = 8 if prec == "fp32" else 16  # complex element
     rsz = esz // 2
     L, nt, ncol = info["lmax"], info["ntheta"], (2 * info["mmax"] + 1 if spin else info["mmax"] + 1)
     R, N2 = info["rows_kept"], info["n2"]
     gsz = rsz * (2 if spin else 1)
     nnorth = (nt + 1) // 2
-    leg_flops = 8 * (3 if spin else 1) * legendre_triples(L, spin, nnorth)
+    triples = info.get("legendre_triples") or legendre_triples(L, spin, nnorth)
+    leg_flops = 8 * (3 if spin else 1) * triples
     ring_b = ncol * nt * esz
     x_b = R * ncol * esz
     grid_b = R * N2 * gsz
@@ -217,6 +226,14 @@ def stage_units(info, npts, spin, prec):
         "interp": ("hbm", grid_b + pt_b, "GB/s"),
         "spread": ("hbm", 2 * grid_b + pt_b, "GB/s"),
     }
+
+
+def kernel_launches(info, prec):
+    """Kernels one synthesis + one adjoint launch on a (non-deterministic) plan: synthesis = coefficient
+    preparation, Legendre, theta, phi, interpolation; adjoint = spreading, phi, theta, Legendre; FP64
+    plans with double-float orders split each Legendre step into two launches (memsets not counted)."""
+    leg = 2 if (prec == "fp64" and info["legendre_df32_mmin"] <= info["mmax"]) else 1
+    return (4 + leg) + (3 + leg)
 
 
 # ------------------------------------------------------------------ ranks
@@ -246,10 +263,45 @@ def whole_job_rate(world, units_per_rank, ms):
 
 
 # ------------------------------------------------------------------ GPU arm
+def analyze(prof_ms, cnt, steps, units, slot0, peaks, prec):
+    """Stage rows of one profiled timed region (slots slot0 .. slot0 + 15: spin 0 then spin s) and the
+    roofline of its dominant kernel.  ALU work is divided by the measured FP32 FMA rate (the FP64
+    plans' Legendre kernels run their orders m >= m_df in double-float on the FP32 pipes; their
+    native-FP64 orders are a small share), bytes by the measured copy bandwidth."""
+    rows = []
+    for slot in range(slot0, slot0 + 16):
+        if cnt[slot] == 0:
+            continue
+        sp = (slot - slot0) // 8
+        name = STAGES[slot % 8]
+        avg = prof_ms[slot] / cnt[slot]
+        bound, work, unit = units[sp][name]
+        rows.append((prof_ms[slot] / steps, name, sp, avg, bound, work, unit, int(cnt[slot])))
+    rows.sort(reverse=True)
+    _, name, sp, avg, bound, work, unit, _ = rows[0]
+    if bound == "alu":
+        peak, achieved, note = peaks["fp32_tflops"], work / (avg * 1e-3) / 1e12, peaks["fp32_note"]
+    else:
+        peak, achieved, note = peaks["hbm_gbs"], work / (avg * 1e-3) / 1e9, peaks["hbm_note"]
+    roof = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "%s (spin %d, %s)" % (name, 2 if sp else 0, prec), "avg_launch_ms": round(avg, 4),
+            "peak_source": note, "slot": (name, sp)}
+    stages = [{"stage": r[1], "spin": 2 if r[2] else 0, "ms_per_step": round(r[0], 4),
+               "avg_launch_ms": round(r[3], 4), "bound": r[4],
+               "achieved": round(r[5] / (r[3] * 1e-3) / (1e12 if r[4] == "alu" else 1e9), 2),
+               "unit": r[6], "frac": round(r[5] / (r[3] * 1e-3) / (1e12 * peaks["fp32_tflops"] if r[4] == "alu"
+                                                                    else 1e9 * peaks["hbm_gbs"]), 4)}
+              for r in rows]
+    t_roof = 1e3 * sum(r[5] / (peaks["fp32_tflops"] * 1e12 if r[4] == "alu" else peaks["hbm_gbs"] * 1e9) * r[7] / steps
+                       for r in rows)
+    return stages, roof, t_roof
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
-    from paper_2304_10431_gb300 import LensPlan, _native, lib_path
+    from paper_2304_10431_gb300 import LensPlan, _native, lib_path, measure_fma_peak
 
     world, rank, local = rank_env()
     if world > 1:
@@ -257,31 +309,45 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _native.load()
-    peaks, peak_src = load_peaks()
+    mp, peak_src = load_peaks()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # FMA rates of the CUDA-core pipes, measured here (the Legendre recursion's roofline denominator)
+    clk = ClockSampler(local)
+    clk.start()
+    fma32, fma64 = measure_fma_peak("fp32"), measure_fma_peak("fp64")
+    fma_clocks = clk.stop()
+    peaks = {"hbm_gbs": float(mp.get("hbm_gbs", HBM_PEAK_FALLBACK)),
+             "hbm_note": "HBM copy bandwidth (MEASURED_PEAKS.json, %s)" % peak_src,
+             "fp32_tflops": fma32 / 1e12,
+             "fp32_note": "FP32 FMA rate measured by lens_measure_fma_peak in this run (fma chains on every SM)"}
+    measured_peaks = {"fp32_fma_tflops": round(fma32 / 1e12, 2), "fp64_fma_tflops": round(fma64 / 1e12, 3),
+                      "clocks": fma_clocks, "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peak_src}
+
     lmax, nside = args.lmax, args.nside
     th0, ph0, phi_lm, aT, aEB, ld = workload_arrays(lmax, nside)
     npts = th0.size
     th, ph, chi = deflect_on_gpu(th0, ph0, phi_lm, lmax, dev)
-    del th0, ph0
 
-    def make(prec, eps, tables=False):
+    def make(prec, eps, tables=False, L=None, geom=None, alms=None):
+        L = L or lmax
+        gth, gph, gchi = geom or (th, ph, chi)
+        at, aeb = alms or (aT, aEB)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sg = args.sigma if prec == "fp32" else None
-        pT = LensPlan(lmax, th, ph, spin=0, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg, device=dev)
-        pP = LensPlan(lmax, th, ph, chi, spin=2, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg,
+        pT = LensPlan(L, gth, gph, spin=0, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg, device=dev)
+        pP = LensPlan(L, gth, gph, gchi, spin=2, epsilon=eps, precision=prec, legendre_tables=tables, sigma=sg,
                       device=dev)
         torch.cuda.synchronize()
         make.plan_s = time.perf_counter() - t0
         ct = pT.complex_dtype
-        a_T = torch.as_tensor(aT, dtype=ct, device=dev)
-        a_P = torch.as_tensor(aEB, dtype=ct, device=dev)
+        a_T = torch.as_tensor(at, dtype=ct, device=dev)
+        a_P = torch.as_tensor(aeb, dtype=ct, device=dev)
         mT = pT.synthesis(a_T)
         mP = pP.synthesis(a_P)
         bufs = dict(a_T=a_T, a_P=a_P, m_T=mT, m_P=mP, o_mT=torch.empty_like(mT), o_mP=torch.empty_like(mP),
@@ -314,7 +380,13 @@ def run_gpu(args):
         lib.lens_profile_enable(0)
         return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
 
-    def per_transform(pT, pP, b, reps=3):
+    def profile_read():
+        pm = np.zeros(32)
+        cn = np.zeros(32, dtype=np.int64)
+        lib.lens_profile_read(pm.ctypes.data, cn.ctypes.data, 32)
+        return pm, cn
+
+    def per_transform(pT, pP, b, reps=3, n=None):
         out = {}
         for name, fn in (("T_synthesis", lambda: pT.synthesis(b["a_T"], out=b["o_mT"])),
                          ("T_adjoint", lambda: pT.adjoint(b["m_T"], out=b["o_aT"])),
@@ -328,78 +400,39 @@ def run_gpu(args):
                 fn()
             e1.record(stream)
             torch.cuda.synchronize()
-            out[name] = npts / (e0.elapsed_time(e1) / reps * 1e-3)
+            out[name] = round((n or npts) / (e0.elapsed_time(e1) / reps * 1e-3), 1)
         return out
 
-    # ---------------- FP32 headline (plans with Legendre tables unless --no-tables)
-    tables = not args.no_tables
-    tables_note = None
-    try:
-        pT, pP, b = make("fp32", 1e-5, tables)
-    except _native.LensError as err:
-        if not tables or err.status != 4:  # LENS_ERR_NOMEM: the tables (138 GB) did not fit
-            raise
-        import gc
-        gc.collect()
-        torch.cuda.empty_cache()
-        tables, tables_note = False, "tables did not fit in free device memory: %s" % err
-        pT, pP, b = make("fp32", 1e-5, False)
+    def leg_mode(info):
+        if info["legendre_table_bytes"]:
+            return {"mode": "tables", "bytes": info["legendre_table_bytes"]}
+        if info["legendre_restart"]:
+            return {"mode": "restarted FP32 recursion", "restart_every": info["legendre_restart"],
+                    "restart_bytes": info["restart_bytes"], "triples": info["legendre_triples"]}
+        return {"mode": "double-float recursion" if info["prec"] == 0 else "FP64 + double-float recursion",
+                "df32_from_m": info["legendre_df32_mmin"]}
+
+    # ---------------- FP32 headline: restarted FP32 Legendre recursion (--tables: plan-time tables)
+    tables = bool(args.tables)
+    pT, pP, b = make("fp32", 1e-5, tables)
     plan_s = make.plan_s
     info_T, info_P = pT.info(), pP.info()
     clk = ClockSampler(local)
     clk.start()
     ms = timed(pT, pP, b, args.steps, max(args.warmup, 3), profile=True, nvtx_name="timed_fp32")
     clocks = clk.stop()
-    prof_ms = np.zeros(32)
-    cnt = np.zeros(32, dtype=np.int64)
-    lib.lens_profile_read(prof_ms.ctypes.data, cnt.ctypes.data, 32)
-    gpu_launches = None
+    pm, cn = profile_read()
     pt = per_transform(pT, pP, b)
-
-    # dominant kernel and its roofline
     units = {0: stage_units(info_T, npts, 0, "fp32"), 1: stage_units(info_P, npts, 2, "fp32")}
-    stage_rows = []
-    for slot in range(16):
-        if cnt[slot] == 0:
-            continue
-        sp = slot // 8
-        name = STAGES[slot % 8]
-        avg = prof_ms[slot] / cnt[slot]
-        bound, work, unit = units[sp][name]
-        stage_rows.append((prof_ms[slot] / args.steps, name, sp, avg, bound, work, unit, int(cnt[slot])))
-    stage_rows.sort(reverse=True)
-    top = stage_rows[0]
-    _, name, sp, avg, bound, work, unit, nl = top
-    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if bound == "alu":
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
-        achieved = work / (avg * 1e-3) / 1e12
-        peak_note = "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_mhz_max
-    else:
-        peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-        achieved = work / (avg * 1e-3) / 1e9
-        peak_note = "HBM copy bandwidth (%s)" % peak_src
+    stages, roofline, t_roof = analyze(pm, cn, args.steps, units, 0, peaks, "fp32")
+    name, sp = roofline.pop("slot")
     key = ("%s%s/spin%d/fp32" % (name, "_tables" if tables else "", 2 if sp else 0), src_hash(KERNEL_FILES[name]))
-    traffic = NCU_TRAFFIC.get(key)
-    roofline = {"bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "%s (spin %d, fp32)" % (name, 2 if sp else 0), "avg_launch_ms": round(avg, 4),
-                "peak_source": peak_note}
-    stages = [{"stage": r[1], "spin": 2 if r[2] else 0, "ms_per_step": round(r[0], 4), "avg_launch_ms": round(r[3], 4),
-               "bound": r[4], "achieved": round(r[5] / (r[3] * 1e-3) / (1e12 if r[4] == "alu" else 1e9), 2),
-               "unit": r[6]} for r in stage_rows]
-    # whole-step roofline: each stage's algorithmic work at its bound's peak (HBM bytes at the
-    # measured copy bandwidth, ALU flops at the FP32 FMA peak), summed, against the step time
-    hbm_bs = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)) * 1e9
-    alu_fs = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6
-    t_roof = 1e3 * sum(r[5] / (alu_fs if r[4] == "alu" else hbm_bs) * r[7] / args.steps for r in stage_rows)
+    roofline["traffic"] = NCU_TRAFFIC.get(key)
     step_roofline = {"t_roof_ms": round(t_roof, 3), "t_measured_ms": round(ms, 3), "frac": round(t_roof / ms, 4),
                      "rule": "sum over stages of work / peak of the stage's bound (HBM bytes at %.1f GB/s, %s; "
-                             "FP32 FMA flops at %.1f TFLOP/s)" % (hbm_bs / 1e9, peak_src, alu_fs / 1e12)}
-    # our kernel launches per step, per spin: coefficient preparation, Legendre, theta, phi,
-    # interpolation (synthesis); spreading, phi, theta, Legendre (adjoint) -> 9 per spin, 18 per
-    # step (memsets excluded; the ncu launch list of the timed region shows the same count)
-    gpu_launches = 18 * args.steps
+                             "FP32 FMA flops at the measured %.1f TFLOP/s)" % (peaks["hbm_gbs"], peak_src,
+                                                                               peaks["fp32_tflops"])}
+    gpu_launches = (kernel_launches(info_T, "fp32") + kernel_launches(info_P, "fp32")) * args.steps
 
     # ---------------- e2e through the host-buffer entry points (pinned memory)
     e2e = None
@@ -441,68 +474,88 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d), "ms_per_step": round(ems, 3),
                "statistic": "median of %d steps" % len(times), "ms_mean": round(float(np.mean(times)), 3),
                "api": "lens_synthesis_host_async / lens_adjoint_host_async, T and E/B on two streams",
-               "ms_min": round(float(np.min(times)), 3), "ms_max": round(float(np.max(times)), 3)}
+               "ms_min": round(float(np.min(times)), 3), "ms_max": round(float(np.max(times)), 3),
+               "ms_all": [round(t, 2) for t in times]}
+    del b
+    pT.close(); pP.close()
+    torch.cuda.empty_cache()
 
-    # ---------------- the same FP32 step with recursion plans (no tables), for comparison
-    recursion = None
-    if tables and not args.no_recursion_compare:
-        rT, rP, rb = make("fp32", 1e-5, False)
-        kr = max(1, min(args.steps, 3))
-        msr = timed(rT, rP, rb, kr, 1, profile=False, nvtx_name="timed_fp32_recursion")
-        recursion = {"value": round(whole_job_rate(world, npts, msr), 1), "unit": "lensed points/s",
-                     "ms_per_step": round(msr, 3), "steps": kr,
-                     "what": "same step, FP32 plans without Legendre tables (df32 recursion per call)"}
-        del rb
-        rT.close(); rP.close()
+    # ---------------- the same FP32 step with plan-time Legendre tables (when they fit)
+    alt = None
+    if not args.no_tables_compare:
+        try:
+            rT, rP, rb = make("fp32", 1e-5, not tables)
+            alt_plan_s = make.plan_s
+            kr = args.steps
+            msr = timed(rT, rP, rb, kr, 3, profile=True, nvtx_name="timed_fp32_alt")
+            apm, acn = profile_read()
+            ui = {0: stage_units(rT.info(), npts, 0, "fp32"), 1: stage_units(rP.info(), npts, 2, "fp32")}
+            ast, aroof, at_roof = analyze(apm, acn, kr, ui, 0, peaks, "fp32")
+            aroof.pop("slot")
+            alt = {"value": round(whole_job_rate(world, npts, msr), 1), "unit": "lensed points/s",
+                   "ms_per_step": round(msr, 3), "steps": kr, "legendre": leg_mode(rT.info()) | {"EB": leg_mode(rP.info())},
+                   "plan_creation_s": round(alt_plan_s, 3), "roofline": aroof, "stages": ast,
+                   "step_roofline": {"t_roof_ms": round(at_roof, 3), "frac": round(at_roof / msr, 4)},
+                   "what": "same step, FP32 plans %s" % ("running the restarted FP32 recursion" if tables else
+                                                         "reading plan-time Legendre tables")}
+            del rb
+            rT.close(); rP.close()
+        except _native.LensError as err:  # LENS_ERR_NOMEM: the tables (138 GB at lmax 4096) did not fit
+            alt = {"unavailable": str(err)}
         torch.cuda.empty_cache()
 
     # ---------------- FP64 plans (epsilon 1e-10), same geometry
     fp64 = None
     if not args.no_fp64:
-        del b
-        pT.close(); pP.close()
-        torch.cuda.empty_cache()
         qT, qP, c = make("fp64", 1e-10)
         k64 = max(1, min(args.steps, 3))
         ms64 = timed(qT, qP, c, k64, 1, profile=True, nvtx_name="timed_fp64")
-        p64 = np.zeros(32)
-        c64 = np.zeros(32, dtype=np.int64)
-        lib.lens_profile_read(p64.ctypes.data, c64.ctypes.data, 32)
+        p64, c64 = profile_read()
         u64 = {0: stage_units(qT.info(), npts, 0, "fp64"), 1: stage_units(qP.info(), npts, 2, "fp64")}
-        rows64 = []
-        for slot in range(16, 32):
-            if c64[slot] == 0:
-                continue
-            s2 = (slot - 16) // 8
-            nm = STAGES[slot % 8]
-            av = p64[slot] / c64[slot]
-            bd, wk, un = u64[s2][nm]
-            rows64.append({"stage": nm, "spin": 2 if s2 else 0, "ms_per_step": round(p64[slot] / k64, 3),
-                           "avg_launch_ms": round(av, 3), "bound": bd,
-                           "achieved": round(wk / (av * 1e-3) / (1e12 if bd == "alu" else 1e9), 3),
-                           "unit": "TFLOP/s (FP64 ALU work)" if bd == "alu" else un})
-        rows64.sort(key=lambda r: -r["ms_per_step"])
-        top64 = rows64[0]
-        if top64["bound"] == "alu":
-            # the FP64 plans' Legendre kernels run orders m >= m_df in double-float on the
-            # FP32 pipes and the orders below natively on the FP64 pipe
-            peak64 = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12
-            note64 = ("FP32 FMA peak derived (152 SMs x 128 lanes x 2 flop x %.0f MHz): the double-float "
-                      "orders m >= m_df carry most of the work; the FP64 pipe's nominal rate is 1.25 TFLOP/s"
-                      % sm_mhz_max)
-        else:
-            peak64 = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-            note64 = "HBM copy bandwidth (%s)" % peak_src
-        roof64 = {"bound": top64["bound"], "achieved": top64["achieved"], "peak": round(peak64, 1),
-                  "unit": "TFLOP/s" if top64["bound"] == "alu" else "GB/s",
-                  "frac": round(top64["achieved"] / peak64, 4), "traffic": None,
-                  "kernel": "%s (spin %d, fp64)" % (top64["stage"], top64["spin"]),
-                  "avg_launch_ms": top64["avg_launch_ms"], "peak_source": note64}
+        st64, roof64, tr64 = analyze(p64, c64, k64, u64, 16, peaks, "fp64")
+        roof64.pop("slot")
         fp64 = {"value": round(whole_job_rate(world, npts, ms64), 1), "unit": "lensed points/s", "epsilon": 1e-10,
                 "ms_per_step": round(ms64, 3), "steps": k64, "per_transform": per_transform(qT, qP, c, reps=1),
+                "arithmetic": "FP64 Legendre recursion for orders m < %d, double-float (pairs of FP32) above; "
+                              "FP64 FFTs, kernel weights and interpolation/spreading" % qT.info()["legendre_df32_mmin"],
                 "plan": {k: qT.info()[k] for k in ("n1", "W", "sigma")} | {"W_spin2": qP.info()["W"]},
-                "roofline": roof64, "stages": rows64}
+                "roofline": roof64, "stages": st64,
+                "step_roofline": {"t_roof_ms": round(tr64, 3), "frac": round(tr64 / ms64, 4)}}
+        del c
         qT.close(); qP.close()
+        torch.cuda.empty_cache()
+
+    # ---------------- lmax 5120 (Fig. 2 configuration: lmax_unl 5120 on the same Nside 2048 points)
+    l5120 = None
+    if not args.no_lmax5120 and lmax == 4096:
+        from paper_2304_10431_gb300 import workloads as W
+        L5 = 5120
+        phi5 = W.draw_alm(W.phi_cl(4096), 4096, 2000)
+        th5, ph5, chi5 = deflect_on_gpu(th0, ph0, phi5, 4096, dev)
+        cl5 = W.cmb_cl(L5, 3750.0)
+        a5 = (W.draw_alm(cl5, L5, 1000)[None],
+              np.stack([W.draw_alm(cl5, L5, 1001, spin=2), W.draw_alm(cl5, L5, 1002, spin=2)]))
+        l5120 = {"workload": "T + E/B, lmax_unl 5120, l_damp 3750, phi lmax 4096, HEALPix Nside %d (%d points)"
+                             % (nside, npts), "legs": []}
+        for prec, eps in (("fp32", 1e-4), ("fp64", 1e-6), ("fp64", 1e-10), ("fp64", 1e-12)):
+            qT, qP, c = make(prec, eps, False, L=L5, geom=(th5, ph5, chi5), alms=a5)
+            ps = make.plan_s
+            k5 = 2 if prec == "fp32" else 1
+            ms5 = timed(qT, qP, c, k5, 1, profile=True, nvtx_name="timed_l5120")
+            p5, c5 = profile_read()
+            u5 = {0: stage_units(qT.info(), npts, 0, prec), 1: stage_units(qP.info(), npts, 2, prec)}
+            st5, roof5, tr5 = analyze(p5, c5, k5, u5, 0 if prec == "fp32" else 16, peaks, prec)
+            roof5.pop("slot")
+            l5120["legs"].append({"precision": prec, "epsilon": eps, "value": round(whole_job_rate(world, npts, ms5), 1),
+                                  "unit": "lensed points/s", "ms_per_step": round(ms5, 3), "steps": k5,
+                                  "per_transform": per_transform(qT, qP, c, reps=1),
+                                  "legendre": leg_mode(qT.info()), "W": qT.info()["W"],
+                                  "sigma": round(qT.info()["sigma"], 3), "plan_creation_s": round(ps, 2),
+                                  "roofline": roof5, "stages": st5[:6]})
+            del c
+            qT.close(); qP.close()
+            torch.cuda.empty_cache()
+        del th5, ph5, chi5
 
     result = {
         "metric": "lensed points/sec (synthesis and adjoint), lmax 4096, eps 1e-5 FP32 vs 1e-10 FP64",
@@ -511,7 +564,8 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (Legendre values from plan-time df32 recursion tables)" if tables else "f32 (df32 Legendre recursion)",
+        "dtype": "f32 (Legendre values from plan-time tables)" if tables else
+                 "f32 (FP32 Legendre recursion restarted from FP64-derived values)",
         "data": "synthetic: seeded CMB/phi a_lm, HEALPix centres lensed on the GPU",
         "config": {"workload": "T + E/B lensing, lmax 4096, HEALPix Nside %d (%d points), phi lmax %d, "
                                "2.5 arcmin rms deflection, l_damp %.0f" % (nside, npts, lmax, ld),
@@ -520,22 +574,20 @@ def run_gpu(args):
                    "plan_T": {k: info_T[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
                    "plan_EB": {k: info_P[k] for k in ("ntheta", "n1", "n2", "W", "sigma", "beta")},
                    "l2": "per-step inputs 0.8 GB > 129 MB L2 (no flush)",
-                   "legendre": ({"mode": "tables", "T_bytes": info_T["legendre_table_bytes"],
-                                 "EB_bytes": info_P["legendre_table_bytes"],
-                                 "plan_creation_s": round(plan_s, 3)} if tables else
-                                {"mode": "recursion", "plan_creation_s": round(plan_s, 3),
-                                 "note": tables_note}),
+                   "legendre": {"T": leg_mode(info_T), "EB": leg_mode(info_P), "plan_creation_s": round(plan_s, 3)},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "per_transform": {k: round(v, 1) for k, v in pt.items()},
+        "per_transform": pt,
         "roofline": roofline,
         "stages": stages,
         "step_roofline": step_roofline,
+        "measured_peaks": measured_peaks,
         "gpu_launches": gpu_launches,
         "library": os.path.relpath(lib_path(), ROOT),
         "clocks": clocks,
         "e2e": e2e,
-        "recursion": recursion,
+        "tables" if not tables else "recursion": alt,
         "fp64": fp64,
+        "lmax5120": l5120,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lmax, nside, args.cpu_seconds)

@@ -107,8 +107,9 @@ typedef struct {
     int W;          /* kernel support in grid cells (4 .. 16) */
     double beta;    /* ES kernel shape parameter */
     int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
-    int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1 or 2) */
-    int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (1 or 2) */
+    int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1 or 2; also 4
+                              for FP32 plans with the restarted FP32 recursion) */
+    int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (as above) */
     int legendre_df32_mmin; /* FP64 plans: orders m >= this value use the double-float Legendre
                                recursion (0 = choose, -1 = never) */
     int fft_cluster;        /* CTAs per FFT vector: 0 = choose (1, or a cluster of 2 or 4 when
@@ -119,6 +120,15 @@ typedef struct {
                                Legendre steps then stream them instead of running the
                                recursion.  0 = recursion (default).  LENS_ERR_NOMEM if the
                                tables do not fit. */
+    int legendre_restart;   /* FP32 plans without tables, Legendre recursion arithmetic:
+                               0 = choose: epsilon >= 1e-5 runs the recursion in FP32 and
+                               resets it every K = 64 degrees (K doubled while the restart
+                               values would exceed 16 GB) to values computed at plan creation
+                               (FP64 recursion; 8 or 16 bytes per ring, restart and order:
+                               2.3 / 4.5 GB for spin 0 / spin s at lmax 4096); smaller
+                               epsilon runs the double-float recursion.
+                               -1 = always the double-float recursion.
+                               K > 0 = restart every K degrees (a power of two, 8 .. 4096). */
 } lens_plan_params;
 
 typedef struct {
@@ -137,6 +147,12 @@ typedef struct {
     unsigned flags;            /* lens_flags the plan was created with */
     int alm_ncomp;             /* components of an a_lm buffer: 1 (spin 0, LENS_GRAD_ONLY) or 2 */
     size_t legendre_table_bytes; /* Legendre tables held by the plan (0: recursion) */
+    int legendre_restart;        /* FP32 recursion restarted every this many degrees
+                                    (0: double-float or FP64 recursion, or tables) */
+    size_t restart_bytes;        /* restart values held by the plan */
+    int legendre_df32_mmin;      /* FP64 plans: first order run in double-float (mmax + 1: none) */
+    int64_t legendre_triples;    /* restarted FP32 recursion: (ring pair, l, m) triples from the first
+                                    degree at which |lambda| reaches 2^-40 on each ring (0 if not counted) */
 } lens_plan_info_t;
 
 /*
@@ -403,9 +419,21 @@ int lens_adjoint_host_async(lens_plan p, const void *map_h, void *alm_h, int nma
  * (the message gives both sizes; use lens_synthesis then).  The array's
  * device address is looked up on the first call made on each device, which
  * should therefore come before any stream capture.  Every call shares the
- * array: calls that overlap on the GPU race.
+ * array: calls that overlap on the GPU race.  The call still uses the plan's
+ * own prepared-coefficient buffer and status flags (allocated when the plan
+ * was created), so it must not overlap any other call on the same plan.
  */
 int lens_synthesis_static(lens_plan p, const void *alm_d, void *map_d, void *stream);
+
+/*
+ * Measured FMA throughput of the current device's CUDA-core pipes (no
+ * counterpart in the paper: the denominator of the ALU rooflines that the
+ * benchmark reports for the Legendre recursion, which is not a contraction).
+ * Runs independent fma chains on every SM for about 0.25 s and returns the
+ * rate in flops per second (2 per fused multiply-add) in *flops_per_s.
+ *   prec  LENS_FP32 or LENS_FP64.  Synchronises the stream.
+ */
+int lens_measure_fma_peak(int prec, double *flops_per_s, void *stream);
 
 /*
  * Legendre step alone (Sect. 3 "synthesis" restricted to the theta direction):

@@ -33,6 +33,19 @@ def lib_path() -> str:
     return _native.lib_path()
 
 
+def measure_fma_peak(precision: str = "fp32", device=None) -> float:
+    """Measured FMA rate of the device's CUDA-core pipes, flops/s (lens_measure_fma_peak)."""
+    if precision not in _PREC:
+        raise ValueError("precision must be 'fp32' or 'fp64'")
+    lib = _native.load()
+    v = ctypes.c_double(0.0)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _native.check(lib.lens_measure_fma_peak(_PREC[precision], ctypes.byref(v),
+                                                _stream_handle(torch.cuda.current_stream(dev))))
+    return float(v.value)
+
+
 def nalm(lmax: int, mmax: int | None = None) -> int:
     return int(_native.load().lens_nalm(lmax, lmax if mmax is None else mmax))
 
@@ -57,7 +70,7 @@ class LensPlan:
                  W: int | None = None, beta: float | None = None, ntheta: int | None = None,
                  legendre_rpt: tuple | None = None, legendre_df32_mmin: int = 0, fft_cluster: int = 0,
                  grad_only: bool = False, deterministic: bool = False, legendre_tables: bool = False,
-                 device=None, stream=None):
+                 legendre_restart: int = 0, device=None, stream=None):
         lib = _native.load()
         if precision not in _PREC:
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -79,7 +92,8 @@ class LensPlan:
             self.npoints = int(th.numel())
             rf, ra = legendre_rpt if legendre_rpt else (0, 0)
             prm = PlanParams(float(sigma or 0.0), int(W or 0), float(beta or 0.0), int(ntheta or 0), int(rf), int(ra),
-                             int(legendre_df32_mmin), int(fft_cluster), 1 if legendre_tables else 0)
+                             int(legendre_df32_mmin), int(fft_cluster), 1 if legendre_tables else 0,
+                             int(legendre_restart))
             handle = ctypes.c_void_p()
             st = _stream_handle(stream)
             rc = lib.lens_plan_create_ex(ctypes.byref(handle), self.lmax, self.mmax, self.spin, self.npoints,

@@ -45,6 +45,7 @@ EXPORTS = {
     "lens_synthesis_host_async": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_adjoint_host_async": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "lens_synthesis_static": (_i32, [_vp, _vp, _vp, _vp]),
+    "lens_measure_fma_peak": (_i32, [_i32, _vp, _vp]),
     "lens_ring_synthesis": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_ring_adjoint": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_pointing": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -62,7 +63,8 @@ EXPORTS = {
 class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("W", ctypes.c_int), ("beta", ctypes.c_double),
                 ("ntheta", ctypes.c_int), ("legendre_rpt_fwd", ctypes.c_int), ("legendre_rpt_adj", ctypes.c_int),
-                ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int), ("legendre_tables", ctypes.c_int)]
+                ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int), ("legendre_tables", ctypes.c_int),
+                ("legendre_restart", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -72,7 +74,9 @@ class PlanInfo(ctypes.Structure):
                 ("beta", ctypes.c_double), ("sigma", ctypes.c_double), ("rows_kept", ctypes.c_int),
                 ("row_pitch", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
                 ("plan_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint), ("alm_ncomp", ctypes.c_int),
-                ("legendre_table_bytes", ctypes.c_size_t)]
+                ("legendre_table_bytes", ctypes.c_size_t), ("legendre_restart", ctypes.c_int),
+                ("restart_bytes", ctypes.c_size_t), ("legendre_df32_mmin", ctypes.c_int),
+                ("legendre_triples", ctypes.c_int64)]
 
 
 def lib_path() -> str:

@@ -12,6 +12,7 @@ namespace gsl {
 
 constexpr int kMaxFftStages = 24;
 constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
+constexpr int kLegBlock = 8;         // degrees per unrolled block of the Legendre kernels
 constexpr int kTileR = 32, kTileC = 32;  // grid tile of the point sort (rows x columns)
 
 // One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
@@ -30,7 +31,37 @@ struct RingTab {
     const float2 *xdf = nullptr;      // cos(theta_j) as a df32 pair
     const double *lsin2 = nullptr;    // log2 sin(theta_j / 2)  (-inf at the pole)
     const double *lcos2 = nullptr;    // log2 cos(theta_j / 2)
+    const float *y1 = nullptr;        // 1 - cos(theta_j) = 2 sin^2(theta_j / 2), FP32
 };
+
+// Restart values of the FP32 Legendre recursion (FP32 plans, see legendre.cu):
+// entry base[m] + (k - 1) nnorth + ring holds the recursion state before the
+// k-th restart of order m (every K degrees) as the pair v (float2, spin s:
+// float4 for +s then -s) scaled by 2^(-60 E) and its exponent E (e: short,
+// spin s short2; kCkZero marks a state that is identically zero).  Rings
+// below jb (a multiple of 128: no warp straddles it) run Reinsch's form of the
+// recursion.
+// kstart[m][g]: the restart at which the 32 rings g*32 .. g*32+31 of order m
+// begin (every degree before it is below 2^-40 on all of them; 0 = from the
+// start value).
+constexpr int kCkZero = -30000;
+struct CkTab {
+    const void *v = nullptr;
+    const void *e = nullptr;
+    const int64_t *base = nullptr;
+    const short *kstart = nullptr;
+    int ngrp = 0;
+    int K = 0, jb = 0;
+};
+
+// Restarts of an order whose block loop starts at degree lf (= max(m, s) + 1):
+// the degrees lf + K k, k >= 1, at which a full block of kLegBlock degrees
+// still runs.
+__host__ __device__ __forceinline__ int ck_count(int lmax, int lf, int K)
+{
+    const int n = lmax + 1 - kLegBlock - lf;
+    return (K > 0 && n >= K) ? n / K : 0;
+}
 
 struct Plan {
     // problem
@@ -61,6 +92,14 @@ struct Plan {
     LegShape leg_f, leg_a, leg_fd, leg_ad;
     LegShape leg_fb[2];  // FP32 forward sharing the recursion among 2 / 4 maps
     int m_df = 0;
+    // FP32 plans: restarted FP32 recursion (rst) with its step table rec_s
+    // (float4 per alm index) and restart values ck (ck_bytes); otherwise the
+    // df32 recursion of rec_a
+    bool rst = false;
+    void *rec_s = nullptr;
+    CkTab ck;
+    size_t ck_bytes = 0;
+    int64_t leg_triples = 0;  // non-negligible (ring pair, l, m) triples (restarted plans)
 
     // tables (device)
     // monic-form recursion coefficients per alm index: alpha and (spin s) tau,
@@ -121,7 +160,7 @@ struct Plan {
     void *stage_in = nullptr, *stage_out = nullptr;
 
     size_t plan_bytes = 0, work_bytes = 0;
-    void *allocs[64];
+    void *allocs[128];
     int nallocs = 0;
 };
 
@@ -129,6 +168,10 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_rec_tables(Plan &p);
+// restarted FP32 recursion: step table, then restart values from the FP64
+// monic recursion (a64, t64: temporary FP64 alpha / tau tables of the plan)
+cudaError_t launch_rec_tables_s(Plan &p);
+cudaError_t launch_ck_build(Plan &p, double *a64, double *t64, void *v_out, void *e_out, int *lt, short *kstart);
 // Legendre tables: shape, first-entry degrees, rows, values (plan creation)
 cudaError_t tab_shape(Plan &p);
 // bounded-wait self-test kernel (one warp, an mbarrier that never completes)
@@ -166,6 +209,17 @@ int run_adjoint(const Plan &p, const void *map, void *alm, cudaStream_t st, doub
 // Sets the stage-timer switch, returning its previous state (stream capture
 // runs with the timers off).
 bool profile_swap(bool on);
+
+// Bytes of the per-call work buffers of one map's forward chain: ring
+// coefficients [ncol][ntheta], torus rows [R][ncol] (complex) and the
+// oversampled grid [R][pitch] (real for spin 0, complex for spin s).
+struct ScratchSizes { size_t ring, X, grid; };
+inline ScratchSizes plan_scratch_sizes(const Plan &p)
+{
+    const size_t esz = p.prec == LENS_FP32 ? 8 : 16;
+    return {esz * (size_t)p.ncol * p.ntheta, esz * (size_t)p.R * p.ncol,
+            (esz / 2) * (p.spin ? 2 : 1) * (size_t)p.R * p.pitch};
+}
 
 // Bytes of one map's a_lm / point values for a plan.
 inline size_t plan_alm_bytes(const Plan &p) { return (size_t)p.nalm * p.alm_ncomp() * (p.prec == LENS_FP32 ? 8 : 16); }

@@ -60,7 +60,7 @@ constexpr float kSmallF = 0x1p-60f;
 constexpr double kBigD = 0x1p60;
 constexpr double kSmallD = 0x1p-60;
 constexpr int kSkipE = -4;  // below 2^-180 before a block; 8 steps grow by at most 2^68
-constexpr int kBlk = 8;
+constexpr int kBlk = kLegBlock;
 
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
@@ -85,6 +85,7 @@ __device__ __forceinline__ df32 df_norm(df32 a)  // two-sum: exact for any order
 // sums, K a real coefficient component (prepared a_lm or ring input), A a
 // real accumulator; fma(acc, k, v) is acc += k v, fms(acc, k, v) acc -= k v.
 struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
+    static constexpr bool kRestart = false;  // no restart values (see PolS)
     using R = float;
     using C = float2;
     using X = df32;
@@ -211,6 +212,7 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
 };
 
 struct PolF64 {  // native FP64 (FP64 plans, low orders)
+    static constexpr bool kRestart = false;
     using R = double;
     using C = double2;
     using X = double;
@@ -368,6 +370,55 @@ struct PolDD : PolDF {
     static __device__ __forceinline__ C cout(A re, A im) { return make_double2(aout(re), aout(im)); }
 };
 
+// FP32 plans with restart values (the default for epsilon >= 1e-5): FP32
+// recursion state in the normalised form
+//   lambda_l = (A_l x + sigma AT_l) lambda_{l-1} - B_l lambda_{l-2},  AT_l = A_l T_l,
+// reset every K degrees to FP32 values of lambda computed at plan creation by
+// an FP64 recursion (k_ck_build), so that FP32 rounding accumulates over at
+// most K steps instead of lmax.  Table entry per (m, l): float4
+// (A_l, B_l, AT_l, K_l) with K_l = 1 + B_l - A_l - AT_l (the +s value;
+// -s: K_l + 2 AT_l).  The values are lambda itself (no monic scale c_l).
+// Two forms of the step, chosen per warp by ring (Rings<PolS> / Rings<PolR>):
+//  * PolS, rings with x = cos theta below ~0.7: the plain step above.
+//  * PolR, rings nearer the pole: Reinsch's form, state (lambda_l,
+//    D_l = lambda_l - lambda_{l-1}) with
+//      D_l = B_l D_{l-1} - d_l lambda_{l-1},  lambda_l = lambda_{l-1} + D_l,
+//      d_l = 1 + B_l - A_l x - sigma AT_l = K_l + A_l (1 - x).
+//    There the plain step coefficient is close to 2 and its FP32 rounding
+//    (an absolute 1e-7) shifts the phase of the oscillation by ~1e-7 / theta
+//    per degree; d_l is formed from 1 - x and the small K_l, so its rounding
+//    is relative to d_l instead.
+// Accumulation as PolDF (FP32).  Start values and the 2^(60 E) scaling as PolDF.
+struct PolS : PolDF {
+    static constexpr bool kRestart = true;
+    using X = float;
+    using Tab = float4;
+    using TTab = float4;
+    using TabAT = float4;
+    struct St { float w[2]; int E; };
+    static __device__ __forceinline__ void start(St &s, double L2, int sign, bool zero)
+    {
+        s.w[0] = 0.f;
+        if (zero) { s.w[1] = 0.f; s.E = -1000; return; }
+        const double e = floor(L2 * (1.0 / kScaleBits));
+        const double fr = L2 - e * kScaleBits;  // [0, 60)
+        const double ip = floor(fr);
+        const float m = ldexpf(exp2f((float)(fr - ip)), (int)ip);
+        s.w[1] = sign < 0 ? -m : m;
+        s.E = (int)e;
+    }
+    static __device__ __forceinline__ void zero(St &s) { s.w[0] = 0.f; s.w[1] = 0.f; s.E = 0; }
+    static __device__ __forceinline__ void rescale(St &s, int newest)
+    {
+        if (s.E < 0 && fabsf(s.w[newest]) > kBigF) {
+            s.w[0] *= kSmallF;
+            s.w[1] *= kSmallF;
+            s.E += 1;
+        }
+    }
+};
+struct PolR : PolS {};
+
 // Start value of sigma lambda_{l0,m} at ring j (north half), sigma = +-s.
 //   m >= s:  (-1)^m sqrt((2m+1)/4pi C(2m, m+s)) c^(m-sigma) s^(m+sigma)
 //   m <  s:  sigma>0: (-1)^m ..(2s+1).. c^(s-m) s^(s+m); sigma<0: (-1)^s .. c^(s+m) s^(s-m)
@@ -483,6 +534,225 @@ template <class P, int RPT, bool SPIN> struct Rings {
         typename P::V v = P::val(sm[k].w[NW]);
         if (SCALED) v = P::vscale(v, P::fac(sm[k].E));
         return v;
+    }
+};
+
+// Rings of the restarted FP32 recursion, plain form: word NW receives the
+// newest value (as in the generic Rings), so at a block boundary w[1] holds
+// lambda_{l-1} and w[0] lambda_{l-2}.
+template <int RPT, bool SPIN> struct Rings<PolS, RPT, SPIN> {
+    using P = PolS;
+    float x[RPT];
+    P::St sp[RPT], sm[RPT];
+
+    // ring geometry only (the state comes from a restart)
+    __device__ __forceinline__ void init_geom(const RingTab &rt, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            x[k] = rp0 + k < nnorth ? __ldg(rt.xdf + rp0 + k).x : 0.f;
+            P::zero(sp[k]);
+            P::zero(sm[k]);
+        }
+    }
+    __device__ __forceinline__ void init(const RingTab &rt, int rp0, int nnorth, int m, int s, double lnm)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp < nnorth) {
+                x[k] = __ldg(rt.xdf + rp).x;
+                const double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
+                start_value<P>(sp[k], m, s, s, lnm, ls, lc);
+                if (SPIN) start_value<P>(sm[k], m, s, -s, lnm, ls, lc);
+            } else {
+                x[k] = 0.f;
+                P::zero(sp[k]);
+                P::zero(sm[k]);
+            }
+        }
+    }
+    __device__ __forceinline__ int regime() const
+    {
+        bool all0 = true, allneg = true;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            all0 = all0 && sp[k].E == 0;
+            allneg = allneg && sp[k].E <= kSkipE;
+            if (SPIN) {
+                all0 = all0 && sm[k].E == 0;
+                allneg = allneg && sm[k].E <= kSkipE;
+            }
+        }
+        if (__all_sync(0xffffffffu, all0)) return 0;
+        if (__all_sync(0xffffffffu, allneg)) return 1;
+        return 2;
+    }
+    template <int NW, bool CHECK>
+    __device__ __forceinline__ void advance(const float4 *reca, const float4 *, int l)
+    {
+        const float4 c = __ldg(reca + l);  // (A, B, AT, K)
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!SPIN) {
+                sp[k].w[NW] = __fmaf_rn(c.x * x[k], sp[k].w[1 - NW], -(c.y * sp[k].w[NW]));
+            } else {
+                const float cp = __fmaf_rn(c.x, x[k], c.z), cm = __fmaf_rn(c.x, x[k], -c.z);
+                sp[k].w[NW] = __fmaf_rn(cp, sp[k].w[1 - NW], -(c.y * sp[k].w[NW]));
+                sm[k].w[NW] = __fmaf_rn(cm, sm[k].w[1 - NW], -(c.y * sm[k].w[NW]));
+            }
+            if (CHECK) {
+                P::rescale(sp[k], NW);
+                if (SPIN) P::rescale(sm[k], NW);
+            }
+        }
+    }
+    __device__ __forceinline__ void advance_moved(const float4 *reca, const float4 *rect, int l)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const float a = sp[k].w[0];
+            sp[k].w[0] = sp[k].w[1];
+            sp[k].w[1] = a;
+            if (SPIN) {
+                const float b = sm[k].w[0];
+                sm[k].w[0] = sm[k].w[1];
+                sm[k].w[1] = b;
+            }
+        }
+        advance<1, true>(reca, rect, l);
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vplus(int k) const
+    {
+        return SCALED ? sp[k].w[NW] * P::fac(sp[k].E) : sp[k].w[NW];
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vminus(int k) const
+    {
+        return SCALED ? sm[k].w[NW] * P::fac(sm[k].E) : sm[k].w[NW];
+    }
+    // restart: state (w[0], w[1]) and exponent E from the table
+    __device__ __forceinline__ void restart(const CkTab &ck, int64_t row, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp >= nnorth) continue;
+            if (!SPIN) {
+                const float2 v = __ldg((const float2 *)ck.v + row + rp);
+                sp[k].w[0] = v.x; sp[k].w[1] = v.y; sp[k].E = __ldg((const short *)ck.e + row + rp);
+            } else {
+                const float4 v = __ldg((const float4 *)ck.v + row + rp);
+                const short2 e = __ldg((const short2 *)ck.e + row + rp);
+                sp[k].w[0] = v.x; sp[k].w[1] = v.y; sp[k].E = e.x;
+                sm[k].w[0] = v.z; sm[k].w[1] = v.w; sm[k].E = e.y;
+            }
+        }
+    }
+};
+
+// Rings of the restarted FP32 recursion, Reinsch's form (PolR): w[1] holds
+// the value lambda_l, w[0] the difference D_l = lambda_l - lambda_{l-1};
+// the word index NW of the interface is not used.
+template <int RPT, bool SPIN> struct Rings<PolR, RPT, SPIN> {
+    using P = PolS;
+    float y1[RPT];  // 1 - cos theta
+    P::St sp[RPT], sm[RPT];
+
+    __device__ __forceinline__ void init_geom(const RingTab &rt, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            y1[k] = rp0 + k < nnorth ? __ldg(rt.y1 + rp0 + k) : 0.f;
+            P::zero(sp[k]);
+            P::zero(sm[k]);
+        }
+    }
+    __device__ __forceinline__ void init(const RingTab &rt, int rp0, int nnorth, int m, int s, double lnm)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp < nnorth) {
+                y1[k] = __ldg(rt.y1 + rp);
+                const double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
+                start_value<P>(sp[k], m, s, s, lnm, ls, lc);
+                sp[k].w[0] = sp[k].w[1];  // D_{l0} = lambda_{l0} (lambda_{l0-1} = 0)
+                if (SPIN) {
+                    start_value<P>(sm[k], m, s, -s, lnm, ls, lc);
+                    sm[k].w[0] = sm[k].w[1];
+                }
+            } else {
+                y1[k] = 0.f;
+                P::zero(sp[k]);
+                P::zero(sm[k]);
+            }
+        }
+    }
+    __device__ __forceinline__ int regime() const
+    {
+        bool all0 = true, allneg = true;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            all0 = all0 && sp[k].E == 0;
+            allneg = allneg && sp[k].E <= kSkipE;
+            if (SPIN) {
+                all0 = all0 && sm[k].E == 0;
+                allneg = allneg && sm[k].E <= kSkipE;
+            }
+        }
+        if (__all_sync(0xffffffffu, all0)) return 0;
+        if (__all_sync(0xffffffffu, allneg)) return 1;
+        return 2;
+    }
+    template <int NW, bool CHECK>
+    __device__ __forceinline__ void advance(const float4 *reca, const float4 *, int l)
+    {
+        const float4 c = __ldg(reca + l);  // (A, B, AT, K)
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const float dp = __fmaf_rn(c.x, y1[k], c.w);
+            sp[k].w[0] = __fmaf_rn(c.y, sp[k].w[0], -(dp * sp[k].w[1]));
+            sp[k].w[1] = __fadd_rn(sp[k].w[1], sp[k].w[0]);
+            if (SPIN) {
+                const float dm = __fmaf_rn(c.x, y1[k], __fmaf_rn(2.f, c.z, c.w));
+                sm[k].w[0] = __fmaf_rn(c.y, sm[k].w[0], -(dm * sm[k].w[1]));
+                sm[k].w[1] = __fadd_rn(sm[k].w[1], sm[k].w[0]);
+            }
+            if (CHECK) {
+                P::rescale(sp[k], 1);
+                if (SPIN) P::rescale(sm[k], 1);
+            }
+        }
+    }
+    __device__ __forceinline__ void advance_moved(const float4 *reca, const float4 *rect, int l)
+    {
+        advance<1, true>(reca, rect, l);
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vplus(int k) const
+    {
+        return SCALED ? sp[k].w[1] * P::fac(sp[k].E) : sp[k].w[1];
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vminus(int k) const
+    {
+        return SCALED ? sm[k].w[1] * P::fac(sm[k].E) : sm[k].w[1];
+    }
+    // restart: state (w[0], w[1]) and exponent E from the table
+    __device__ __forceinline__ void restart(const CkTab &ck, int64_t row, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp >= nnorth) continue;
+            if (!SPIN) {
+                const float2 v = __ldg((const float2 *)ck.v + row + rp);
+                sp[k].w[0] = v.x; sp[k].w[1] = v.y; sp[k].E = __ldg((const short *)ck.e + row + rp);
+            } else {
+                const float4 v = __ldg((const float4 *)ck.v + row + rp);
+                const short2 e = __ldg((const short2 *)ck.e + row + rp);
+                sp[k].w[0] = v.x; sp[k].w[1] = v.y; sp[k].E = e.x;
+                sm[k].w[0] = v.z; sm[k].w[1] = v.w; sm[k].E = e.y;
+            }
+        }
     }
 };
 
@@ -614,12 +884,25 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
 // NM maps share each recursion (prepared coefficients of map b at coef + b *
 // ncomp nalm entries, its ring coefficients at ring + b * ring_stride).
 // GRAD: gradient-only spin s (prepared coefficients of G alone, see FwdAcc).
-template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false>
-__global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_a,
-                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
-                                                 RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
-                                                 int spin, int ntheta, int nnorth, int64_t nalm, int m_begin,
-                                                 int64_t ring_stride)
+// First restart of the calling warp for order m: the smallest kstart over the
+// 32-ring groups its 32 RPT rings cover (uniform over the warp).
+template <int RPT> __device__ __forceinline__ int first_restart(const CkTab &ck, int m)
+{
+    const int lane = threadIdx.x & 31;
+    const int g0 = (((blockIdx.x * blockDim.x + threadIdx.x) & ~31) * RPT) >> 5;
+    int k = 0x7fff;
+    if (lane < RPT && g0 + lane < ck.ngrp) k = __ldg(ck.kstart + (int64_t)m * ck.ngrp + g0 + lane);
+    return __reduce_min_sync(0xffffffffu, k);
+}
+
+// Restarted FP32 recursions (P::kRestart) reset their state from ck at every
+// K-th degree of the block loop.
+template <class P, int RPT, bool SPIN, int NM, bool GRAD>
+__device__ __forceinline__ void leg_fwd_body(const void *__restrict__ coef, const void *__restrict__ rec_a,
+                                             const void *__restrict__ rec_t, const double *__restrict__ lognorm,
+                                             const RingTab &rt, typename P::C *__restrict__ ring, int lmax, int mmax,
+                                             int spin, int ntheta, int nnorth, int64_t nalm, int m_begin,
+                                             int64_t ring_stride, const CkTab &ck)
 {
     using Sg = decltype(P::fac(0));
     using Cx = typename P::C;
@@ -636,16 +919,31 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
     const typename P::TTab *rect = SPIN ? (const typename P::TTab *)rec_t + base : nullptr;
     const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * RPT;
 
+    const int lf = l0 + 1;
     Rings<P, RPT, SPIN> st;
-    st.init(rt, rp0, nnorth, m, s, lognorm[m]);
     FwdAcc<P, RPT, SPIN, NM, GRAD> acc;
     acc.init(coef, nalm, base);
-
-    const int lf = l0 + 1;
     const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);  // (-1)^(lf - m)
-    acc.add_rt(st, l0, true);                         // l0 = lf - 1
     int l = lf;
+    bool jumped = false;
+    if constexpr (P::kRestart) {  // start at the warp's first restart: every earlier degree is negligible
+        const int kj = first_restart<RPT>(ck, m);
+        if (kj > 0) {
+            st.init_geom(rt, rp0, nnorth);
+            l = lf + kj * ck.K;  // the restart at l sets the state
+            jumped = true;
+        }
+    }
+    if (!jumped) {
+        st.init(rt, rp0, nnorth, m, s, lognorm[m]);
+        acc.add_rt(st, l0, true);  // l0 = lf - 1
+    }
+    const int64_t ckrow = P::kRestart ? __ldg(ck.base + m) : 0;
     for (; l + kBlk <= lmax + 1; l += kBlk) {
+        if constexpr (P::kRestart) {
+            const int dl = l - lf;
+            if (dl != 0 && (dl & (ck.K - 1)) == 0) st.restart(ck, ckrow + (int64_t)(dl / ck.K - 1) * nnorth, rp0, nnorth);
+        }
         const int reg = st.regime();
         acc.renorm();
         if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM, GRAD>(st, acc, reca, rect, l);
@@ -699,6 +997,35 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
                 }
             }
         }
+}
+
+template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false>
+__global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, const void *__restrict__ rec_a,
+                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
+                                                 RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
+                                                 int spin, int ntheta, int nnorth, int64_t nalm, int m_begin,
+                                                 int64_t ring_stride)
+{
+    leg_fwd_body<P, RPT, SPIN, NM, GRAD>(coef, rec_a, rec_t, lognorm, rt, ring, lmax, mmax, spin, ntheta, nnorth,
+                                         nalm, m_begin, ring_stride, CkTab{});
+}
+
+// Restarted FP32 recursion: warps whose rings lie below ck.jb run Reinsch's
+// form, the others the plain form (the choice is uniform per warp).
+template <int RPT, bool SPIN, int NM = 1, bool GRAD = false>
+__global__ void __launch_bounds__(512) k_leg_fwd32(const void *__restrict__ coef, const void *__restrict__ rec_s,
+                                                   const double *__restrict__ lognorm, RingTab rt,
+                                                   float2 *__restrict__ ring, int lmax, int mmax, int spin, int ntheta,
+                                                   int nnorth, int64_t nalm, int m_begin, int64_t ring_stride,
+                                                   CkTab ck)
+{
+    const int wr0 = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) * RPT;  // first ring of the warp
+    if (wr0 < ck.jb)
+        leg_fwd_body<PolR, RPT, SPIN, NM, GRAD>(coef, rec_s, nullptr, lognorm, rt, ring, lmax, mmax, spin, ntheta,
+                                                nnorth, nalm, m_begin, ring_stride, ck);
+    else
+        leg_fwd_body<PolS, RPT, SPIN, NM, GRAD>(coef, rec_s, nullptr, lognorm, rt, ring, lmax, mmax, spin, ntheta,
+                                                nnorth, nalm, m_begin, ring_stride, ck);
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -859,8 +1186,9 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
     if (!SPIN) {
         if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1)) {
             const int64_t dst = 2 * (base + l) + c;
-            if (fx) P::atomic_add_fx(fx + dst, tot, __ldg(sc + l) * wm, fxu);
-            else P::atomic_add(out + dst, tot, __ldg(sc + l) * wm);
+            const double cl = sc ? __ldg(sc + l) : 1.0;
+            if (fx) P::atomic_add_fx(fx + dst, tot, cl * wm, fxu);
+            else P::atomic_add(out + dst, tot, cl * wm);
         }
     } else {
         // lanes hold U.re, U.im, V.re, V.im of degree l at c = 0..3; the G/C
@@ -877,8 +1205,9 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
             else if (c == 2) { val = P::ascale(P::aadd(other, P::ascale(tot, -sgs)), h); dst = 2 * (nalm + base + l) + 1; }
             else { val = P::ascale(P::aadd(other, P::ascale(tot, sgs)), -h); dst = 2 * (nalm + base + l); }
             if (!(m == 0 && (c == 1 || c == 2))) {
-                if (fx) P::atomic_add_fx(fx + dst, val, __ldg(sc + l) * wm, fxu);
-                else P::atomic_add(out + dst, val, __ldg(sc + l) * wm);
+                const double cl = sc ? __ldg(sc + l) : 1.0;
+                if (fx) P::atomic_add_fx(fx + dst, val, cl * wm, fxu);
+                else P::atomic_add(out + dst, val, cl * wm);
             }
         }
     }
@@ -927,8 +1256,9 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
     if (!SPIN) {
         if (lane < NV && l <= lmax && !(m == 0 && c == 1)) {
             const int64_t dst = 2 * (base + l) + c;
-            if (fx) PolDF::atomic_add_fx(fx + dst, tot, __ldg(sc + l) * wm, fxu);
-            else atomicAdd(out + dst, tot * (float)(__ldg(sc + l) * wm));
+            const double cl = sc ? __ldg(sc + l) : 1.0;
+            if (fx) PolDF::atomic_add_fx(fx + dst, tot, cl * wm, fxu);
+            else atomicAdd(out + dst, tot * (float)(cl * wm));
         }
     } else {
         const float other = __shfl_xor_sync(0xffffffffu, tot, 2);  // U <-> V of the same l
@@ -940,8 +1270,9 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
             else if (c == 2) { val = 0.5f * (other - sgs * tot); dst = 2 * (nalm + base + l) + 1; }
             else { val = -0.5f * (other + sgs * tot); dst = 2 * (nalm + base + l); }
             if (!(m == 0 && (c == 1 || c == 2))) {
-                if (fx) PolDF::atomic_add_fx(fx + dst, val, __ldg(sc + l) * wm, fxu);
-                else atomicAdd(out + dst, val * (float)(__ldg(sc + l) * wm));
+                const double cl = sc ? __ldg(sc + l) : 1.0;
+                if (fx) PolDF::atomic_add_fx(fx + dst, val, cl * wm, fxu);
+                else atomicAdd(out + dst, val * (float)(cl * wm));
             }
         }
     }
@@ -971,13 +1302,13 @@ __device__ __forceinline__ void adj_block(Rings<P, RPT, SPIN> &st, const AdjIn<P
 
 // GRAD: gradient-only spin s, G alone is written (out [nalm]); the reduction
 // then has the shape of spin 0's, with the factor -1/2 in the weight.
-template <class P, int RPT, bool SPIN, bool GRAD = false>
-__global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_a,
-                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
-                                                 const double *__restrict__ scale, RingTab rt,
-                                                 typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
-                                                 int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos,
-                                                 unsigned long long *fx, const double *__restrict__ fxs)
+template <class P, int RPT, bool SPIN, bool GRAD>
+__device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ ring, const void *__restrict__ rec_a,
+                                             const void *__restrict__ rec_t, const double *__restrict__ lognorm,
+                                             const double *__restrict__ scale, const RingTab &rt,
+                                             typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
+                                             int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos,
+                                             unsigned long long *fx, const double *__restrict__ fxs, const CkTab &ck)
 {
     using A = typename P::A;
     using R = typename P::R;
@@ -995,7 +1326,7 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
         SPIN ? reinterpret_cast<const typename P::Tab *>((const typename P::TabAT *)rec_a + base)
              : (const typename P::Tab *)rec_a + base;
     const typename P::TTab *rect = SPIN ? (const typename P::TTab *)rec_t + base : nullptr;
-    const double *sc = scale + base;
+    const double *sc = P::kRestart ? nullptr : scale + base;  // restarted recursions carry lambda itself
     const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * RPT;
     const Sg sgs = (s & 1) ? Sg(-1) : Sg(1);
     R *out = reinterpret_cast<R *>(alm);
@@ -1004,25 +1335,39 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
     const double fxu = fx ? fxs[1 + m] : 0.0;  // deterministic plans: fixed-point unit of order m
 
     Rings<P, RPT, SPIN> st;
-    st.init(rt, rp0, nnorth, m, s, lognorm[m]);
     AdjIn<P, RPT, SPIN, GRAD> in;
     in.init(ring, rp0, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
-
-    {  // degree l0 (the start value): one reduction of NCOMP values
+    int l = lf;
+    bool jumped = false;
+    if constexpr (P::kRestart) {  // start at the warp's first restart: every earlier degree is negligible
+        const int kj = first_restart<RPT>(ck, m);
+        if (kj > 0) {
+            st.init_geom(rt, rp0, nnorth);
+            l = lf + kj * ck.K;  // the restart at l sets the state
+            jumped = true;
+        }
+    }
+    if (!jumped) {
+        st.init(rt, rp0, nnorth, m, s, lognorm[m]);
+        // degree l0 (the start value): one reduction of NCOMP values
         A p0[NCOMP];
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
         in.add_rt(st, true, p0);  // l0 = lf - 1
         flush<P, FSPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs, fx, fxu);
     }
-    int l = lf;
     A part[NV];
     // measured at lmax 4096: spin s 42.8 -> 41.6 ms; spin 0 (16 values per lane)
     // 17.2 -> 18.4 ms, so spin 0 keeps the transpose-reduce
-    constexpr bool kSmemFlush = std::is_same<P, PolDF>::value && FSPIN;
+    constexpr bool kSmemFlush = std::is_same<typename P::A, float>::value && FSPIN;
     extern __shared__ __align__(16) float adj_smem[];
     float *wbuf = adj_smem + (threadIdx.x >> 5) * (adj_smem_per_warp<FSPIN>() / sizeof(float));
+    const int64_t ckrow = P::kRestart ? __ldg(ck.base + m) : 0;
     for (; l + kBlk <= lmax + 1; l += kBlk) {
+        if constexpr (P::kRestart) {
+            const int dl = l - lf;
+            if (dl != 0 && (dl & (ck.K - 1)) == 0) st.restart(ck, ckrow + (int64_t)(dl / ck.K - 1) * nnorth, rp0, nnorth);
+        }
         const int reg = st.regime();
         if (reg == 1) {  // every contribution of this block is below 2^-180: recursion only
             adj_block<P, RPT, SPIN, 1, GRAD>(st, in, part, reca, rect, l);
@@ -1050,6 +1395,35 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
         }
         flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs, fx, fxu);
     }
+}
+
+template <class P, int RPT, bool SPIN, bool GRAD = false>
+__global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict__ ring, const void *__restrict__ rec_a,
+                                                 const void *__restrict__ rec_t, const double *__restrict__ lognorm,
+                                                 const double *__restrict__ scale, RingTab rt,
+                                                 typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
+                                                 int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos,
+                                                 unsigned long long *fx, const double *__restrict__ fxs)
+{
+    leg_adj_body<P, RPT, SPIN, GRAD>(ring, rec_a, rec_t, lognorm, scale, rt, alm, lmax, mmax, spin, ntheta, nnorth,
+                                     nalm, m_begin, wpos, fx, fxs, CkTab{});
+}
+
+// Restarted FP32 recursion (see k_leg_fwd32).
+template <int RPT, bool SPIN, bool GRAD = false>
+__global__ void __launch_bounds__(512) k_leg_adj32(const float2 *__restrict__ ring, const void *__restrict__ rec_s,
+                                                   const double *__restrict__ lognorm, RingTab rt,
+                                                   float2 *__restrict__ alm, int lmax, int mmax, int spin, int ntheta,
+                                                   int nnorth, int64_t nalm, int m_begin, double wpos,
+                                                   unsigned long long *fx, const double *__restrict__ fxs, CkTab ck)
+{
+    const int wr0 = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) * RPT;  // first ring of the warp
+    if (wr0 < ck.jb)
+        leg_adj_body<PolR, RPT, SPIN, GRAD>(ring, rec_s, nullptr, lognorm, nullptr, rt, alm, lmax, mmax, spin, ntheta,
+                                            nnorth, nalm, m_begin, wpos, fx, fxs, ck);
+    else
+        leg_adj_body<PolS, RPT, SPIN, GRAD>(ring, rec_s, nullptr, lognorm, nullptr, rt, alm, lmax, mmax, spin, ntheta,
+                                            nnorth, nalm, m_begin, wpos, fx, fxs, ck);
 }
 
 // ---------------------------------------------- fixed point (deterministic plans)
@@ -1156,6 +1530,134 @@ __global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, flo
     }
 }
 
+// Step table of the restarted FP32 recursion (PolS / PolR): per (m, l > l0)
+// float4 (A_l, B_l, AT_l, K_l), K_l = 1 + B_l - A_l - AT_l formed in FP64 and
+// rounded once (B_{l0+1} = 0: lambda_{l0-1} does not exist); zeros for l <= l0.
+__global__ void k_rec_tables_s(int lmax, int spin, float4 *__restrict__ out)
+{
+    const int m = blockIdx.x;
+    const int s = spin;
+    const int l0 = m > s ? m : s;
+    const int64_t base = alm_base(lmax, m);
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l > l0) {
+            const double j = l - 1, mm = m, ss = s;
+            const double den = ((j + 1) * (j + 1) - mm * mm) * ((j + 1) * (j + 1) - ss * ss);
+            const double A = (j + 1) * sqrt((2 * j + 3) * (2 * j + 1) / den);
+            const double T = j > 0 ? mm * ss / (j * (j + 1)) : 0.0;
+            const double B = l >= l0 + 2 ? rec_B(l, m, s) : 0.0;
+            const double AT = A * T;
+            v = make_float4((float)A, (float)B, (float)AT, (float)(((1.0 + B) - A) - AT));
+        }
+        out[base + l] = v;
+    }
+}
+
+// Restart values of the FP32 recursion (CkTab), from the FP64 monic recursion
+// (alpha, tau and c_l of k_rec_tables in FP64, start values and 2^(60 E)
+// scaling as PolF64); one thread per (north ring, m).  Before degree
+// lb = lf + K k (k = 1 .. ck_count) the FP32 kernels hold (lambda_{lb-2},
+// lambda_{lb-1}) in the plain form and (D_{lb-1}, lambda_{lb-1}) in Reinsch's
+// form (rings below jb); those pairs are written scaled by 2^(-60 E) in FP32
+// with E (kCkZero for a state that is identically zero).  lt[m][j]: the first
+// degree at which |lambda| (either sign of the spin) reaches 2^-40, lmax + 1
+// if none does before the last restart.
+template <bool SPIN>
+__global__ void k_ck_build(const double *__restrict__ a64, const double *__restrict__ t64,
+                           const double *__restrict__ scale, const double *__restrict__ lognorm, RingTab rt, int lmax,
+                           int spin, int nnorth, int K, int jb, const int64_t *__restrict__ ckbase,
+                           void *__restrict__ vout, void *__restrict__ eout, int *__restrict__ lt)
+{
+    const int m = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = SPIN ? spin : 0;
+    const int l0 = m > s ? m : s;
+    if (j >= nnorth) return;
+    int *ltp = lt + (int64_t)m * nnorth + j;
+    *ltp = lmax + 1;
+    if (l0 > lmax) return;
+    const int lf = l0 + 1;
+    const int nck = ck_count(lmax, lf, K);
+    if (nck == 0) return;
+    const int64_t base = alm_base(lmax, m);
+    const double x = rt.x[j];
+    PolF64::St sp, sm;
+    start_value<PolF64>(sp, m, s, s, lognorm[m], rt.lsin2[j], rt.lcos2[j]);
+    if (SPIN) start_value<PolF64>(sm, m, s, -s, lognorm[m], rt.lsin2[j], rt.lcos2[j]);
+    const bool rein = j < jb;
+    auto pair = [&](const PolF64::St &st, int l, float &w0, float &w1, short &e) {
+        if (st.w[0] == 0.0 && st.w[1] == 0.0) { w0 = 0.f; w1 = 0.f; e = (short)kCkZero; return; }
+        const double v1 = st.w[1] * scale[base + l];
+        const double v0 = st.w[0] * scale[base + l - 1];
+        w1 = (float)v1;
+        w0 = (float)(rein ? v1 - v0 : v0);
+        e = (short)max(st.E, kCkZero + 1);
+    };
+    auto big = [&](const PolF64::St &st, int l) {  // |lambda_l| >= 2^-40
+        return st.E >= -1 && ldexp(fabs(st.w[1]) * scale[base + l], kScaleBits * st.E) >= 0x1p-40;
+    };
+    int lfirst = lmax + 1;
+    if (big(sp, l0) || (SPIN && big(sm, l0))) lfirst = l0;
+    int k = 1;
+    int lck = lf + K - 1;  // last degree before the k-th restart
+    for (int l = lf; k <= nck; ++l) {
+        const double ax = a64[base + l] * x;
+        if (!SPIN) {
+            const double nv = fma(ax, sp.w[1], -sp.w[0]);
+            sp.w[0] = sp.w[1]; sp.w[1] = nv;
+            PolF64::rescale(sp, 1);
+        } else {
+            const double t = t64[base + l];
+            const double np = fma(ax + t, sp.w[1], -sp.w[0]);
+            const double nm = fma(ax - t, sm.w[1], -sm.w[0]);
+            sp.w[0] = sp.w[1]; sp.w[1] = np;
+            sm.w[0] = sm.w[1]; sm.w[1] = nm;
+            PolF64::rescale(sp, 1);
+            PolF64::rescale(sm, 1);
+        }
+        if (lfirst > lmax && (big(sp, l) || (SPIN && big(sm, l)))) lfirst = l;
+        if (l == lck) {
+            const int64_t idx = ckbase[m] + (int64_t)(k - 1) * nnorth + j;
+            if (!SPIN) {
+                float2 v;
+                short e;
+                pair(sp, l, v.x, v.y, e);
+                reinterpret_cast<float2 *>(vout)[idx] = v;
+                reinterpret_cast<short *>(eout)[idx] = e;
+            } else {
+                float4 v;
+                short2 e;
+                pair(sp, l, v.x, v.y, e.x);
+                pair(sm, l, v.z, v.w, e.y);
+                reinterpret_cast<float4 *>(vout)[idx] = v;
+                reinterpret_cast<short2 *>(eout)[idx] = e;
+            }
+            ++k;
+            lck += K;
+        }
+    }
+    *ltp = lfirst;
+}
+
+// First restart of every 32-ring group and order: the largest k <= ck_count
+// with lf + K k <= min over the group's rings of lt (so every degree before
+// the restart is below 2^-40 on all of them).
+__global__ void k_ck_start(const int *__restrict__ lt, int lmax, int mmax, int spin, int nnorth, int K, int ngrp,
+                           short *__restrict__ kstart)
+{
+    const int m = blockIdx.x;
+    const int l0 = m > spin ? m : spin;
+    const int lf = l0 + 1;
+    const int nck = l0 > lmax ? 0 : ck_count(lmax, lf, K);
+    for (int g = threadIdx.x; g < ngrp; g += blockDim.x) {
+        int lmin = lmax + 1;
+        for (int j = 32 * g; j < 32 * g + 32 && j < nnorth; ++j) lmin = min(lmin, lt[(int64_t)m * nnorth + j]);
+        const int k = lmin > lf ? (lmin - lf) / K : 0;
+        kstart[(int64_t)m * ngrp + g] = (short)min(k, nck);
+    }
+}
+
 // Forward coefficients of one call: spin 0 c_l a_lm; spin s c_l (G + iC) and
 // c_l (-1)^s (conj G + i conj C) (m = 0: imaginary parts of a, G, C dropped),
 // all multiplied by wpos for m > 0; gradient-only plans (grad, alm holds G
@@ -1189,7 +1691,8 @@ __global__ void k_coef_prep(const Tin *__restrict__ alm, const double *__restric
     const bool hi = m >= m_split;
     for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
         const int64_t i = base + l;
-        const double c = scale[i] * wm;
+        // plans with restarted FP32 recursions carry lambda itself (no monic scale)
+        const double c = (scale ? scale[i] : (l >= (m > spin ? m : spin) ? 1.0 : 0.0)) * wm;
         const Tin gv = alm[i];
         const double gr = gv.x, gi = m == 0 ? 0.0 : (double)gv.y;
         if (!spin) {
@@ -1256,6 +1759,90 @@ cudaError_t adj_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, c
 {
     if (sh.rpt == 1) return adj_launch<P, 1, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
     return adj_launch<P, 2, SPIN, GRAD>(p, sh, ring, ta, tt, alm, m_begin, m_end, st, wpos, fx);
+}
+
+// Restarted FP32 recursion (plans with p.rst): one launch per direction
+template <int RPT, bool SPIN, int NM = 1, bool GRAD = false>
+cudaError_t fwd32_launch(const Plan &p, const Plan::LegShape &sh, const void *coef, void *ring, int m_begin,
+                         int m_end, cudaStream_t st)
+{
+    if (m_end <= m_begin) return cudaSuccess;
+    dim3 grid(sh.chunks, m_end - m_begin);
+    dim3 block(sh.warps * 32);
+    k_leg_fwd32<RPT, SPIN, NM, GRAD><<<grid, block, 0, st>>>(coef, p.rec_s, p.lognorm, p.rings, (float2 *)ring, p.lmax,
+                                                           p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin,
+                                                           (int64_t)p.ncol * p.ntheta, p.ck);
+    return cudaGetLastError();
+}
+
+template <int RPT, bool SPIN, bool GRAD = false>
+cudaError_t adj32_launch(const Plan &p, const Plan::LegShape &sh, const void *ring, void *alm, int m_begin, int m_end,
+                         cudaStream_t st, double wpos, void *fx)
+{
+    if (m_end <= m_begin) return cudaSuccess;
+    dim3 grid(sh.chunks, m_end - m_begin);
+    dim3 block(sh.warps * 32);
+    k_leg_adj32<RPT, SPIN, GRAD><<<grid, block, adj_smem_bytes<PolDF, SPIN, GRAD>(sh.warps), st>>>(
+        (const float2 *)ring, p.rec_s, p.lognorm, p.rings, (float2 *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
+        p.nalm, m_begin, wpos, (unsigned long long *)fx, p.fx_scale, p.ck);
+    return cudaGetLastError();
+}
+
+// rings per thread 1, 2 or 4 (the warp-uniform table loads are shared by the rings of a thread)
+template <bool SPIN, int NM = 1, bool GRAD = false>
+cudaError_t fwd32_rpt(const Plan &p, const Plan::LegShape &sh, const void *coef, void *ring, int m_begin, int m_end,
+                      cudaStream_t st)
+{
+    if (sh.rpt == 1) return fwd32_launch<1, SPIN, NM, GRAD>(p, sh, coef, ring, m_begin, m_end, st);
+    if (sh.rpt == 2) return fwd32_launch<2, SPIN, NM, GRAD>(p, sh, coef, ring, m_begin, m_end, st);
+    return fwd32_launch<4, SPIN, NM, GRAD>(p, sh, coef, ring, m_begin, m_end, st);
+}
+
+cudaError_t fwd32_spin(const Plan &p, const Plan::LegShape &sh, const void *coef, void *ring, int m_begin, int m_end,
+                       cudaStream_t st)
+{
+    if (!p.spin) return fwd32_rpt<false>(p, sh, coef, ring, m_begin, m_end, st);
+    if (p.grad) return fwd32_rpt<true, 1, true>(p, sh, coef, ring, m_begin, m_end, st);
+    return fwd32_rpt<true>(p, sh, coef, ring, m_begin, m_end, st);
+}
+
+template <bool SPIN, bool GRAD = false>
+cudaError_t adj32_rpt(const Plan &p, const Plan::LegShape &sh, const void *ring, void *alm, int m_begin, int m_end,
+                      cudaStream_t st, double wpos, void *fx)
+{
+    if (sh.rpt == 1) return adj32_launch<1, SPIN, GRAD>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+    if (sh.rpt == 2) return adj32_launch<2, SPIN, GRAD>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+    return adj32_launch<4, SPIN, GRAD>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+}
+
+cudaError_t adj32_spin(const Plan &p, const Plan::LegShape &sh, const void *ring, void *alm, int m_begin, int m_end,
+                       cudaStream_t st, double wpos, void *fx)
+{
+    if (!p.spin) return adj32_rpt<false>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+    if (p.grad) return adj32_rpt<true, true>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+    return adj32_rpt<true>(p, sh, ring, alm, m_begin, m_end, st, wpos, fx);
+}
+
+template <int RPT> const void *kernel_of32_r(bool spin, bool grad, bool adjoint, int nm)
+{
+    if (adjoint) {
+        if (spin && grad) return (const void *)k_leg_adj32<RPT, true, true>;
+        if (spin) return (const void *)k_leg_adj32<RPT, true>;
+        return (const void *)k_leg_adj32<RPT, false>;
+    }
+    if (nm == 2) return spin ? (const void *)k_leg_fwd32<RPT, true, 2> : (const void *)k_leg_fwd32<RPT, false, 2>;
+    if (nm == 4) return spin ? (const void *)k_leg_fwd32<RPT, true, 4> : (const void *)k_leg_fwd32<RPT, false, 4>;
+    if (spin && grad) return (const void *)k_leg_fwd32<RPT, true, 1, true>;
+    if (spin) return (const void *)k_leg_fwd32<RPT, true>;
+    return (const void *)k_leg_fwd32<RPT, false>;
+}
+
+// Kernel entry of a restarted-FP32 variant (nm > 1: forward sharing the recursion among nm maps)
+const void *kernel_of32(bool spin, bool grad, int rpt, bool adjoint, int nm)
+{
+    if (rpt == 4) return kernel_of32_r<4>(spin, grad, adjoint, nm);
+    if (rpt == 2) return kernel_of32_r<2>(spin, grad, adjoint, nm);
+    return kernel_of32_r<1>(spin, grad, adjoint, nm);
 }
 
 template <class P>
@@ -1740,7 +2327,8 @@ const void *kernel_of_batch(bool spin, int rpt, int nm)
 // the fewest idle ring slots.  nm > 1: the FP32 forward kernel for nm maps.
 Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int nm)
 {
-    const void *fn = (nm > 1)            ? kernel_of_batch(p.spin != 0, rpt, nm)
+    const void *fn = (p.rst && p.prec == LENS_FP32) ? kernel_of32(p.spin != 0, p.grad, rpt, adjoint, nm)
+                     : (nm > 1)            ? kernel_of_batch(p.spin != 0, rpt, nm)
                      : p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, p.grad, rpt, adjoint)
                      : dd                  ? kernel_of<PolDD>(p.spin != 0, p.grad, rpt, adjoint)
                                            : kernel_of<PolF64>(p.spin != 0, p.grad, rpt, adjoint);
@@ -1766,6 +2354,31 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
     return best;
 }
 
+cudaError_t launch_rec_tables_s(Plan &p)
+{
+    k_rec_tables_s<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, (float4 *)p.rec_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ck_build(Plan &p, double *a64, double *t64, void *v_out, void *e_out, int *lt, short *kstart)
+{
+    // FP64 alpha / tau / c_l of the monic recursion (c_l rewritten with the same values)
+    k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, nullptr, nullptr, a64,
+                                                   p.spin ? t64 : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 g((p.nnorth + 127) / 128, p.mmax + 1);
+    if (p.spin)
+        k_ck_build<true><<<g, 128, 0, p.stream>>>(a64, t64, p.scale, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
+                                                  p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt);
+    else
+        k_ck_build<false><<<g, 128, 0, p.stream>>>(a64, nullptr, p.scale, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
+                                                   p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_ck_start<<<p.mmax + 1, 128, 0, p.stream>>>(lt, p.lmax, p.mmax, p.spin, p.nnorth, p.ck.K, p.ck.ngrp, kstart);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rec_tables(Plan &p)
 {
     if (p.prec == LENS_FP32)
@@ -1782,8 +2395,12 @@ cudaError_t launch_rec_tables(Plan &p)
 //   FP32 spin 2: fwd 47.4 / 73.4 / 158 and adj 52.4 / 75.6 / 193
 //   FP64 spin 0: fwd 246 / 252 / 295 and adj 258 / 236 / 262
 //   FP64 spin 2: fwd 760 / 700 / 790 and adj 851 / 801 / 916
-int legendre_rpt(int prec, int spin, bool adjoint)
+// Restarted FP32 recursion (FP32 state, rst), lmax 4096 (ms per launch, fwd / adj):
+//   spin 0: 6.9 / 8.7, 4.8 / 5.9, 4.5 / 5.7 for RPT 1 / 2 / 4
+//   spin 2: 12.3 / 17.1, 14.0 / 15.9, 15.8 / 20.5
+int legendre_rpt(int prec, int spin, bool adjoint, bool rst)
 {
+    if (prec == LENS_FP32 && rst) return spin ? (adjoint ? 2 : 1) : 4;
     if (prec == LENS_FP32) return spin ? 1 : 2;
     return spin ? 2 : (adjoint ? 2 : 1);
 }
@@ -1791,7 +2408,10 @@ int legendre_rpt(int prec, int spin, bool adjoint)
 // df32 part of FP64 plans: twice the accumulator words of the FP32 plans
 int legendre_rpt_dd(int spin, bool adjoint) { return (spin || adjoint) ? 1 : 2; }
 
-bool legendre_rpt_supported(int, int, bool, int rpt) { return rpt == 1 || rpt == 2; }
+bool legendre_rpt_supported(int prec, int, bool, int rpt, bool rst)
+{
+    return rpt == 1 || rpt == 2 || (rpt == 4 && prec == LENS_FP32 && rst);
+}
 
 cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cudaStream_t st, double wpos)
 {
@@ -1802,8 +2422,8 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     if (e != cudaSuccess) return e;
     const dim3 g(4, p.mmax + 1);
     if (p.prec == LENS_FP32) {
-        k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef, p.lmax, p.spin,
-                                                               p.nalm, p.mmax + 1, wpos, p.grad);
+        k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.rst ? nullptr : p.scale, p.coef,
+                                                               p.lmax, p.spin, p.nalm, p.mmax + 1, wpos, p.grad);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (p.tab) {
             const dim3 tg(p.tab_fchunks, p.mmax + 1);
@@ -1819,6 +2439,7 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
             else args(k_tab_fwd<true, false>);
             return cudaGetLastError();
         }
+        if (p.rst) return fwd32_spin(p, p.leg_f, p.coef, ring, 0, p.mmax + 1, st);
         return fwd_spin<PolDF>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st);
     }
     k_coef_prep<double2, double2, float4><<<g, 256, 0, st>>>((const double2 *)alm, p.scale, p.coef, p.lmax, p.spin,
@@ -1839,7 +2460,8 @@ cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring
     const dim3 g(4, p.mmax + 1);
     for (int b = 0; b < nm; ++b) {
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm + (size_t)b * ncomp * p.nalm,
-                                                               p.scale, (float2 *)coef + (size_t)b * ncomp * p.nalm,
+                                                               p.rst ? nullptr : p.scale,
+                                                               (float2 *)coef + (size_t)b * ncomp * p.nalm,
                                                                p.lmax, p.spin, p.nalm, p.mmax + 1, wpos, false);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -1864,6 +2486,13 @@ cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring
         return cudaGetLastError();
     }
     const Plan::LegShape &sh = p.leg_fb[nm == 2 ? 0 : 1];
+    if (p.rst) {
+        if (p.spin)
+            return nm == 2 ? fwd32_rpt<true, 2>(p, sh, coef, ring, 0, p.mmax + 1, st)
+                           : fwd32_rpt<true, 4>(p, sh, coef, ring, 0, p.mmax + 1, st);
+        return nm == 2 ? fwd32_rpt<false, 2>(p, sh, coef, ring, 0, p.mmax + 1, st)
+                       : fwd32_rpt<false, 4>(p, sh, coef, ring, 0, p.mmax + 1, st);
+    }
     if (p.spin) {
         if (sh.rpt == 1)
             return nm == 2 ? fwd_launch<PolDF, 1, true, 2>(p, sh, coef, p.rec_a, p.rec_t, ring, 0, p.mmax + 1, st)
@@ -1910,7 +2539,8 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
         else args(k_tab_adj<true, false>, warps * tab_smem_per_warp<true, true>());
         e = cudaGetLastError();
     } else if (f32) {
-        e = adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos, fx);
+        e = p.rst ? adj32_spin(p, p.leg_a, ring, alm, 0, p.mmax + 1, st, wpos, fx)
+                  : adj_spin<PolDF>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.mmax + 1, st, wpos, fx);
     } else {
         e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos, fx);
         if (e == cudaSuccess)

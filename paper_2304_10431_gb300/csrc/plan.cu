@@ -17,9 +17,9 @@
 #include "internal.h"
 
 namespace gsl {
-int legendre_rpt(int prec, int spin, bool adjoint);
+int legendre_rpt(int prec, int spin, bool adjoint, bool rst);
 int legendre_rpt_dd(int spin, bool adjoint);
-bool legendre_rpt_supported(int prec, int spin, bool adjoint, int rpt);
+bool legendre_rpt_supported(int prec, int spin, bool adjoint, int rpt, bool rst);
 }
 
 using namespace gsl;
@@ -454,13 +454,40 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         else if (epsilon >= 5e-11) p->m_df = std::min(256, mmax + 1);
         else p->m_df = mmax + 1;
     }
+    // ---- FP32 plans: restarted FP32 recursion (legendre.cu, PolS / PolR) or df32
+    {
+        const int want = prm ? prm->legendre_restart : 0;
+        if (want < -1 || (want > 0 && (want < 8 || want > 4096 || (want & (want - 1)) != 0)))
+            return bail(LENS_ERR_INVALID, "legendre_restart must be -1, 0 or a power of two in [8, 4096]");
+        if (prec == LENS_FP32 && !p->tab && want != -1 && (want > 0 || epsilon >= 1e-5)) {
+            int K = want > 0 ? want : 64;
+            const size_t esz_ck = spin ? 16 : 8;
+            auto bytes_for = [&](int k) {
+                size_t n = 0;
+                for (int m = 0; m <= mmax; ++m) n += (size_t)ck_count(lmax, std::max(m, spin) + 1, k);
+                return n * p->nnorth * esz_ck;
+            };
+            size_t b = bytes_for(K);
+            while (want == 0 && b > ((size_t)16 << 30) && K < 4096) b = bytes_for(K *= 2);
+            p->rst = true;
+            p->ck.K = K;
+            p->ck_bytes = b;
+            // Reinsch's form on the rings with cos theta >= 0.7, rounded up to a multiple of 128 rings
+            // (beyond 0.7 down to cos theta = 0.5 it is still the more accurate form).  The kernels
+            // choose the form per warp (32 x 1, 2 or 4 rings) and the restart values were written for
+            // the form of each ring, so no warp of any rings-per-thread setting may straddle jb.
+            const double jr = acos(0.7) / kPi * (nt - 1);
+            p->ck.jb = (int)std::ceil(jr / 128.0) * 128;
+        }
+    }
     // ---- Legendre launch shapes: RPT rings per thread; warps per CTA chosen
     // for occupancy of the kernel variant (legendre_shape)
     for (int adj = 0; adj < 2; ++adj) {
         const int want = prm ? (adj ? prm->legendre_rpt_adj : prm->legendre_rpt_fwd) : 0;
-        if (want && !legendre_rpt_supported(prec, spin, adj != 0, want))
+        if (want && !legendre_rpt_supported(prec, spin, adj != 0, want, p->rst))
             return bail(LENS_ERR_INVALID, "unsupported Legendre rings-per-thread setting");
-        (adj ? p->leg_a : p->leg_f) = legendre_shape(*p, adj != 0, false, want ? want : legendre_rpt(prec, spin, adj != 0));
+        (adj ? p->leg_a : p->leg_f) =
+            legendre_shape(*p, adj != 0, false, want ? want : legendre_rpt(prec, spin, adj != 0, p->rst));
         if (prec == LENS_FP64)
             (adj ? p->leg_ad : p->leg_fd) = legendre_shape(*p, adj != 0, true, legendre_rpt_dd(spin, adj != 0));
     }
@@ -479,15 +506,47 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if (spin && prec == LENS_FP64 && (e = B.alloc(&p->rec_t, (size_t)p->nalm * 8, false)) != cudaSuccess)
         return bailc(e, "alloc rec_t");
     if ((e = B.alloc((void **)&p->scale, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc scale");
+    if (p->rst) {
+        if ((e = B.alloc(&p->rec_s, (size_t)p->nalm * 16, false)) != cudaSuccess) return bailc(e, "alloc rec_s");
+        std::vector<int64_t> cb(mmax + 1);
+        int64_t off = 0;
+        for (int m = 0; m <= mmax; ++m) {
+            cb[m] = off;
+            off += (int64_t)ck_count(lmax, std::max(m, spin) + 1, p->ck.K) * p->nnorth;
+        }
+        void *d = nullptr;
+        if ((e = B.upload(&d, cb)) != cudaSuccess) return bailc(e, "upload restart offsets");
+        p->ck.base = (const int64_t *)d;
+        p->ck.ngrp = (p->nnorth + 31) / 32;
+        if ((e = B.alloc(&d, sizeof(short) * (size_t)(mmax + 1) * p->ck.ngrp, false)) != cudaSuccess)
+            return bailc(e, "alloc restart starts");
+        p->ck.kstart = (const short *)d;
+        if (p->ck_bytes > 0) {
+            // values (8 / 16 bytes) and exponents (2 / 4 bytes) per entry
+            const size_t ebytes = p->ck_bytes / 4;
+            void *dv = nullptr, *de = nullptr;
+            if ((e = B.alloc(&dv, p->ck_bytes, false)) != cudaSuccess || (e = B.alloc(&de, ebytes, false)) != cudaSuccess) {
+                if (e == cudaErrorMemoryAllocation) {
+                    cudaGetLastError();
+                    return bail(LENS_ERR_NOMEM, "Legendre restart values: " + std::to_string((p->ck_bytes + ebytes) >> 20) +
+                                                    " MiB not available (legendre_restart = -1 runs without them)");
+                }
+                return bailc(e, "alloc restart values");
+            }
+            p->ck.v = dv;
+            p->ck.e = de;
+            p->ck_bytes += ebytes;
+        }
+    }
     if (prec == LENS_FP64 && p->m_df <= mmax) {
         if ((e = B.alloc(&p->rec_a_df, (size_t)p->nalm * (spin ? 16 : 8), false)) != cudaSuccess)
             return bailc(e, "alloc rec_a_df");
     }
     if ((e = B.alloc(&p->coef, (size_t)p->nalm * esz * ncomp, true)) != cudaSuccess) return bailc(e, "alloc coef");
-    if ((e = B.alloc(&p->ring, esz * (size_t)p->ncol * p->ntheta, true)) != cudaSuccess) return bailc(e, "alloc ring");
-    if ((e = B.alloc(&p->X, esz * (size_t)p->R * p->ncol, true)) != cudaSuccess) return bailc(e, "alloc X");
-    if ((e = B.alloc(&p->grid, (esz / 2) * ncomp * (size_t)p->R * p->pitch, true)) != cudaSuccess)
-        return bailc(e, "alloc grid");
+    const ScratchSizes scr = plan_scratch_sizes(*p);
+    if ((e = B.alloc(&p->ring, scr.ring, true)) != cudaSuccess) return bailc(e, "alloc ring");
+    if ((e = B.alloc(&p->X, scr.X, true)) != cudaSuccess) return bailc(e, "alloc X");
+    if ((e = B.alloc(&p->grid, scr.grid, true)) != cudaSuccess) return bailc(e, "alloc grid");
     if (p->det) {  // fixed-point sums; the small scalars share one allocation
         if ((e = B.alloc((void **)&p->fx_scale, sizeof(double) * ((size_t)mmax + 2), false)) != cudaSuccess ||
             (e = B.alloc((void **)&p->fx_maxbits, 64, false)) != cudaSuccess)
@@ -553,12 +612,15 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
 
         std::vector<double> x(p->nnorth), ls(p->nnorth), lc(p->nnorth);
         std::vector<float2> xdf(p->nnorth);
+        std::vector<float> y1(p->nnorth);
         for (int j = 0; j < p->nnorth; ++j) {
             const double th = kPi * j / (nt - 1);
             x[j] = cos(th);
             if (2 * j == nt - 1) x[j] = 0.0;
             const float h = (float)x[j];
             xdf[j] = make_float2(h, (float)(x[j] - (double)h));
+            const double sh = sin(0.5 * th);
+            y1[j] = (float)(2.0 * sh * sh);
             ls[j] = j == 0 ? -INFINITY : log2(sin(0.5 * th));
             lc[j] = log2(cos(0.5 * th));
         }
@@ -570,6 +632,8 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         p->rings.lsin2 = (const double *)d;
         if ((e = B.upload(&d, lc)) != cudaSuccess) return bailc(e, "upload rings");
         p->rings.lcos2 = (const double *)d;
+        if ((e = B.upload(&d, y1)) != cudaSuccess) return bailc(e, "upload rings");
+        p->rings.y1 = (const float *)d;
 
         Quad q(std::max(64, 4 * p->W + 40));
         std::vector<double> w1(2 * lmax + 1), w2(p->ncol);
@@ -596,6 +660,40 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if ((e = B.fft(p->fN2, p->N2)) != cudaSuccess) return bailc(e, "fft tables");
 
     if ((e = launch_rec_tables(*p)) != cudaSuccess) return bailc(e, "recursion tables");
+    if (p->rst) {  // step table, then restart values from the FP64 recursion (temporary FP64 tables)
+        if ((e = launch_rec_tables_s(*p)) != cudaSuccess) return bailc(e, "restart step table");
+        if (p->ck_bytes > 0) {
+            // temporaries: FP64 alpha and tau [nalm] each, first significant degree [mmax + 1][nnorth]
+            const size_t tb = (size_t)p->nalm * 16 + sizeof(int) * (size_t)(mmax + 1) * p->nnorth;
+            double *tmp = nullptr;
+            if ((e = cudaMalloc((void **)&tmp, tb)) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(LENS_ERR_NOMEM, "Legendre restart values: temporary tables not available");
+            }
+            e = launch_ck_build(*p, tmp, tmp + p->nalm, const_cast<void *>(p->ck.v), const_cast<void *>(p->ck.e),
+                                reinterpret_cast<int *>(tmp + 2 * p->nalm), const_cast<short *>(p->ck.kstart));
+            if (e == cudaSuccess) {  // non-negligible triples (the Legendre steps' algorithmic work)
+                std::vector<int> lt((size_t)(mmax + 1) * p->nnorth);
+                e = cudaMemcpyAsync(lt.data(), tmp + 2 * p->nalm, sizeof(int) * lt.size(), cudaMemcpyDeviceToHost,
+                                    p->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+                if (e == cudaSuccess) {
+                    int64_t n = 0;
+                    for (int m = 0; m <= mmax; ++m) {
+                        const int l0 = std::max(m, spin);
+                        for (int j = 0; j < p->nnorth; ++j)
+                            n += std::max(0, lmax + 1 - std::max(lt[(size_t)m * p->nnorth + j], l0));
+                    }
+                    p->leg_triples = n;
+                }
+            }
+            cudaFree(tmp);
+            if (e != cudaSuccess) return bailc(e, "restart values");
+        } else if ((e = cudaMemsetAsync(const_cast<short *>(p->ck.kstart), 0,
+                                        sizeof(short) * (size_t)(mmax + 1) * p->ck.ngrp, p->stream)) != cudaSuccess) {
+            return bailc(e, "restart starts");
+        }
+    }
     if (p->tab) {
         const int rc = build_legendre_tables(*p, B);
         if (rc != LENS_OK) {
@@ -636,6 +734,10 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
     info->flags = (p->grad ? (unsigned)LENS_GRAD_ONLY : 0u) | (p->det ? (unsigned)LENS_DETERMINISTIC : 0u);
     info->alm_ncomp = p->alm_ncomp();
     info->legendre_table_bytes = p->tab_bytes;
+    info->legendre_restart = p->rst ? p->ck.K : 0;
+    info->restart_bytes = p->ck_bytes;
+    info->legendre_df32_mmin = p->prec == LENS_FP64 ? p->m_df : 0;
+    info->legendre_triples = p->leg_triples;
     return LENS_OK;
 }
 

@@ -14,7 +14,10 @@
 // made with that device current; that first call should come before any
 // stream capture.  All calls share the array and it keeps the contents of the
 // last call: calls that overlap on the GPU (different streams, or several
-// host threads) race on it.
+// host threads) race on it.  A call also writes the plan's own prepared
+// coefficients and status flags (allocated with the plan), as every
+// transform on that plan does, so it must not overlap another call on the
+// same plan either.
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -42,10 +45,8 @@ extern "C" int lens_synthesis_static(lens_plan pl, const void *alm_d, void *map_
     if (!pl || !alm_d || (!map_d && reinterpret_cast<const Plan *>(pl)->npts > 0))
         return record_failure(LENS_ERR_INVALID, "lens_synthesis_static: NULL argument");
     const Plan &p = *reinterpret_cast<const Plan *>(pl);
-    const size_t esz = p.prec == LENS_FP32 ? 8 : 16;
-    const size_t ring_b = esz * (size_t)p.ncol * p.ntheta;
-    const size_t x_b = esz * (size_t)p.R * p.ncol;
-    const size_t grid_b = (esz / 2) * (p.spin ? 2 : 1) * (size_t)p.R * p.pitch;
+    const ScratchSizes scr = plan_scratch_sizes(p);  // the plan builder's own workspace sizes
+    const size_t ring_b = scr.ring, x_b = scr.X, grid_b = scr.grid;
     const size_t need = align256(ring_b) + align256(x_b) + align256(grid_b);
     if (need > kStaticScratchBytes) {
         char msg[256];
@@ -54,14 +55,12 @@ extern "C" int lens_synthesis_static(lens_plan pl, const void *alm_d, void *map_
                  "use lens_synthesis", need, kStaticScratchBytes);
         return record_failure(LENS_ERR_UNSUPPORTED, msg);
     }
+    if (p.device < 0 || p.device >= kMaxDevices)
+        return record_failure(LENS_ERR_UNSUPPORTED, "lens_synthesis_static: device index out of range");
     int dev0 = -1;
     cudaGetDevice(&dev0);
     if (dev0 != p.device) cudaSetDevice(p.device);
     void *base = nullptr;
-    if (p.device < 0 || p.device >= kMaxDevices) {
-        if (dev0 != p.device) cudaSetDevice(dev0);
-        return record_failure(LENS_ERR_UNSUPPORTED, "lens_synthesis_static: device index out of range");
-    }
     {
         std::lock_guard<std::mutex> lk(g_scratch_mutex);
         if (!g_scratch_addr[p.device]) {

@@ -411,7 +411,8 @@ def test_legendre_tables_match_recursion(spin, grad, det):
     th, ph, chi = W.random_points(n, 410 + spin)
     kw = dict(spin=spin, epsilon=1e-5, precision="fp32", grad_only=grad, deterministic=det, device=DEV)
     tab = LensPlan(L, th, ph, chi if spin else None, legendre_tables=True, **kw)
-    rec = LensPlan(L, th, ph, chi if spin else None, **kw)
+    # the tables hold the double-float recursion's values: compare with that recursion
+    rec = LensPlan(L, th, ph, chi if spin else None, legendre_restart=-1, **kw)
     inf = tab.info()
     nnp = (inf["ntheta"] + 1) // 2
     dense = ((nnp + 3) // 4 * 4) * tab.nalm * (8 if spin else 4)

@@ -26,13 +26,18 @@ def _static(plan, alm, out):
     return lib.lens_synthesis_static(plan.handle, alm.data_ptr(), out.data_ptr(), st)
 
 
-@pytest.mark.parametrize("spin,prec,tol", [(0, "fp32", 1e-6), (2, "fp32", 1e-6), (0, "fp64", 1e-13), (2, "fp64", 1e-13)])
-def test_static_scratch_matches_lens_synthesis(spin, prec, tol):
+@pytest.mark.parametrize("spin,prec,tol,tables", [(0, "fp32", 1e-6, False), (2, "fp32", 1e-6, False),
+                                                  (0, "fp32", 1e-6, True), (2, "fp32", 1e-6, True),
+                                                  (0, "fp64", 1e-13, False), (2, "fp64", 1e-13, False)])
+def test_static_scratch_matches_lens_synthesis(spin, prec, tol, tables):
+    # tables: FP32 plans holding precomputed Legendre values, whose synthesis reads them instead of
+    # running the recursion (a different kernel inside the same entry point)
     dev = torch.device("cuda:0")
     L = 96
     th, ph, chi = W.random_points(30000, 77)
     plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-5 if prec == "fp32" else 1e-10, precision=prec,
-                    device=dev)
+                    legendre_tables=tables, device=dev)
+    assert plan.info()["legendre_table_bytes"] > 0 if tables else plan.info()["legendre_table_bytes"] == 0
     nc = 1 if spin == 0 else 2
     for call, seed in enumerate((500, 501)):  # two calls in a row, different inputs
         a = np.stack([W.draw_alm(W.cmb_cl(L, 70.0), L, seed + 10 * k, spin=spin) for k in range(nc)])
