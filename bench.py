@@ -319,7 +319,9 @@ def run_gpu(args):
     # FMA rates of the CUDA-core pipes, measured here (the Legendre recursion's roofline denominator)
     clk = ClockSampler(local)
     clk.start()
-    fma32, fma64 = measure_fma_peak("fp32"), measure_fma_peak("fp64")
+    time.sleep(0.5)  # the sampler's first lines
+    fma32 = max(measure_fma_peak("fp32") for _ in range(3))
+    fma64 = max(measure_fma_peak("fp64") for _ in range(2))
     fma_clocks = clk.stop()
     peaks = {"hbm_gbs": float(mp.get("hbm_gbs", HBM_PEAK_FALLBACK)),
              "hbm_note": "HBM copy bandwidth (MEASURED_PEAKS.json, %s)" % peak_src,

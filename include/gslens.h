@@ -220,6 +220,21 @@ int lens_selftest_bounded_wait(void *stream);
 int lens_plan_set_grouping(lens_plan p, int on);
 
 /*
+ * Tensor-core Legendre synthesis (no counterpart in the paper, which runs one
+ * map at a time on CPUs).  For spin-0 FP32 plans that run the restarted FP32
+ * recursion (lens_plan_params.legendre_restart), lens_synthesis with 16 or more
+ * maps computes the Legendre step of up to 64 maps at a time as a dense
+ * contraction (Legendre values x coefficients per order m) on the tensor cores
+ * (tcgen05, TF32 operands split into high and low parts: three products per
+ * term, FP32 accumulation), then the Fourier stages and the interpolation per
+ * map.  The first such call allocates its workspace (ring coefficients of 64
+ * maps and the coefficient tiles: 18 GB at lmax 4096); inside a stream capture,
+ * or if the allocation fails, the maps run on the CUDA-core paths instead.
+ * on = 0 turns the tensor-core path off for this plan (default on).
+ */
+int lens_plan_set_tensor_cores(lens_plan p, int on);
+
+/*
  * Adjoint lensing (Sect. 2 Eq. "adjoint" and its spin-s form; Sect. 3 adjoint
  * steps NUFFT type 1, FFT, undoubling, adjoint synthesis).
  *   map_d  device [nmaps][ncomp][npoints] real

@@ -121,6 +121,11 @@ class LensPlan:
         """Raise LensError (LENS_ERR_TIMEOUT) if a device-side wait of an earlier call gave up."""
         _native.check(_native.load().lens_plan_status(self._h, _stream_handle(stream)))
 
+    def set_tensor_cores(self, on: bool):
+        """Spin-0 FP32 plans (restarted recursion): synthesis of 16 or more maps per call runs the
+        Legendre step on the tensor cores (default on)."""
+        _native.check(_native.load().lens_plan_set_tensor_cores(self._h, 1 if on else 0))
+
     def set_grouping(self, on: bool):
         """FP32 plans: synthesise several maps per call with a shared Legendre
         recursion (default on); off runs every map alone."""

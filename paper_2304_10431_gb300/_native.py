@@ -20,6 +20,7 @@ EXPORTS = {
     "lens_plan_destroy": (_i32, [_vp]),
     "lens_plan_info": (_i32, [_vp, _vp]),
     "lens_plan_set_grouping": (_i32, [_vp, _i32]),
+    "lens_plan_set_tensor_cores": (_i32, [_vp, _i32]),
     "lens_plan_status": (_i32, [_vp, _vp]),
     "lens_torus_coefficients": (_i32, [_vp, _vp, _vp, _vp]),
     "lens_selftest_bounded_wait": (_i32, [_vp]),

@@ -100,6 +100,11 @@ struct Plan {
     CkTab ck;
     size_t ck_bytes = 0;
     int64_t leg_triples = 0;  // non-negligible (ring pair, l, m) triples (restarted plans)
+    // tensor-core batched synthesis (spin-0 restarted plans, 16 or more maps per call):
+    // ring coefficients of up to 64 maps, prepared coefficient tiles, chunk offsets per m
+    bool tc_on = true;
+    void *tc_ring = nullptr, *tc_coef = nullptr;
+    int64_t *tc_cbase = nullptr;
 
     // tables (device)
     // monic-form recursion coefficients per alm index: alpha and (spin s) tau,
@@ -187,6 +192,14 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
 // one recursion; ring and coef hold nm maps' ring / prepared coefficients
 cudaError_t launch_legendre_fwd_batch(const Plan &p, const void *alm, void *ring, void *coef, int nm, cudaStream_t st,
                                       double wpos);
+// Tensor-core Legendre synthesis of nm <= nb maps (nb = 16, 32 or 64; spin-0 FP32
+// plans with the restarted recursion): prepares the coefficient tiles of the
+// call in coefB (tc_coef_floats(nb, total chunks) floats, chunk offsets per m
+// in cbase) and writes nm maps' ring coefficients (map stride ncol ntheta).
+int64_t tc_chunks(int lmax, int m);
+size_t tc_coef_floats(int nb, int64_t chunks);
+cudaError_t launch_legendre_fwd_tc(const Plan &p, const void *alm, int nm, void *ring, void *coefB,
+                                   const int64_t *cbase, int nb, cudaStream_t st);
 cudaError_t launch_theta_fwd(const Plan &p, const void *ring, void *X, cudaStream_t st);
 cudaError_t launch_theta_adj(const Plan &p, const void *X, void *ring, cudaStream_t st);
 cudaError_t launch_phi_fwd(const Plan &p, const void *X, void *grid, cudaStream_t st);
