@@ -75,6 +75,9 @@ def parse():
                     help="headline FP32 plans read plan-time Legendre tables instead of running the recursion")
     ap.add_argument("--no-lmax5120", action="store_true",
                     help="skip the lmax 5120 workload (paper's Fig. 2 configuration)")
+    ap.add_argument("--tc-maps", default="32,64",
+                    help="batched T synthesis with the tensor-core Legendre step: comma list of map counts "
+                         "('' to skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -479,7 +482,55 @@ def run_gpu(args):
                "ms_min": round(float(np.min(times)), 3), "ms_max": round(float(np.max(times)), 3),
                "ms_all": [round(t, 2) for t in times]}
     del b
-    pT.close(); pP.close()
+    pP.close()
+    torch.cuda.empty_cache()
+
+    # ---------------- many T maps of the same geometry: Legendre step on the tensor cores
+    tc = None
+    if args.tc_maps and not tables:
+        tc = {"what": "synthesis of nm spin-0 maps in one lens_synthesis call (T plan of the headline); the "
+                      "Legendre step runs on the tensor cores (tcgen05 kind::tf32, hi/lo split: 3 MMAs per term), "
+                      "32 maps per launch; the Fourier stages and interpolation per map",
+              "peak_tf32_tflops": round(mp.get("bf16_tflops", 1900.0) * 1.1 / 2.25, 1),
+              "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/BF16 ratio 1.1/2.25",
+              "legs": []}
+        rng = np.random.default_rng(7)
+        for nm in [int(v) for v in args.tc_maps.split(",") if v]:
+            a = torch.zeros(nm, 1, pT.nalm, dtype=pT.complex_dtype, device=dev)
+            a.real.normal_()
+            a.imag.normal_()
+            out = torch.empty(nm, 1, npts, dtype=torch.float32, device=dev)
+            res = {"maps": nm}
+            for on in (True, False):
+                pT.set_tensor_cores(on)
+                pT.synthesis(a, out=out)
+                barrier()
+                lib.lens_profile_reset()
+                lib.lens_profile_enable(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.nvtx.range_push("timed_tc" if on else "timed_tc_off")
+                e0.record(stream)
+                pT.synthesis(a, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
+                lib.lens_profile_enable(0)
+                tpm, tcn = profile_read()
+                call_ms = e0.elapsed_time(e1)
+                key = "tensor_cores" if on else "cuda_cores"
+                res[key] = {"synthesis_points_per_s": round(nm * npts / (call_ms * 1e-3), 1),
+                            "call_ms": round(call_ms, 3), "legendre_ms": round(tpm[0], 3),
+                            "legendre_ms_per_map": round(tpm[0] / nm, 4), "legendre_launches": int(tcn[0])}
+                if on:
+                    alg = 4.0 * nm * info_T["legendre_triples"]  # complex coefficient x real value per triple
+                    res[key]["legendre_alg_tflops"] = round(alg / (tpm[0] * 1e-3) / 1e12, 2)
+                    res[key]["tensor_tflops_split"] = round(3 * alg / (tpm[0] * 1e-3) / 1e12, 2)
+                    res[key]["tensor_frac"] = round(3 * alg / (tpm[0] * 1e-3) / 1e12 / tc["peak_tf32_tflops"], 4)
+            pT.set_tensor_cores(True)
+            tc["legs"].append(res)
+            del a, out
+        pT.status()
+    pT.close()
     torch.cuda.empty_cache()
 
     # ---------------- the same FP32 step with plan-time Legendre tables (when they fit)
@@ -588,6 +639,7 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
         "tables" if not tables else "recursion": alt,
+        "tensor_cores": tc,
         "fp64": fp64,
         "lmax5120": l5120,
     }

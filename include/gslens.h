@@ -123,12 +123,18 @@ typedef struct {
     int legendre_restart;   /* FP32 plans without tables, Legendre recursion arithmetic:
                                0 = choose: epsilon >= 1e-5 runs the recursion in FP32 and
                                resets it every K = 64 degrees (K doubled while the restart
-                               values would exceed 16 GB) to values computed at plan creation
+                               values would exceed 20 GB) to values computed at plan creation
                                (FP64 recursion; 8 or 16 bytes per ring, restart and order:
                                2.3 / 4.5 GB for spin 0 / spin s at lmax 4096); smaller
                                epsilon runs the double-float recursion.
                                -1 = always the double-float recursion.
                                K > 0 = restart every K degrees (a power of two, 8 .. 4096). */
+    int point_weights;      /* FP64 plans: 0 = keep the 2W kernel weights of every point when they
+                               take at most 48 GB (16 W bytes per point), else evaluate the taps in
+                               every call; -1 = always evaluate them per call (no weight table);
+                               1 = always keep them (LENS_ERR_NOMEM if they do not fit). */
+    int spread_tile_rows;   /* rows of the grid tiles that sort the points and that the spreading
+                               accumulates in shared memory (32 columns): 16, 32 or 64 (0 = 32) */
 } lens_plan_params;
 
 typedef struct {
@@ -153,6 +159,7 @@ typedef struct {
     int legendre_df32_mmin;      /* FP64 plans: first order run in double-float (mmax + 1: none) */
     int64_t legendre_triples;    /* restarted FP32 recursion: (ring pair, l, m) triples from the first
                                     degree at which |lambda| reaches 2^-40 on each ring (0 if not counted) */
+    size_t point_weight_bytes;   /* FP64 plans: kernel weights kept per point (0: evaluated per call) */
 } lens_plan_info_t;
 
 /*
@@ -166,7 +173,13 @@ typedef struct {
  *   chi_d      device double[npoints] spin phase, or NULL (ignored for spin 0).
  *   epsilon    target relative accuracy (Sect. 4, eps_eff); FP32 plans accept
  *              epsilon >= 2e-6 (FP32 rounding alone leaves ~1.2e-6 at lmax
- *              4096), FP64 plans epsilon >= 1e-13.
+ *              4096), FP64 plans epsilon >= 1e-13.  FP64 rounding sets a floor
+ *              that grows with lmax: epsilon below ~5e-12 is not reached at lmax
+ *              4096-5120 (epsilon 1e-12 or 1e-13 gives an adjoint eps_eff of
+ *              3.6e-12 .. 4.2e-12 there).  The orders run in double-float
+ *              (m >= legendre_df32_mmin, default 64 / 256 for epsilon >= 1e-9 /
+ *              >= 5e-11, scaled by (lmax / 4096)^2 above lmax 4096, none below
+ *              5e-11) keep the error of the all-FP64 recursion.
  *   prec       LENS_FP32 or LENS_FP64.
  *   flags      0, or LENS_GRAD_ONLY and / or LENS_DETERMINISTIC (lens_flags);
  *              other bits: LENS_ERR_INVALID.

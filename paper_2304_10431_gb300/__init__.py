@@ -70,7 +70,8 @@ class LensPlan:
                  W: int | None = None, beta: float | None = None, ntheta: int | None = None,
                  legendre_rpt: tuple | None = None, legendre_df32_mmin: int = 0, fft_cluster: int = 0,
                  grad_only: bool = False, deterministic: bool = False, legendre_tables: bool = False,
-                 legendre_restart: int = 0, device=None, stream=None):
+                 legendre_restart: int = 0, point_weights: int = 0, spread_tile_rows: int = 0,
+                 device=None, stream=None):
         lib = _native.load()
         if precision not in _PREC:
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -93,7 +94,7 @@ class LensPlan:
             rf, ra = legendre_rpt if legendre_rpt else (0, 0)
             prm = PlanParams(float(sigma or 0.0), int(W or 0), float(beta or 0.0), int(ntheta or 0), int(rf), int(ra),
                              int(legendre_df32_mmin), int(fft_cluster), 1 if legendre_tables else 0,
-                             int(legendre_restart))
+                             int(legendre_restart), int(point_weights), int(spread_tile_rows))
             handle = ctypes.c_void_p()
             st = _stream_handle(stream)
             rc = lib.lens_plan_create_ex(ctypes.byref(handle), self.lmax, self.mmax, self.spin, self.npoints,

@@ -65,7 +65,8 @@ class PlanParams(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("W", ctypes.c_int), ("beta", ctypes.c_double),
                 ("ntheta", ctypes.c_int), ("legendre_rpt_fwd", ctypes.c_int), ("legendre_rpt_adj", ctypes.c_int),
                 ("legendre_df32_mmin", ctypes.c_int), ("fft_cluster", ctypes.c_int), ("legendre_tables", ctypes.c_int),
-                ("legendre_restart", ctypes.c_int)]
+                ("legendre_restart", ctypes.c_int), ("point_weights", ctypes.c_int),
+                ("spread_tile_rows", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -77,7 +78,7 @@ class PlanInfo(ctypes.Structure):
                 ("plan_bytes", ctypes.c_size_t), ("flags", ctypes.c_uint), ("alm_ncomp", ctypes.c_int),
                 ("legendre_table_bytes", ctypes.c_size_t), ("legendre_restart", ctypes.c_int),
                 ("restart_bytes", ctypes.c_size_t), ("legendre_df32_mmin", ctypes.c_int),
-                ("legendre_triples", ctypes.c_int64)]
+                ("legendre_triples", ctypes.c_int64), ("point_weight_bytes", ctypes.c_size_t)]
 
 
 def lib_path() -> str:

@@ -13,7 +13,7 @@ namespace gsl {
 constexpr int kMaxFftStages = 24;
 constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
 constexpr int kLegBlock = 8;         // degrees per unrolled block of the Legendre kernels
-constexpr int kTileR = 32, kTileC = 32;  // grid tile of the point sort (rows x columns)
+constexpr int kTileR = 32, kTileC = 32;  // default grid tile of the point sort (rows x columns)
 
 // One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
 // and the digit-reversal table (input element i is stored at position perm[i]).
@@ -129,6 +129,11 @@ struct Plan {
     double *fx_scale = nullptr;               // [0] spreading unit, [1 + m] adjoint Legendre unit of order m
     unsigned long long *fx_maxbits = nullptr; // max |map value| of a call (bits of a double)
     uint32_t *fx_kmax = nullptr;              // most points any grid cell receives
+    // FP32 plans at epsilon >= 1e-5 (not deterministic): spreading tiles in 32-bit fixed point,
+    // per tile the most of its points covering one cell (plan time) and the map's largest
+    // |value| of a call (bits of a double)
+    unsigned short *tile_kmax = nullptr;
+    unsigned long long *maxbits = nullptr;
     // Legendre tables (FP32 plans, lens_plan_params.legendre_tables): values of
     // the monic functions per (m, l, ring group), see legendre.cu
     bool tab = false;
@@ -152,6 +157,7 @@ struct Plan {
     int32_t *perm = nullptr;   // sorted -> user index
     uint32_t *tile_start = nullptr;  // [ntiles + 1] first sorted point of each 32 x 32 grid tile
     int ntile_c = 0, ntiles = 0;     // tiles per grid row band, total tiles
+    int tile_r = kTileR;             // rows of a tile (16, 32 or 64; 32 columns)
     void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
     double *wts = nullptr;     // FP64 plans: [npts][2W] kernel weights (theta taps, then phi taps)
 

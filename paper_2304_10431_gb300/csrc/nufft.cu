@@ -66,9 +66,9 @@ __device__ __forceinline__ int grid_coord(double t, double2 c, double hw, double
 
 __global__ void k_prep(const double *__restrict__ theta, const double *__restrict__ phi,
                        const double *__restrict__ chi, int64_t n, int N1, int N2, int W, int r_lo, int R, int pitch,
-                       int spin, double2 c1, double2 c2, uint32_t *__restrict__ key, int32_t *__restrict__ idx,
-                       uint32_t *__restrict__ cell_u, double2 *__restrict__ frac_u, double2 *__restrict__ phase_u,
-                       unsigned *__restrict__ flags)
+                       int spin, double2 c1, double2 c2, int tile_r, uint32_t *__restrict__ key,
+                       int32_t *__restrict__ idx, uint32_t *__restrict__ cell_u, double2 *__restrict__ frac_u,
+                       double2 *__restrict__ phase_u, unsigned *__restrict__ flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -96,7 +96,7 @@ __global__ void k_prep(const double *__restrict__ theta, const double *__restric
     cell_u[i] = (uint32_t)row * (uint32_t)pitch + (uint32_t)j0;
     frac_u[i] = make_double2(fu, fv);
     const int ntc = (N2 + kTileC - 1) / kTileC;
-    key[i] = (uint32_t)(row / kTileR) * (uint32_t)ntc + (uint32_t)(j0 / kTileC);
+    key[i] = (uint32_t)(row / tile_r) * (uint32_t)ntc + (uint32_t)(j0 / kTileC);
     idx[i] = (int32_t)i;
     if (spin) {
         const double c = chi ? chi[i] : 0.0;
@@ -288,8 +288,20 @@ __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, 
     }
 }
 
-// FX: fixed-point integers in shared memory and in the grid (scale *fxs)
-template <typename T, int W, bool SPIN, bool PRE, bool FX>
+// FX: fixed-point integers in shared memory and in the grid (scale *fxs).
+// I32 (FP32 plans, epsilon >= 1e-5, not FX): the tile accumulates in 32-bit
+// fixed point in shared memory (integer atomics there run ~3x the rate of
+// float atomics), in units of 1/u with u = 2^k per tile, k the largest
+// integer with kmax_t max|x| u <= 2^30: kmax_t (plan time) is the most of the
+// tile's points whose W x W windows cover one cell and max|x| (per call) the
+// map's largest |value| (|Q| + |U| for spin s), taps |psi| <= 1, so no cell
+// sum can overflow.  Every term is rounded once (to 2^-k); the flush converts
+// back to FP32 for one global atomic per non-zero cell.  A map with a
+// non-finite value makes the whole tile NaN.
+template <typename T, bool FX, bool I32> struct SAcc { using type = typename Acc<T, FX>::type; };
+template <typename T> struct SAcc<T, false, true> { using type = int; };
+
+template <typename T, int W, bool SPIN, bool PRE, bool FX, bool I32 = false>
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                            const cplx<T> *__restrict__ frac,
                                                            const int32_t *__restrict__ perm,
@@ -297,22 +309,33 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
                                                            const double *__restrict__ wts, const T *__restrict__ map,
                                                            int64_t n, int pitch, int R, int ntc,
                                                            const uint32_t *__restrict__ tile_start, T beta,
-                                                           const double *__restrict__ fxs)
+                                                           const double *__restrict__ fxs,
+                                                           int tile_r, const unsigned short *__restrict__ tile_kmax,
+                                                           const unsigned long long *__restrict__ maxbits)
 {
-    using G = typename Acc<T, FX>::type;
-    constexpr int TR = kTileR + W - 1, TC = kTileC + W - 1, NC = SPIN ? 2 : 1;
-    __shared__ G buf[TR * TC * NC];
+    static_assert(!(I32 && FX), "fixed-point tiles or fixed-point grid");
+    using G = typename SAcc<T, FX, I32>::type;
+    constexpr int TC = kTileC + W - 1, NC = SPIN ? 2 : 1;
+    const int TR = tile_r + W - 1;  // tile rows (16, 32 or 64) plus the kernel halo
+    extern __shared__ __align__(16) unsigned char spread_smem[];
+    G *buf = reinterpret_cast<G *>(spread_smem);  // TR x TC cells x NC planes
     const int t = blockIdx.x;
     const uint32_t p0 = tile_start[t], p1 = tile_start[t + 1];
     if (p0 == p1) return;
-    const T sc = FX ? (T)fxs[0] : T(1);
+    T sc = FX ? (T)fxs[0] : T(1);
+    bool bad = false;  // I32: non-finite map value
+    if constexpr (I32) {
+        const double bound = (double)tile_kmax[t] * __longlong_as_double((long long)*maxbits);
+        if (!(bound < 1e300)) bad = true;  // infinity or NaN in the map
+        else if (bound > 0.0) sc = (T)ldexp(1.0, 30 - (ilogb(bound) + 1));  // bound < 2^(ilogb+1)
+    }
     for (int i = threadIdx.x; i < TR * TC * NC; i += blockDim.x) buf[i] = G(0);
     __syncthreads();
-    const int r0 = (t / ntc) * kTileR, c0 = (t % ntc) * kTileC;
-    for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const int r0 = (t / ntc) * tile_r, c0 = (t % ntc) * kTileC;
+    for (uint32_t p = p0 + threadIdx.x; p < (bad ? p0 : p1); p += blockDim.x) {
         const uint32_t c = cell[p];
         const int lr = (int)(c / (uint32_t)pitch) - r0, lc = (int)(c % (uint32_t)pitch) - c0;
-        if ((unsigned)lr >= (unsigned)kTileR || (unsigned)lc >= (unsigned)kTileC) continue;  // not this tile's
+        if ((unsigned)lr >= (unsigned)tile_r || (unsigned)lc >= (unsigned)kTileC) continue;  // not this tile's
         T wa[W], wb[W];
         tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
         const int32_t src = perm[p];
@@ -325,7 +348,10 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
             for (int a = 0; a < W; ++a) {
                 const T xa = wa[a] * x;
 #pragma unroll
-                for (int b = 0; b < W; ++b) acc_add<T, FX>(b0 + a * TC + b, xa * wb[b], sc);
+                for (int b = 0; b < W; ++b) {
+                    if constexpr (I32) atomicAdd(b0 + a * TC + b, __float2int_rn(xa * wb[b] * sc));
+                    else acc_add<T, FX>(b0 + a * TC + b, xa * wb[b], sc);
+                }
             }
         } else {
             // e^{-i s chi} (Q + i U)
@@ -338,13 +364,36 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
                     G *q2 = b0 + (a * TC + b);
-                    acc_add<T, FX>(q2, xa * wb[b], sc);
-                    acc_add<T, FX>(q2 + TR * TC, ya * wb[b], sc);
+                    if constexpr (I32) {
+                        atomicAdd(q2, __float2int_rn(xa * wb[b] * sc));
+                        atomicAdd(q2 + TR * TC, __float2int_rn(ya * wb[b] * sc));
+                    } else {
+                        acc_add<T, FX>(q2, xa * wb[b], sc);
+                        acc_add<T, FX>(q2 + TR * TC, ya * wb[b], sc);
+                    }
                 }
             }
         }
     }
     __syncthreads();
+    if constexpr (I32) {
+        T *g = (T *)grid;
+        const T inv = bad ? T(NAN) : T(1) / sc;
+        for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
+            const int gr = r0 + i / TC, gc = c0 + i % TC;
+            if (gr >= R || gc >= pitch) continue;
+            const int64_t o = (int64_t)gr * pitch + gc;
+            if (!SPIN) {
+                const int v = buf[i];
+                if (v != 0 || bad) atomicAdd(g + o, (T)v * inv);
+            } else {
+                const int vx = buf[i], vy = buf[TR * TC + i];
+                if (vx != 0 || bad) atomicAdd(g + 2 * o, (T)vx * inv);
+                if (vy != 0 || bad) atomicAdd(g + 2 * o + 1, (T)vy * inv);
+            }
+        }
+        return;
+    }
     G *g = (G *)grid;
     for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
         const int gr = r0 + i / TC, gc = c0 + i % TC;
@@ -359,6 +408,54 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
             if (vy != G(0)) atomicAdd(g + 2 * o + 1, vy);
         }
     }
+}
+
+// Plan time, FP32 plans: kmax_t of every tile, the most of the tile's points
+// whose W x W windows (from their first-tap cell) cover a single cell: counts
+// h per first-tap cell of the tile, then window sums over W rows and W columns
+// for every cell of the tile and its halo.
+template <int W>
+__global__ void __launch_bounds__(256) k_tile_window_kmax(const uint32_t *__restrict__ cell, int pitch, int ntc,
+                                                         int tile_r, const uint32_t *__restrict__ tile_start,
+                                                         unsigned short *__restrict__ out)
+{
+    constexpr int TC = kTileC + W - 1;
+    const int TR = tile_r + W - 1;
+    extern __shared__ int kmax_smem[];
+    int *h = kmax_smem;                    // [tile_r][32] points per first-tap cell (lr, lc)
+    int *v = kmax_smem + tile_r * kTileC;  // [TR][32]: v[r][c] = sum over a < W of h[r - a][c]
+    __shared__ int best;
+    const int t = blockIdx.x;
+    const uint32_t p0 = tile_start[t], p1 = tile_start[t + 1];
+    for (int i = threadIdx.x; i < tile_r * kTileC; i += blockDim.x) h[i] = 0;
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    const int r0 = (t / ntc) * tile_r, c0 = (t % ntc) * kTileC;
+    for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t c = cell[p];
+        const int lr = (int)(c / (uint32_t)pitch) - r0, lc = (int)(c % (uint32_t)pitch) - c0;
+        if ((unsigned)lr < (unsigned)tile_r && (unsigned)lc < (unsigned)kTileC) atomicAdd(&h[lr * kTileC + lc], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TR * kTileC; i += blockDim.x) {
+        const int r = i / kTileC, c = i % kTileC;
+        int sum = 0;
+        for (int a = 0; a < W; ++a)
+            if (r - a >= 0 && r - a < tile_r) sum += h[(r - a) * kTileC + c];
+        v[i] = sum;
+    }
+    __syncthreads();
+    int mx = 0;
+    for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
+        const int r = i / TC, c = i % TC;
+        int sum = 0;
+        for (int b = 0; b < W; ++b)
+            if (c - b >= 0 && c - b < kTileC) sum += v[r * kTileC + c - b];
+        mx = max(mx, sum);
+    }
+    atomicMax(&best, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) out[t] = (unsigned short)min(best, 65535);
 }
 
 // ---------------------------------------------- fixed point (deterministic plans)
@@ -456,14 +553,19 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
                 grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
         }
     } else {
-        if (p.det)
-            k_spread<T, W, SPIN, false, true><<<(unsigned)p.ntiles, kSpreadThreads, 0, st>>>(
+        const size_t cells = (size_t)(p.tile_r + W - 1) * (kTileC + W - 1) * (SPIN ? 2 : 1);
+        const auto run = [&](auto kern, size_t esz) {
+            const size_t sm = cells * esz;
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e2 != cudaSuccess) return e2;
+            kern<<<(unsigned)p.ntiles, kSpreadThreads, sm, st>>>(
                 grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs);
-        else
-            k_spread<T, W, SPIN, false, false><<<(unsigned)p.ntiles, kSpreadThreads, 0, st>>>(
-                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs);
+                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+            return cudaGetLastError();
+        };
+        if (p.det) return run(k_spread<T, W, SPIN, false, true>, 8);
+        if (p.tile_kmax) return run(k_spread<T, W, SPIN, false, false, true>, 4);
+        return run(k_spread<T, W, SPIN, false, false>, sizeof(T));
     }
     return cudaGetLastError();
 }
@@ -527,6 +629,15 @@ cudaError_t launch_spread(const Plan &p, const void *map, void *grid, cudaStream
     if (e != cudaSuccess) return e;
     const bool f32 = p.prec == LENS_FP32;
     if (!p.det) {
+        if (f32 && p.tile_kmax) {  // fixed-point tiles: the map's largest |value| first
+            if ((e = cudaMemsetAsync(p.maxbits, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+            if (p.npts > 0) {
+                const unsigned mb = (unsigned)std::min<int64_t>((p.npts + 255) / 256, 152 * 8);
+                if (p.spin) k_fx_maxabs<float, true><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
+                else k_fx_maxabs<float, false><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+        }
         if (f32)
             return p.spin ? spread_dispatch<float, true>(p, map, grid, st)
                           : spread_dispatch<float, false>(p, map, grid, st);
@@ -600,10 +711,10 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
         return make_double2(hi, q2 - (hi - q1));
     };
     k_prep<<<blocks, thr, 0, st>>>(theta, phi, chi, n, p.N1, p.N2, p.W, p.r_lo, p.R, p.pitch, p.spin, scale_of(p.N1),
-                                   scale_of(p.N2), key, idx, cell_u, frac_u, phase_u, p.flags);
+                                   scale_of(p.N2), p.tile_r, key, idx, cell_u, frac_u, phase_u, p.flags);
     GSL_TRY(cudaGetLastError());
     const int ntc = (p.N2 + kTileC - 1) / kTileC;
-    const uint64_t nkeys = (uint64_t)((p.R + kTileR - 1) / kTileR) * ntc;
+    const uint64_t nkeys = (uint64_t)((p.R + p.tile_r - 1) / p.tile_r) * ntc;
     int bits = 1;
     while (bits < 32 && (1ull << bits) < nkeys) ++bits;
     GSL_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, key2, idx, p.perm, (int)n, 0, bits, st));
@@ -618,6 +729,28 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
     if (p.det) {
         GSL_TRY(cudaMemsetAsync(p.fx_kmax, 0, sizeof(uint32_t), st));
         k_tile_kmax<<<(unsigned)((p.ntiles + thr - 1) / thr), thr, 0, st>>>(p.tile_start, p.ntiles / ntc, ntc, p.fx_kmax);
+        GSL_TRY(cudaGetLastError());
+    }
+    if (p.tile_kmax) {  // FP32 fixed-point spreading tiles: kmax_t per tile
+        const size_t sm = sizeof(int) * (size_t)kTileC * (2 * p.tile_r + p.W - 1);
+        const auto run = [&](auto kern) {
+            kern<<<(unsigned)p.ntiles, 256, sm, st>>>(p.cell, p.pitch, ntc, p.tile_r, p.tile_start, p.tile_kmax);
+        };
+        switch (p.W) {
+        case 4: run(k_tile_window_kmax<4>); break;
+        case 5: run(k_tile_window_kmax<5>); break;
+        case 6: run(k_tile_window_kmax<6>); break;
+        case 7: run(k_tile_window_kmax<7>); break;
+        case 8: run(k_tile_window_kmax<8>); break;
+        case 9: run(k_tile_window_kmax<9>); break;
+        case 10: run(k_tile_window_kmax<10>); break;
+        case 11: run(k_tile_window_kmax<11>); break;
+        case 12: run(k_tile_window_kmax<12>); break;
+        case 13: run(k_tile_window_kmax<13>); break;
+        case 14: run(k_tile_window_kmax<14>); break;
+        case 15: run(k_tile_window_kmax<15>); break;
+        default: run(k_tile_window_kmax<16>); break;
+        }
         GSL_TRY(cudaGetLastError());
     }
     if (p.wts) {

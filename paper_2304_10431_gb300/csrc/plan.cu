@@ -443,16 +443,24 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     // HEALPix Nside 2048, eps 1e-10 (spin 0 / spin 2) against FP64 direct summation:
     //   df32 from m = 1: 2.3e-10 / 1.7e-10;  m = 64: 6.1e-11 / 5.1e-11;
     //   m = 128: 2.5e-11 / 2.3e-11;  m = 256: 8.3e-12 / 8.8e-12 (= all-FP64).
-    // Hence m_df = 64 for epsilon >= 1e-9, 256 for epsilon >= 5e-11, none below.
+    // Hence m_df = 64 for epsilon >= 1e-9, 256 for epsilon >= 5e-11, none below,
+    // times (lmax / 4096)^2 above lmax 4096 (lmax 8192, spin 0, eps 1e-10: adjoint
+    // eps_eff 3.5e-10 with m_df = 256, 6.3e-11 with m_df = 1024 = all-FP64's).
     if (prec == LENS_FP32) {
         p->m_df = 0;
     } else {
         const int want = prm ? prm->legendre_df32_mmin : 0;
         if (want < 0) p->m_df = mmax + 1;
         else if (want > 0) p->m_df = std::min(want, mmax + 1);
-        else if (epsilon >= 1e-9) p->m_df = std::min(64, mmax + 1);
-        else if (epsilon >= 5e-11) p->m_df = std::min(256, mmax + 1);
-        else p->m_df = mmax + 1;
+        else {
+            // the double-float recursion's error grows with lmax at a given m: at lmax 8192,
+            // epsilon 1e-10, orders 256..1023 in df32 gave an adjoint eps_eff of 3.5e-10
+            // against 6.3e-11 with FP64 up to m = 1024; so the FP64 orders scale as lmax^2
+            const double g = std::max(1.0, ((double)lmax / 4096.0) * ((double)lmax / 4096.0));
+            if (epsilon >= 1e-9) p->m_df = (int)std::min<double>(64.0 * g, mmax + 1);
+            else if (epsilon >= 5e-11) p->m_df = (int)std::min<double>(256.0 * g, mmax + 1);
+            else p->m_df = mmax + 1;
+        }
     }
     // ---- FP32 plans: restarted FP32 recursion (legendre.cu, PolS / PolR) or df32
     {
@@ -468,7 +476,7 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
                 return n * p->nnorth * esz_ck;
             };
             size_t b = bytes_for(K);
-            while (want == 0 && b > ((size_t)16 << 30) && K < 4096) b = bytes_for(K *= 2);
+            while (want == 0 && b > ((size_t)20 << 30) && K < 4096) b = bytes_for(K *= 2);
             p->rst = true;
             p->ck.K = K;
             p->ck_bytes = b;
@@ -563,19 +571,37 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if ((e = B.alloc((void **)&p->cell, sizeof(uint32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc cell");
         if ((e = B.alloc(&p->frac, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc frac");
         if ((e = B.alloc((void **)&p->perm, sizeof(int32_t) * npoints, false)) != cudaSuccess) return bailc(e, "alloc perm");
+        const int tr = prm ? prm->spread_tile_rows : 0;
+        if (tr != 0 && tr != 16 && tr != 32 && tr != 64)
+            return bail(LENS_ERR_INVALID, "spread_tile_rows must be 0, 16, 32 or 64");
+        p->tile_r = tr ? tr : kTileR;
         p->ntile_c = (p->N2 + kTileC - 1) / kTileC;
-        p->ntiles = (p->R + kTileR - 1) / kTileR * p->ntile_c;
+        p->ntiles = (p->R + p->tile_r - 1) / p->tile_r * p->ntile_c;
         if ((e = B.alloc((void **)&p->tile_start, sizeof(uint32_t) * ((size_t)p->ntiles + 1), false)) != cudaSuccess)
             return bailc(e, "alloc tile table");
         if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
+        // FP32 plans at epsilon >= 1e-5 accumulate the spreading tiles in 32-bit fixed point
+        // (nufft.cu, k_spread); smaller epsilon and deterministic plans keep their own paths
+        if (prec == LENS_FP32 && !p->det && epsilon >= 1e-5) {
+            if ((e = B.alloc((void **)&p->tile_kmax, sizeof(unsigned short) * (size_t)p->ntiles, false)) != cudaSuccess ||
+                (e = B.alloc((void **)&p->maxbits, sizeof(unsigned long long), true)) != cudaSuccess)
+                return bailc(e, "alloc spreading bounds");
+        }
         // FP64 plans keep the 2W kernel weights of every point (GB300's FP64 pipe makes
         // evaluating exp/sqrt per tap far dearer than reading 16 W bytes per point),
         // unless the table would exceed 48 GB (e.g. 805M points at W = 16: 206 GB);
         // then the taps are evaluated per call
         const size_t wbytes = sizeof(double) * 2 * (size_t)p->W * npoints;
-        if (prec == LENS_FP64 && wbytes <= (size_t)48 << 30 &&
-            (e = B.alloc((void **)&p->wts, wbytes, false)) != cudaSuccess)
+        const int pw = prm ? prm->point_weights : 0;
+        if (pw < -1 || pw > 1) return bail(LENS_ERR_INVALID, "point_weights must be -1, 0 or 1");
+        if (prec == LENS_FP64 && (pw == 1 || (pw == 0 && wbytes <= (size_t)48 << 30)) &&
+            (e = B.alloc((void **)&p->wts, wbytes, false)) != cudaSuccess) {
+            if (e == cudaErrorMemoryAllocation) {
+                cudaGetLastError();
+                return bail(LENS_ERR_NOMEM, "point kernel weights: " + std::to_string(wbytes >> 20) + " MiB not available");
+            }
             return bailc(e, "alloc weights");
+        }
     }
 
     // ---- host tables: start-value norms, rings, deconvolution factors
@@ -738,6 +764,7 @@ int lens_plan_info(lens_plan pl, lens_plan_info_t *info)
     info->restart_bytes = p->ck_bytes;
     info->legendre_df32_mmin = p->prec == LENS_FP64 ? p->m_df : 0;
     info->legendre_triples = p->leg_triples;
+    info->point_weight_bytes = p->wts ? sizeof(double) * 2 * (size_t)p->W * p->npts : 0;
     return LENS_OK;
 }
 

@@ -171,6 +171,29 @@ def test_fp64_plan_df32_orders(spin, mmin):
     assert rel(at, O.adjoint(L, L, spin, th, ph, y, chi)) <= 1e-10
 
 
+@pytest.mark.parametrize("spin", [0, 2])
+def test_fp64_without_point_weights(spin):
+    """FP64 plans evaluate the kernel taps in every call when the per-point weight table is not kept
+    (above 48 GB, or point_weights = -1): same results as with the table, and the oracle's."""
+    L, n = 160, 6000
+    th, ph, chi = W.random_points(n, 51 + spin)
+    kw = dict(spin=spin, epsilon=1e-10, precision="fp64", device=DEV)
+    p0 = LensPlan(L, th, ph, chi, point_weights=-1, **kw)
+    p1 = LensPlan(L, th, ph, chi, point_weights=1, **kw)
+    assert p0.info()["point_weight_bytes"] == 0 and p1.info()["point_weight_bytes"] == 16 * p1.info()["W"] * n
+    a = make_alm(L, spin, 23)
+    m0 = p0.synthesis(gpu_alm(p0, a)).cpu().numpy()
+    m1 = p1.synthesis(gpu_alm(p1, a)).cpu().numpy()
+    ref = O.synthesis(L, L, spin, th, ph, a, chi)
+    assert rel(m0, ref) <= 1e-10 and rel(m0, m1) <= 1e-12
+    y = np.random.default_rng(spin + 5).standard_normal(ref.shape)
+    a0 = p0.adjoint(gpu_map(p0, y)).cpu().numpy()
+    a1 = p1.adjoint(gpu_map(p1, y)).cpu().numpy()
+    assert rel(a0, O.adjoint(L, L, spin, th, ph, y, chi)) <= 1e-10 and rel(a0, a1) <= 1e-12
+    with pytest.raises(LensError):
+        LensPlan(L, th, ph, chi, point_weights=2, **kw)
+
+
 # ---------------------------------------------------------------- edge cases
 def test_mmax_below_lmax():
     L, mmax, n = 40, 17, 1500
