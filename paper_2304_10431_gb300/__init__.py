@@ -16,6 +16,8 @@ Maps: real tensor [ncomp, npoints] (or [nmaps, ncomp, npoints]).
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 
 import numpy as np
 import torch
@@ -541,25 +543,67 @@ class LensBatch:
             pass
 
 
+def _autotune_cache_path() -> str:
+    d = os.environ.get("LENS_CACHE_DIR") or os.path.join(os.path.expanduser("~"), ".cache", "gslens")
+    return os.path.join(d, "autotune.json")
+
+
 def autotune(lmax: int, theta, phi, chi=None, spin: int = 0, mmax: int | None = None, epsilon: float = 1e-5,
-             precision: str = "fp32", reps: int = 2, device=None, stream=None) -> dict:
-    """Measured plan parameters for these points (lens_autotune): LensPlan keyword
-    arguments (sigma, legendre_rpt) plus "ms", one forward + adjoint pair."""
+             precision: str = "fp32", reps: int = 2, device=None, stream=None, cache: bool = True) -> dict:
+    """Measured plan parameters for these points (lens_autotune): LensPlan keyword arguments
+    (sigma, W, spread_tile_rows, legendre_rpt) plus "ms", one forward + adjoint pair.
+
+    Results are kept in a JSON file ($LENS_CACHE_DIR/autotune.json, default ~/.cache/gslens),
+    keyed by the GPU name, lmax, mmax, spin, precision, epsilon and the point count rounded to
+    a quarter octave (the point density per ring); cache=False always measures (and updates
+    the file)."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    mm = int(lmax if mmax is None else mmax)
     with torch.cuda.device(dev):
         th, ph = _dev_f64(theta, dev), _dev_f64(phi, dev)
         ch = _dev_f64(chi, dev) if (chi is not None and spin) else None
+        n = int(th.numel())
+        key = "%s|lmax=%d|mmax=%d|spin=%d|%s|eps=%.3g|npts~2^%.2f" % (
+            torch.cuda.get_device_name(dev), int(lmax), mm, int(spin), precision, float(epsilon),
+            round(4 * np.log2(max(n, 1))) / 4)
+        path = _autotune_cache_path()
+        table = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as fh:
+                    table = json.load(fh)
+            except (OSError, ValueError):
+                table = {}
+        if cache and key in table:
+            out = dict(table[key])
+            if "legendre_rpt" in out:
+                out["legendre_rpt"] = tuple(out["legendre_rpt"])
+            out["cached"] = True
+            return out
         best = PlanParams()
         ms = ctypes.c_double()
-        _native.check(_native.load().lens_autotune(int(lmax), int(lmax if mmax is None else mmax), int(spin),
-                                                   int(th.numel()), th.data_ptr() if th.numel() else None,
-                                                   ph.data_ptr() if ph.numel() else None,
+        _native.check(_native.load().lens_autotune(int(lmax), mm, int(spin), n, th.data_ptr() if n else None,
+                                                   ph.data_ptr() if n else None,
                                                    ch.data_ptr() if ch is not None else None, float(epsilon),
                                                    _PREC[precision], _stream_handle(stream), int(reps),
                                                    ctypes.byref(best), ctypes.byref(ms)))
     out = {"sigma": best.sigma, "ms": ms.value}
+    if best.W:
+        out["W"] = best.W
+    if best.spread_tile_rows:
+        out["spread_tile_rows"] = best.spread_tile_rows
     if best.legendre_rpt_fwd or best.legendre_rpt_adj:
         out["legendre_rpt"] = (best.legendre_rpt_fwd, best.legendre_rpt_adj)
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        table[key] = {k: (list(v) if isinstance(v, tuple) else v) for k, v in out.items()}
+        tmp = path + ".%d.tmp" % os.getpid()
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # an unwritable cache directory only costs a re-measurement next time
+    out["cached"] = False
     return out
 
 

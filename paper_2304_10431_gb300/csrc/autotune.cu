@@ -2,10 +2,17 @@
 //
 // The paper picks its kernel parameters with a "simple heuristic"; a plan here
 // uses a cost model (plan.cu).  lens_autotune instead builds candidate plans
-// for the caller's points and times them on the GPU: first the oversampling
-// factor sigma (the kernel support W follows from epsilon), then the Legendre
-// rings per thread of the forward and adjoint kernels at the best sigma.  Each
-// candidate is timed over `reps` forward + adjoint pairs after one warm-up
+// for the caller's points and times them on the GPU, one parameter group at a
+// time, each at the best values found so far:
+//   1. the oversampling factor sigma with the smallest kernel support W that
+//      meets epsilon (the accuracy frontier of (sigma, W));
+//   2. W + 1 at that sigma (a wider kernel: more taps per point, a better
+//      conditioned deconvolution);
+//   3. the rows of the grid tiles that sort the points and hold the spreading
+//      accumulators (16, 32, 64; 32 columns);
+//   4. the Legendre rings per thread of the forward and adjoint kernels (1, 2,
+//      and 4 for FP32 plans with the restarted recursion).
+// Each candidate is timed over `reps` forward + adjoint pairs after one warm-up
 // pair, with CUDA events on the caller's stream.  No counterpart in the paper.
 #include <cuda_runtime.h>
 
@@ -92,14 +99,17 @@ extern "C" int lens_autotune(int lmax, int mmax, int spin, int64_t npoints, cons
     lens_plan_params cur = {};
     lens_plan_params win = {};
     double win_ms = -1.0;
+    int win_W = 0;  // kernel support of the winning plan
     auto trial = [&](const lens_plan_params &prm) {
         lens_plan pl = nullptr;
         if (lens_plan_create_ex(&pl, lmax, mmax, spin, npoints, theta_d, phi_d, chi_d, epsilon, prec, 0, stream,
                                 &prm) != LENS_OK)
             return;  // candidate outside this build's limits
         const double ms = time_plan(pl, alm, map, reps, st);
+        lens_plan_info_t inf;
+        const int w = lens_plan_info(pl, &inf) == LENS_OK ? inf.W : 0;
         lens_plan_destroy(pl);
-        if (ms > 0 && (win_ms < 0 || ms < win_ms)) { win_ms = ms; win = prm; }
+        if (ms > 0 && (win_ms < 0 || ms < win_ms)) { win_ms = ms; win = prm; win_W = w; }
     };
     const double sig_cand[] = {1.25, 1.5, 1.75, 2.0, 2.25, 2.5};
     for (double sg : sig_cand) {
@@ -107,10 +117,24 @@ extern "C" int lens_autotune(int lmax, int mmax, int spin, int64_t npoints, cons
         cur.sigma = sg;
         trial(cur);
     }
-    if (win_ms > 0) {
+    if (win_ms > 0 && win_W > 0 && win_W < 16) {  // 2. one tap wider at the best sigma
+        cur = win;
+        cur.W = win_W + 1;
+        trial(cur);
+    }
+    if (win_ms > 0) {  // 3. tile rows of the point sort / spreading accumulators
         const lens_plan_params base = win;
-        for (int rf = 1; rf <= 2; ++rf)
-            for (int ra = 1; ra <= 2; ++ra) {
+        for (int tr : {16, 64}) {
+            cur = base;
+            cur.spread_tile_rows = tr;
+            trial(cur);
+        }
+    }
+    if (win_ms > 0) {  // 4. Legendre rings per thread (4: restarted FP32 recursion only)
+        const lens_plan_params base = win;
+        const int rmax = prec == LENS_FP32 ? 4 : 2;
+        for (int rf = 1; rf <= rmax; rf *= 2)
+            for (int ra = 1; ra <= rmax; ra *= 2) {
                 cur = base;
                 cur.legendre_rpt_fwd = rf;
                 cur.legendre_rpt_adj = ra;
@@ -121,6 +145,7 @@ extern "C" int lens_autotune(int lmax, int mmax, int spin, int64_t npoints, cons
     cudaFree(map);
     if (win_ms < 0) return record_failure(LENS_ERR_UNSUPPORTED, "lens_autotune: no candidate plan could be built");
     *best = win;
+    if (best->W == 0) best->W = win_W;  // report the support the winning plan used
     if (best_ms) *best_ms = win_ms;
     return LENS_OK;
 }

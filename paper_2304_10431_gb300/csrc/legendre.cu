@@ -157,6 +157,30 @@ template <class P, int RPT, bool SPIN, int NM = 1, bool GRAD = false> struct Fwd
             }
         }
     }
+    // add_vals with the degree's prepared coefficients already loaded (one map, full spin-s or spin 0)
+    template <bool ODD>
+    __device__ __forceinline__ void add_vals_c(const typename P::V (&vp)[RPT], const typename P::V (&vm)[RPT], K ar,
+                                               K ai, K br, K bi)
+    {
+        static_assert(NM == 1 && !GRAD, "one map, not gradient-only");
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!SPIN) {
+                if (!ODD) { P::fma(r0[0][k], ar, vp[k]); P::fma(i0[0][k], ai, vp[k]); }
+                else { P::fma(r1[0][k], ar, vp[k]); P::fma(i1[0][k], ai, vp[k]); }
+            } else {
+                P::fma(r0[0][k], ar, vp[k]); P::fma(i0[0][k], ai, vp[k]);
+                P::fma(r2[0][k], br, vm[k]); P::fma(i2[0][k], bi, vm[k]);
+                if (!ODD) {
+                    P::fma(r1[0][k], ar, vm[k]); P::fma(i1[0][k], ai, vm[k]);
+                    P::fma(r3[0][k], br, vp[k]); P::fma(i3[0][k], bi, vp[k]);
+                } else {
+                    P::fms(r1[0][k], ar, vm[k]); P::fms(i1[0][k], ai, vm[k]);
+                    P::fms(r3[0][k], br, vp[k]); P::fms(i3[0][k], bi, vp[k]);
+                }
+            }
+        }
+    }
     // general path (start value and tail): parity known at run time only
     __device__ __forceinline__ void add_rt(const Rings<P, RPT, SPIN> &st, int l, bool odd)
     {
@@ -179,6 +203,40 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
             st.template advance<0, REG != 0>(reca, rect, l);
             if (REG != 1) acc.template add<0, REG == 2, false>(st, l);
         }
+    }
+}
+
+// Restarted FP32 recursion, one map: the block's step-table entries and
+// prepared coefficients are loaded together before its 8 steps, so their
+// latency is paid once per block instead of once per degree.
+template <class P, int RPT, bool SPIN, int REG>
+__device__ __forceinline__ void fwd_block_pf(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, 1, false> &acc,
+                                             const float4 *reca, const float2 *ca, const float2 *cb, int lb)
+{
+    float4 tb[kBlk];
+    float2 a[kBlk], b[kBlk];
+#pragma unroll
+    for (int j = 0; j < kBlk; ++j) {
+        tb[j] = __ldg(reca + lb + j);
+        if (REG != 1) {
+            a[j] = __ldg(ca + lb + j);
+            if (SPIN) b[j] = __ldg(cb + lb + j);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kBlk; ++j) {
+        typename P::V vp[RPT], vm[RPT];
+        if (j & 1) st.template advance_c<1, REG != 0>(tb[j]);
+        else st.template advance_c<0, REG != 0>(tb[j]);
+        if (REG == 1) continue;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            vp[k] = (j & 1) ? st.template vplus<1, REG == 2>(k) : st.template vplus<0, REG == 2>(k);
+            if (SPIN) vm[k] = (j & 1) ? st.template vminus<1, REG == 2>(k) : st.template vminus<0, REG == 2>(k);
+        }
+        const float2 bb = SPIN ? b[j] : make_float2(0.f, 0.f);
+        if (j & 1) acc.template add_vals_c<true>(vp, vm, a[j].x, a[j].y, bb.x, bb.y);
+        else acc.template add_vals_c<false>(vp, vm, a[j].x, a[j].y, bb.x, bb.y);
     }
 }
 
@@ -236,9 +294,17 @@ __device__ __forceinline__ void leg_fwd_body(const void *__restrict__ coef, cons
         }
         const int reg = st.regime();
         acc.renorm();
-        if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM, GRAD>(st, acc, reca, rect, l);
-        else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM, GRAD>(st, acc, reca, rect, l);
-        else fwd_block<P, RPT, SPIN, 2, NM, GRAD>(st, acc, reca, rect, l);
+        if constexpr (P::kRestart && NM == 1 && !GRAD) {
+            const float2 *ca = (const float2 *)coef + base;
+            const float2 *cb = (const float2 *)coef + nalm + base;
+            if (reg == 0) fwd_block_pf<P, RPT, SPIN, 0>(st, acc, (const float4 *)reca, ca, cb, l);
+            else if (reg == 1) fwd_block_pf<P, RPT, SPIN, 1>(st, acc, (const float4 *)reca, ca, cb, l);
+            else fwd_block_pf<P, RPT, SPIN, 2>(st, acc, (const float4 *)reca, ca, cb, l);
+        } else {
+            if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM, GRAD>(st, acc, reca, rect, l);
+            else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM, GRAD>(st, acc, reca, rect, l);
+            else fwd_block<P, RPT, SPIN, 2, NM, GRAD>(st, acc, reca, rect, l);
+        }
     }
     for (; l <= lmax; ++l) {  // tail: general path
         st.advance_moved(reca, rect, l);

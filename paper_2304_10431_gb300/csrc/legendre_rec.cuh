@@ -549,7 +549,11 @@ template <int RPT, bool SPIN> struct Rings<PolS, RPT, SPIN> {
     template <int NW, bool CHECK>
     __device__ __forceinline__ void advance(const float4 *reca, const float4 *, int l)
     {
-        const float4 c = __ldg(reca + l);  // (A, B, AT, K)
+        advance_c<NW, CHECK>(__ldg(reca + l));
+    }
+    // one step with the step-table entry c = (A, B, AT, K) of the degree already loaded
+    template <int NW, bool CHECK> __device__ __forceinline__ void advance_c(const float4 c)
+    {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!SPIN) {
@@ -665,7 +669,10 @@ template <int RPT, bool SPIN> struct Rings<PolR, RPT, SPIN> {
     template <int NW, bool CHECK>
     __device__ __forceinline__ void advance(const float4 *reca, const float4 *, int l)
     {
-        const float4 c = __ldg(reca + l);  // (A, B, AT, K)
+        advance_c<NW, CHECK>(__ldg(reca + l));
+    }
+    template <int NW, bool CHECK> __device__ __forceinline__ void advance_c(const float4 c)
+    {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const float dp = __fmaf_rn(c.x, y1[k], c.w);

@@ -72,7 +72,7 @@ def test_autotune_returns_a_working_plan():
     th, ph, chi = W.random_points(200000, 71)
     best = autotune(256, th, ph, chi, spin=2, epsilon=1e-5, precision="fp32", reps=2, device=DEV)
     assert best["ms"] > 0 and 1.2 <= best["sigma"] <= 2.5
-    kw = {k: v for k, v in best.items() if k != "ms"}
+    kw = {k: v for k, v in best.items() if k not in ("ms", "cached")}
     plan = LensPlan(256, th, ph, chi, spin=2, epsilon=1e-5, precision="fp32", device=DEV, **kw)
     a = np.stack([W.draw_alm(W.cmb_cl(256, 180.0), 256, 80 + c, spin=2) for c in range(2)])
     s = np.arange(0, th.size, 997)
@@ -98,7 +98,7 @@ def test_batched_lensing_64_instances():
         key = (lmax, spin, prec)
         if key not in tuned:  # one autotuner run per (lmax, spin, precision) class
             best = autotune(lmax, th, ph, chi, spin=spin, epsilon=eps, precision=prec, reps=1, device=DEV)
-            tuned[key] = {k2: v for k2, v in best.items() if k2 != "ms"}
+            tuned[key] = {k2: v for k2, v in best.items() if k2 not in ("ms", "cached")}
         plan, alm, x, a = _instance(k, lmax, spin, prec, eps, th, ph, chi, **tuned[key])
         geoms[k] = (th, ph, chi, a)
         items.append((plan, alm, x))
@@ -120,19 +120,46 @@ def test_batched_lensing_64_instances():
     npts = sum(p.npoints for p, *_ in items)
     print("64 instances, %d points: graph %.3f s (%.3g lensed points/s, forward + adjoint)"
           % (npts, t_graph, 2 * npts / t_graph))
-    # every instance equals its individual call; two small ones also against the oracle
+    # every instance equals its individual call
     for k, ((plan, alm, x), (m, a)) in enumerate(zip(items, outs)):
         tol = 1e-6 if plan.precision == "fp32" else 1e-13
         assert rel(m, plan.synthesis(alm)) <= tol, k
         assert rel(a, plan.adjoint(x)) <= tol, k
-    small = [k for k in range(64) if items[k][0].lmax == 256][:2]
-    for k in small:
+    # one instance of every lmax class against the oracle on sampled outputs (forward), and the
+    # adjoint of a map supported on those samples (exact a_lm from the oracle)
+    checked = {}
+    for k in range(64):
+        L = items[k][0].lmax
+        if L in checked:
+            continue
+        checked[L] = k
         plan, alm, x = items[k]
         th, ph, chi, a = geoms[k]
-        s = np.arange(0, th.size, max(1, th.size // 200))
+        nsamp = 96 if L <= 1024 else 32
+        s = np.arange(0, th.size, max(1, th.size // nsamp))
         got = outs[k][0][:, torch.as_tensor(s, device=DEV)].cpu().numpy()
-        ref = O.synthesis(plan.lmax, plan.lmax, plan.spin, th[s], ph[s], a, chi[s] if plan.spin else None)
-        assert np.linalg.norm(got - ref) <= plan.epsilon * np.linalg.norm(ref)
+        ref = O.synthesis(L, L, plan.spin, th[s], ph[s], a, chi[s] if plan.spin else None)
+        assert np.linalg.norm(got - ref) <= plan.epsilon * np.linalg.norm(ref), (k, L)
+        y = np.random.default_rng(k).standard_normal((plan.ncomp, s.size))
+        ymap = torch.zeros(plan.ncomp, plan.npoints, dtype=plan.real_dtype, device=DEV)
+        ymap[:, torch.as_tensor(s, device=DEV)] = torch.as_tensor(y, dtype=plan.real_dtype, device=DEV)
+        aref = O.adjoint(L, L, plan.spin, th[s], ph[s], y, chi[s] if plan.spin else None)
+        at = plan.adjoint(ymap).cpu().numpy()
+        assert np.linalg.norm(at - aref) <= plan.epsilon * np.linalg.norm(aref), (k, L)
+    assert sorted(checked) == sorted(set(int(v) for v in lmaxes))
     batch.close()
     for plan, *_ in items:
         plan.close()
+
+
+def test_autotune_cache(tmp_path, monkeypatch):
+    """The second autotune call for the same key reads the JSON cache instead of measuring."""
+    monkeypatch.setenv("LENS_CACHE_DIR", str(tmp_path))
+    th, ph, chi = W.random_points(30000, 72)
+    a = autotune(128, th, ph, chi, spin=0, epsilon=1e-5, precision="fp32", reps=1, device=DEV)
+    assert a["cached"] is False and (tmp_path / "autotune.json").exists()
+    b = autotune(128, th, ph, chi, spin=0, epsilon=1e-5, precision="fp32", reps=1, device=DEV)
+    assert b["cached"] is True and {k: b[k] for k in a if k != "cached"} == {k: a[k] for k in a if k != "cached"}
+    assert "W" in a and a["W"] >= 4
+    c = autotune(128, th, ph, chi, spin=0, epsilon=1e-5, precision="fp32", reps=1, device=DEV, cache=False)
+    assert c["cached"] is False
