@@ -206,9 +206,10 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
     }
 }
 
-// Restarted FP32 recursion, one map: the block's step-table entries and
+// Restarted FP32 recursion, one spin-0 map: the block's step-table entries and
 // prepared coefficients are loaded together before its 8 steps, so their
-// latency is paid once per block instead of once per degree.
+// latency is paid once per block instead of once per degree (spin s: the
+// 16 more coefficient registers cost as much as the latency saves).
 template <class P, int RPT, bool SPIN, int REG>
 __device__ __forceinline__ void fwd_block_pf(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, 1, false> &acc,
                                              const float4 *reca, const float2 *ca, const float2 *cb, int lb)
@@ -294,7 +295,7 @@ __device__ __forceinline__ void leg_fwd_body(const void *__restrict__ coef, cons
         }
         const int reg = st.regime();
         acc.renorm();
-        if constexpr (P::kRestart && NM == 1 && !GRAD) {
+        if constexpr (P::kRestart && NM == 1 && !GRAD && !SPIN) {  // lmax 4096: 4.52 -> 4.40 ms; spin s gains nothing
             const float2 *ca = (const float2 *)coef + base;
             const float2 *cb = (const float2 *)coef + nalm + base;
             if (reg == 0) fwd_block_pf<P, RPT, SPIN, 0>(st, acc, (const float4 *)reca, ca, cb, l);

@@ -401,8 +401,16 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         const bool f64 = prec == LENS_FP64;
         const double pts = (double)npoints * ncomp * ((double)W * W + (f64 ? 0.0 : 16.0 * W));
         const size_t nmax = std::max<size_t>(N1, N2);
-        const double clf = nmax > 2 * fft_one ? 2.0 : nmax > fft_one ? 1.5 : 1.0;
-        const double cell_w = f64 ? 60.0 : 12.0;
+        double clf = nmax > 2 * fft_one ? 2.0 : nmax > fft_one ? 1.5 : 1.0;
+        // FP32 plans at epsilon >= 1e-5 spread through 32-bit fixed-point tiles (half the tap
+        // cost of the float tiles): a grid cell then weighs ~32 taps (lmax 4096 stage times,
+        // 50M points: sigma 1.5 / W 8 beats sigma 2.26 / W 6 by 3 ms per T + E/B pair); vectors
+        // too long for two CTAs per SM (about 14k FP32 elements) run 1.3x slower per cell.
+        // LENS_DETERMINISTIC plans take the same sigma, so that they match the atomic path
+        // to rounding
+        const bool fx32 = !f64 && epsilon >= 1e-5;
+        if (fx32 && nmax * esz > 110000) clf *= 1.3;
+        const double cell_w = f64 ? 60.0 : fx32 ? 32.0 : 12.0;
         const double grd = clf * (cell_w * ncomp * (double)N1 * 0.5 * N2 + 3.0 * (double)p->ncol * N1);
         const double cost = pts + grd;
         if (cost < best.cost) { best.cost = cost; best.sigma = sg; best.W = W; best.N1 = N1; best.N2 = N2; }

@@ -73,8 +73,8 @@ template <> __device__ __forceinline__ Buf<double2, 4> make_buf<double2, 4>(doub
 // with one (no CTA exits while a partner may still read its part).
 
 // ----------------------------------------------------------------- theta fwd
-template <typename T, int CL>
-__global__ void __launch_bounds__(512) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
+template <typename T, int CL, int OCC = 1>
+__global__ void __launch_bounds__(512, OCC) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
                                                     int spin, int ncol, int r_lo, int R, int chunk)
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(512) k_theta_coeffs(const cplx<T> *__restrict_
 }
 
 // ----------------------------------------------------------------- theta adj
-template <typename T, int CL>
-__global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
+template <typename T, int CL, int OCC = 1>
+__global__ void __launch_bounds__(512, OCC) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
                                                     const T *__restrict__ w2, int ntheta, int lmax, int mmax,
                                                     int spin, int ncol, int r_lo, int R, int chunk)
@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(512) k_theta_adj(const cplx<T> *__restrict__ X
 
 // ------------------------------------------------------------------- phi fwd
 // spin 0: team = row pair (2b, 2b+1); spin s: team = one row.
-template <typename T, bool SPIN, int CL>
-__global__ void __launch_bounds__(512) k_phi_fwd(const cplx<T> *__restrict__ X, void *__restrict__ grid,
+template <typename T, bool SPIN, int CL, int OCC = 1>
+__global__ void __launch_bounds__(512, OCC) k_phi_fwd(const cplx<T> *__restrict__ X, void *__restrict__ grid,
                                                  FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk)
 {
     using C = cplx<T>;
@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(512) k_phi_fwd(const cplx<T> *__restrict__ X, 
 }
 
 // ------------------------------------------------------------------- phi adj
-template <typename T, bool SPIN, int CL>
-__global__ void __launch_bounds__(512) k_phi_adj(const void *__restrict__ grid, cplx<T> *__restrict__ X,
+template <typename T, bool SPIN, int CL, int OCC = 1>
+__global__ void __launch_bounds__(512, OCC) k_phi_adj(const void *__restrict__ grid, cplx<T> *__restrict__ X,
                                                  FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk)
 {
     using C = cplx<T>;
@@ -336,6 +336,12 @@ namespace {
 
 constexpr int kThetaThreads = 512;
 int phi_threads(const Plan &p) { return p.prec == LENS_FP32 ? 512 : 256; }
+// Two 512-thread CTAs per SM need at most 64 registers per thread and half the
+// SM's shared memory each; FP32 single-CTA vectors that fit then run the
+// variant compiled for two CTAs per SM (measured at lmax 4096, sigma 1.5:
+// theta 0.82 -> 0.68 ms, phi 0.35 -> 0.29 ms spin 0; at sigma 2.26, where one
+// vector takes 148 KB, the cap only adds spills).
+constexpr size_t kTwoCtaSmem = 113 * 1024;
 
 // Launches nvec teams of cl CTAs (a cluster of two when cl = 2).
 template <class... KArgs, class... Args>
@@ -370,6 +376,8 @@ cudaError_t theta_fwd_t(const Plan &p, const void *ring, void *X, cudaStream_t s
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
+    if constexpr (sizeof(T) == 4)
+        if (p.cl_theta == 1 && sm <= kTwoCtaSmem) return args(k_theta_fwd<T, 1, 2>);
     return p.cl_theta == 4 ? args(k_theta_fwd<T, 4>) : p.cl_theta == 2 ? args(k_theta_fwd<T, 2>) : args(k_theta_fwd<T, 1>);
 }
 
@@ -384,6 +392,8 @@ cudaError_t theta_adj_t(const Plan &p, const void *X, void *ring, cudaStream_t s
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
+    if constexpr (sizeof(T) == 4)
+        if (p.cl_theta == 1 && sm <= kTwoCtaSmem) return args(k_theta_adj<T, 1, 2>);
     return p.cl_theta == 4 ? args(k_theta_adj<T, 4>) : p.cl_theta == 2 ? args(k_theta_adj<T, 2>) : args(k_theta_adj<T, 1>);
 }
 
@@ -398,6 +408,8 @@ cudaError_t phi_fwd_t(const Plan &p, const void *X, void *grid, cudaStream_t st)
         return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const C *)X, grid, p.fN2, p.mmax, p.ncol,
                            p.R, p.pitch, p.W, chunk);
     };
+    if constexpr (sizeof(T) == 4)
+        if (p.cl_phi == 1 && sm <= kTwoCtaSmem) return args(k_phi_fwd<T, SPIN, 1, 2>);
     return p.cl_phi == 4   ? args(k_phi_fwd<T, SPIN, 4>)
            : p.cl_phi == 2 ? args(k_phi_fwd<T, SPIN, 2>)
                            : args(k_phi_fwd<T, SPIN, 1>);
@@ -414,6 +426,8 @@ cudaError_t phi_adj_t(const Plan &p, const void *grid, void *X, cudaStream_t st)
         return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const void *)grid, (C *)X, p.fN2, p.mmax,
                            p.ncol, p.R, p.pitch, p.W, chunk);
     };
+    if constexpr (sizeof(T) == 4)
+        if (p.cl_phi == 1 && sm <= kTwoCtaSmem) return args(k_phi_adj<T, SPIN, 1, 2>);
     return p.cl_phi == 4   ? args(k_phi_adj<T, SPIN, 4>)
            : p.cl_phi == 2 ? args(k_phi_adj<T, SPIN, 2>)
                            : args(k_phi_adj<T, SPIN, 1>);
