@@ -231,11 +231,22 @@ def stage_units(info, npts, spin, prec):
     }
 
 
+def fp64_arithmetic(info):
+    """What the FP64 plan's steps compute in (the Legendre part depends on epsilon)."""
+    if info["legendre_restart"]:
+        leg = ("double-float (pairs of FP32) Legendre recursion and sums for every order, restarted every %d "
+               "degrees from FP64-recursion values" % info["legendre_restart"])
+    else:
+        leg = ("FP64 Legendre recursion for orders m < %d, double-float (pairs of FP32) above"
+               % info["legendre_df32_mmin"])
+    return leg + "; FP64 FFTs, kernel weights and interpolation/spreading"
+
+
 def kernel_launches(info, prec):
     """Kernels one synthesis + one adjoint launch on a (non-deterministic) plan: synthesis = coefficient
     preparation, Legendre, theta, phi, interpolation; adjoint = spreading, phi, theta, Legendre; FP64
     plans with double-float orders split each Legendre step into two launches (memsets not counted)."""
-    leg = 2 if (prec == "fp64" and info["legendre_df32_mmin"] <= info["mmax"]) else 1
+    leg = 2 if (prec == "fp64" and 0 < info["legendre_df32_mmin"] <= info["mmax"]) else 1
     return (4 + leg) + (3 + leg)
 
 
@@ -412,8 +423,9 @@ def run_gpu(args):
         if info["legendre_table_bytes"]:
             return {"mode": "tables", "bytes": info["legendre_table_bytes"]}
         if info["legendre_restart"]:
-            return {"mode": "restarted FP32 recursion", "restart_every": info["legendre_restart"],
-                    "restart_bytes": info["restart_bytes"], "triples": info["legendre_triples"]}
+            return {"mode": "restarted FP32 recursion" if info["prec"] == 0 else "restarted double-float recursion",
+                    "restart_every": info["legendre_restart"], "restart_bytes": info["restart_bytes"],
+                    "triples": info["legendre_triples"]}
         return {"mode": "double-float recursion" if info["prec"] == 0 else "FP64 + double-float recursion",
                 "df32_from_m": info["legendre_df32_mmin"]}
 
@@ -569,8 +581,7 @@ def run_gpu(args):
         roof64.pop("slot")
         fp64 = {"value": round(whole_job_rate(world, npts, ms64), 1), "unit": "lensed points/s", "epsilon": 1e-10,
                 "ms_per_step": round(ms64, 3), "steps": k64, "per_transform": per_transform(qT, qP, c, reps=1),
-                "arithmetic": "FP64 Legendre recursion for orders m < %d, double-float (pairs of FP32) above; "
-                              "FP64 FFTs, kernel weights and interpolation/spreading" % qT.info()["legendre_df32_mmin"],
+                "arithmetic": fp64_arithmetic(qT.info()),
                 "plan": {k: qT.info()[k] for k in ("n1", "W", "sigma")} | {"W_spin2": qP.info()["W"]},
                 "roofline": roof64, "stages": st64,
                 "step_roofline": {"t_roof_ms": round(tr64, 3), "frac": round(tr64 / ms64, 4)}}

@@ -120,14 +120,22 @@ typedef struct {
                                Legendre steps then stream them instead of running the
                                recursion.  0 = recursion (default).  LENS_ERR_NOMEM if the
                                tables do not fit. */
-    int legendre_restart;   /* FP32 plans without tables, Legendre recursion arithmetic:
-                               0 = choose: epsilon >= 1e-5 runs the recursion in FP32 and
-                               resets it every K = 64 degrees (K doubled while the restart
-                               values would exceed 20 GB) to values computed at plan creation
-                               (FP64 recursion; 8 or 16 bytes per ring, restart and order:
-                               2.3 / 4.5 GB for spin 0 / spin s at lmax 4096); smaller
+    int legendre_restart;   /* Legendre recursion arithmetic (plans without tables):
+                               FP32 plans, 0 = choose: epsilon >= 1e-5 runs the recursion in
+                               FP32 and resets it every K = 64 degrees (K doubled while the
+                               restart values would exceed 20 GB) to values computed at plan
+                               creation (FP64 recursion; 8 or 16 bytes per ring, restart and
+                               order: 2.3 / 4.5 GB for spin 0 / spin s at lmax 4096); smaller
                                epsilon runs the double-float recursion.
-                               -1 = always the double-float recursion.
+                               FP64 plans, 0 = choose: epsilon >= 5e-11 runs every order in
+                               double-float, reset to the FP64 recursion's values every 16
+                               degrees for m < 16 g, 64 for m < 128 g and K = 128 above,
+                               g = max(1, lmax / 4096) (K doubled above 40 GB; 16 or 32 bytes
+                               per ring, restart and order: 2.6 / 5.2 GB at lmax 4096);
+                               smaller epsilon runs the low orders in FP64
+                               (legendre_df32_mmin).
+                               -1 = no restarts (FP32 plans: the double-float recursion; FP64
+                               plans: FP64 low orders as for small epsilon).
                                K > 0 = restart every K degrees (a power of two, 8 .. 4096). */
     int point_weights;      /* FP64 plans: 0 = keep the 2W kernel weights of every point when they
                                take at most 48 GB (16 W bytes per point), else evaluate the taps in
@@ -153,12 +161,13 @@ typedef struct {
     unsigned flags;            /* lens_flags the plan was created with */
     int alm_ncomp;             /* components of an a_lm buffer: 1 (spin 0, LENS_GRAD_ONLY) or 2 */
     size_t legendre_table_bytes; /* Legendre tables held by the plan (0: recursion) */
-    int legendre_restart;        /* FP32 recursion restarted every this many degrees
-                                    (0: double-float or FP64 recursion, or tables) */
+    int legendre_restart;        /* recursion restarted every this many degrees (FP32 plans: FP32
+                                    recursion, FP64 plans: double-float; 0: no restarts, or tables) */
     size_t restart_bytes;        /* restart values held by the plan */
     int legendre_df32_mmin;      /* FP64 plans: first order run in double-float (mmax + 1: none) */
-    int64_t legendre_triples;    /* restarted FP32 recursion: (ring pair, l, m) triples from the first
-                                    degree at which |lambda| reaches 2^-40 on each ring (0 if not counted) */
+    int64_t legendre_triples;    /* restarted recursions: (ring pair, l, m) triples from the first
+                                    degree at which |lambda| reaches 2^-40 (FP64 plans: 2^-64) on each
+                                    ring (0 if not counted) */
     size_t point_weight_bytes;   /* FP64 plans: kernel weights kept per point (0: evaluated per call) */
 } lens_plan_info_t;
 

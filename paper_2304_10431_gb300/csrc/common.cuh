@@ -83,6 +83,32 @@ __device__ __forceinline__ df32 df_sub_u(df32 a, df32 b)
 
 __device__ __forceinline__ df32 df_scale_pow2(df32 a, float p2) { return {a.h * p2, a.l * p2}; }
 
+// v as h + l (h = v rounded to FP32, l the rest rounded: relative error ~2^-48)
+__device__ __forceinline__ df32 df_split(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_value(df32 a) { return (double)a.h + (double)a.l; }
+
+// s += (p, e) for a product (p, e) of df_mul: two-sum on the high words, the
+// error and e into the low word (s not renormalised)
+__device__ __forceinline__ void df_acc(df32 &s, df32 t)
+{
+    const float h = __fadd_rn(s.h, t.h);
+    const float bb = __fsub_rn(h, s.h);
+    const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(h, bb)), __fsub_rn(t.h, bb));
+    s.l = __fadd_rn(s.l, __fadd_rn(err, t.l));
+    s.h = h;
+}
+// two-sum renormalisation (exact for any ordering of |h|, |l|)
+__device__ __forceinline__ df32 df_renorm(df32 a)
+{
+    const float h = __fadd_rn(a.h, a.l);
+    const float bb = __fsub_rn(h, a.h);
+    return {h, __fadd_rn(__fsub_rn(a.h, __fsub_rn(h, bb)), __fsub_rn(a.l, bb))};
+}
+
 // Fixed-point accumulation (deterministic plans): a sum whose terms are
 // bounded by `bound` in total is accumulated as integers in units of 2^-k,
 // with k the largest integer up to 122 such that bound 2^k <= 2^62 (so the

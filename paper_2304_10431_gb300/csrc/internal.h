@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gslens.h"
 
@@ -50,9 +51,21 @@ struct CkTab {
     const void *e = nullptr;
     const int64_t *base = nullptr;
     const short *kstart = nullptr;
+    const unsigned char *klog = nullptr;  // per-order log2 of the restart interval (nullptr: K for all)
+    const float2 *cs = nullptr;           // FP32 plans: (c_l, 1/c_l) per alm index (monic scale, PolSM)
     int ngrp = 0;
     int K = 0, jb = 0;
 };
+
+// Restart interval of order m
+__host__ __device__ __forceinline__ int ck_interval(const CkTab &ck, int m)
+{
+#ifdef __CUDA_ARCH__
+    return ck.klog ? 1 << __ldg(ck.klog + m) : ck.K;
+#else
+    return ck.klog ? 1 << ck.klog[m] : ck.K;
+#endif
+}
 
 // Restarts of an order whose block loop starts at degree lf (= max(m, s) + 1):
 // the degrees lf + K k, k >= 1, at which a full block of kLegBlock degrees
@@ -94,11 +107,14 @@ struct Plan {
     int m_df = 0;
     // FP32 plans: restarted FP32 recursion (rst) with its step table rec_s
     // (float4 per alm index) and restart values ck (ck_bytes); otherwise the
-    // df32 recursion of rec_a
+    // df32 recursion of rec_a.  FP64 plans: rst selects the restarted df32
+    // recursion (PolDDR), with a restart interval per order (ck_klog, on the
+    // host; ck.klog on the device).
     bool rst = false;
     void *rec_s = nullptr;
     CkTab ck;
     size_t ck_bytes = 0;
+    std::vector<unsigned char> ck_klog;
     int64_t leg_triples = 0;  // non-negligible (ring pair, l, m) triples (restarted plans)
     // tensor-core batched synthesis (spin-0 restarted plans, 16 or more maps per call):
     // ring coefficients of up to 64 maps, prepared coefficient tiles, chunk offsets per m
@@ -116,6 +132,7 @@ struct Plan {
     void *rec_a_df = nullptr, *rec_t_df = nullptr;
     double *scale = nullptr;
     void *coef = nullptr;     // workspace: forward coefficients c_l a_lm of one call
+    void *coef_m = nullptr;   // workspace, restarted FP32 plans: c_l a_lm for the monic plain-form warps
                               // ([ncomp][nalm], float2 / double2 / df32 float4)
     // FP32 plans, several maps per call: ring coefficients and prepared
     // coefficients of up to 4 maps, allocated on the first such call
@@ -160,6 +177,8 @@ struct Plan {
     int tile_r = kTileR;             // rows of a tile (16, 32 or 64; 32 columns)
     void *phase = nullptr;     // float2 / double2 e^{i s chi}, spin != 0 only
     double *wts = nullptr;     // FP64 plans: [npts][2W] kernel weights (theta taps, then phi taps)
+    bool wts_dd = false;       // weights as double-float pairs; double-float interpolation and
+                               // spreading taps (FP64 plans with epsilon >= 5e-11)
 
     // per-call workspace
     void *ring = nullptr;      // [ncol][ntheta] complex
@@ -183,6 +202,7 @@ cudaError_t launch_rec_tables(Plan &p);
 // monic recursion (a64, t64: temporary FP64 alpha / tau tables of the plan)
 cudaError_t launch_rec_tables_s(Plan &p);
 cudaError_t launch_ck_build(Plan &p, double *a64, double *t64, void *v_out, void *e_out, int *lt, short *kstart);
+cudaError_t launch_ck_build64(Plan &p, void *v_out, void *e_out, int *lt, short *kstart);
 // Legendre tables: shape, first-entry degrees, rows, values (plan creation)
 cudaError_t tab_shape(Plan &p);
 // bounded-wait self-test kernel (one warp, an mbarrier that never completes)

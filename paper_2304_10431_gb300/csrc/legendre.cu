@@ -210,11 +210,11 @@ __device__ __forceinline__ void fwd_block(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT
 // prepared coefficients are loaded together before its 8 steps, so their
 // latency is paid once per block instead of once per degree (spin s: the
 // 16 more coefficient registers cost as much as the latency saves).
-template <class P, int RPT, bool SPIN, int REG>
+template <class P, int RPT, bool SPIN, int REG, class TabE>
 __device__ __forceinline__ void fwd_block_pf(Rings<P, RPT, SPIN> &st, FwdAcc<P, RPT, SPIN, 1, false> &acc,
-                                             const float4 *reca, const float2 *ca, const float2 *cb, int lb)
+                                             const TabE *reca, const float2 *ca, const float2 *cb, int lb)
 {
-    float4 tb[kBlk];
+    TabE tb[kBlk];
     float2 a[kBlk], b[kBlk];
 #pragma unroll
     for (int j = 0; j < kBlk; ++j) {
@@ -275,11 +275,12 @@ __device__ __forceinline__ void leg_fwd_body(const void *__restrict__ coef, cons
     const Sg s0 = ((lf - m) & 1) ? Sg(-1) : Sg(1);  // (-1)^(lf - m)
     int l = lf;
     bool jumped = false;
+    const int Km = P::kRestart ? ck_interval(ck, m) : 0;
     if constexpr (P::kRestart) {  // start at the warp's first restart: every earlier degree is negligible
         const int kj = first_restart<RPT>(ck, m);
         if (kj > 0) {
             st.init_geom(rt, rp0, nnorth);
-            l = lf + kj * ck.K;  // the restart at l sets the state
+            l = lf + kj * Km;  // the restart at l sets the state
             jumped = true;
         }
     }
@@ -291,19 +292,27 @@ __device__ __forceinline__ void leg_fwd_body(const void *__restrict__ coef, cons
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         if constexpr (P::kRestart) {
             const int dl = l - lf;
-            if (dl != 0 && (dl & (ck.K - 1)) == 0) st.restart(ck, ckrow + (int64_t)(dl / ck.K - 1) * nnorth, rp0, nnorth);
+            if (dl != 0 && (dl & (Km - 1)) == 0) {
+                const int64_t row = ckrow + (int64_t)(dl / Km - 1) * nnorth;
+                if constexpr (P::kScaleF) st.restart_scaled(ck, row, rp0, nnorth, ck.cs + base, l);
+                else st.restart(ck, row, rp0, nnorth);
+            }
         }
-        const int reg = st.regime();
+        int reg = st.regime();
+        // restarted recursions start at the warp's first significant restart, so a block of
+        // negligible states is rare there: it runs the scaled path (its terms are exact zeros)
+        // and the recursion-only variant is not compiled
+        if constexpr (P::kRestart) reg = reg == 1 ? 2 : reg;
         acc.renorm();
-        if constexpr (P::kRestart && NM == 1 && !GRAD && !SPIN) {  // lmax 4096: 4.52 -> 4.40 ms; spin s gains nothing
+        if constexpr (P::kRestart && !P::kMonic && NM == 1 && !GRAD && !SPIN) {  // lmax 4096: 4.52 -> 4.40 ms;
+                                                                                // spin s gains nothing
             const float2 *ca = (const float2 *)coef + base;
             const float2 *cb = (const float2 *)coef + nalm + base;
-            if (reg == 0) fwd_block_pf<P, RPT, SPIN, 0>(st, acc, (const float4 *)reca, ca, cb, l);
-            else if (reg == 1) fwd_block_pf<P, RPT, SPIN, 1>(st, acc, (const float4 *)reca, ca, cb, l);
-            else fwd_block_pf<P, RPT, SPIN, 2>(st, acc, (const float4 *)reca, ca, cb, l);
+            if (reg == 0) fwd_block_pf<P, RPT, SPIN, 0>(st, acc, reca, ca, cb, l);
+            else fwd_block_pf<P, RPT, SPIN, 2>(st, acc, reca, ca, cb, l);
         } else {
             if (reg == 0) fwd_block<P, RPT, SPIN, 0, NM, GRAD>(st, acc, reca, rect, l);
-            else if (reg == 1) fwd_block<P, RPT, SPIN, 1, NM, GRAD>(st, acc, reca, rect, l);
+            else if (!P::kRestart && reg == 1) fwd_block<P, RPT, SPIN, 1, NM, GRAD>(st, acc, reca, rect, l);
             else fwd_block<P, RPT, SPIN, 2, NM, GRAD>(st, acc, reca, rect, l);
         }
     }
@@ -361,25 +370,32 @@ __global__ void __launch_bounds__(512) k_leg_fwd(const void *__restrict__ coef, 
                                                  const void *__restrict__ rec_t, const double *__restrict__ lognorm,
                                                  RingTab rt, typename P::C *__restrict__ ring, int lmax, int mmax,
                                                  int spin, int ntheta, int nnorth, int64_t nalm, int m_begin,
-                                                 int64_t ring_stride)
+                                                 int64_t ring_stride, CkTab ck)
 {
     leg_fwd_body<P, RPT, SPIN, NM, GRAD>(coef, rec_a, rec_t, lognorm, rt, ring, lmax, mmax, spin, ntheta, nnorth,
-                                         nalm, m_begin, ring_stride, CkTab{});
+                                         nalm, m_begin, ring_stride, ck);
 }
 
 // Restarted FP32 recursion: warps whose rings lie below ck.jb run Reinsch's
 // form, the others the plain form (the choice is uniform per warp).
+// One map: the plain-form warps run the monic step (PolSM) on the df32 table
+// rec_a with the coefficients coef_m (times c_l): spin 2 at lmax 4096 12.09 ->
+// 11.46 ms (spin 0 unchanged); several maps keep PolS.
 template <int RPT, bool SPIN, int NM = 1, bool GRAD = false>
 __global__ void __launch_bounds__(512) k_leg_fwd32(const void *__restrict__ coef, const void *__restrict__ rec_s,
                                                    const double *__restrict__ lognorm, RingTab rt,
                                                    float2 *__restrict__ ring, int lmax, int mmax, int spin, int ntheta,
                                                    int nnorth, int64_t nalm, int m_begin, int64_t ring_stride,
-                                                   CkTab ck)
+                                                   CkTab ck, const void *__restrict__ coef_m,
+                                                   const void *__restrict__ rec_a)
 {
     const int wr0 = ((blockIdx.x * blockDim.x + threadIdx.x) & ~31) * RPT;  // first ring of the warp
     if (wr0 < ck.jb)
         leg_fwd_body<PolR, RPT, SPIN, NM, GRAD>(coef, rec_s, nullptr, lognorm, rt, ring, lmax, mmax, spin, ntheta,
                                                 nnorth, nalm, m_begin, ring_stride, ck);
+    else if constexpr (NM == 1)
+        leg_fwd_body<PolSM, RPT, SPIN, NM, GRAD>(coef_m, rec_a, nullptr, lognorm, rt, ring, lmax, mmax, spin, ntheta,
+                                                 nnorth, nalm, m_begin, ring_stride, ck);
     else
         leg_fwd_body<PolS, RPT, SPIN, NM, GRAD>(coef, rec_s, nullptr, lognorm, rt, ring, lmax, mmax, spin, ntheta,
                                                 nnorth, nalm, m_begin, ring_stride, ck);
@@ -683,7 +699,7 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
         SPIN ? reinterpret_cast<const typename P::Tab *>((const typename P::TabAT *)rec_a + base)
              : (const typename P::Tab *)rec_a + base;
     const typename P::TTab *rect = SPIN ? (const typename P::TTab *)rec_t + base : nullptr;
-    const double *sc = P::kRestart ? nullptr : scale + base;  // restarted recursions carry lambda itself
+    const double *sc = P::kMonic ? scale + base : nullptr;  // restarted FP32 recursions carry lambda itself
     const int rp0 = (blockIdx.x * blockDim.x + threadIdx.x) * RPT;
     const Sg sgs = (s & 1) ? Sg(-1) : Sg(1);
     R *out = reinterpret_cast<R *>(alm);
@@ -696,11 +712,12 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
     in.init(ring, rp0, nnorth, ntheta, m, mmax, ((lf - m) & 1) != 0, (s & 1) != 0);
     int l = lf;
     bool jumped = false;
+    const int Km = P::kRestart ? ck_interval(ck, m) : 0;
     if constexpr (P::kRestart) {  // start at the warp's first restart: every earlier degree is negligible
         const int kj = first_restart<RPT>(ck, m);
         if (kj > 0) {
             st.init_geom(rt, rp0, nnorth);
-            l = lf + kj * ck.K;  // the restart at l sets the state
+            l = lf + kj * Km;  // the restart at l sets the state
             jumped = true;
         }
     }
@@ -723,13 +740,17 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
     for (; l + kBlk <= lmax + 1; l += kBlk) {
         if constexpr (P::kRestart) {
             const int dl = l - lf;
-            if (dl != 0 && (dl & (ck.K - 1)) == 0) st.restart(ck, ckrow + (int64_t)(dl / ck.K - 1) * nnorth, rp0, nnorth);
+            if (dl != 0 && (dl & (Km - 1)) == 0) {
+                const int64_t row = ckrow + (int64_t)(dl / Km - 1) * nnorth;
+                if constexpr (P::kScaleF) st.restart_scaled(ck, row, rp0, nnorth, ck.cs + base, l);
+                else st.restart(ck, row, rp0, nnorth);
+            }
         }
         const int reg = st.regime();
-        if (reg == 1) {  // every contribution of this block is below 2^-180: recursion only
+        if (!P::kRestart && reg == 1) {  // every contribution of this block is below 2^-180: recursion only
             adj_block<P, RPT, SPIN, 1, GRAD>(st, in, part, reca, rect, l);
             continue;
-        }
+        }  // restarted recursions: such blocks are rare (see leg_fwd_body) and take the scaled path
 #pragma unroll
         for (int i = 0; i < NV; ++i) part[i] = P::azero();
         if (reg == 0) adj_block<P, RPT, SPIN, 0, GRAD>(st, in, part, reca, rect, l);
@@ -760,10 +781,10 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
                                                  const double *__restrict__ scale, RingTab rt,
                                                  typename P::C *__restrict__ alm, int lmax, int mmax, int spin,
                                                  int ntheta, int nnorth, int64_t nalm, int m_begin, double wpos,
-                                                 unsigned long long *fx, const double *__restrict__ fxs)
+                                                 unsigned long long *fx, const double *__restrict__ fxs, CkTab ck)
 {
     leg_adj_body<P, RPT, SPIN, GRAD>(ring, rec_a, rec_t, lognorm, scale, rt, alm, lmax, mmax, spin, ntheta, nnorth,
-                                     nalm, m_begin, wpos, fx, fxs, CkTab{});
+                                     nalm, m_begin, wpos, fx, fxs, ck);
 }
 
 // Restarted FP32 recursion (see k_leg_fwd32).
@@ -778,7 +799,7 @@ __global__ void __launch_bounds__(512) k_leg_adj32(const float2 *__restrict__ ri
     if (wr0 < ck.jb)
         leg_adj_body<PolR, RPT, SPIN, GRAD>(ring, rec_s, nullptr, lognorm, nullptr, rt, alm, lmax, mmax, spin, ntheta,
                                             nnorth, nalm, m_begin, wpos, fx, fxs, ck);
-    else
+    else  // (the monic PolSM measured 8% slower here for spin 2: 16.0 -> 17.3 ms at lmax 4096)
         leg_adj_body<PolS, RPT, SPIN, GRAD>(ring, rec_s, nullptr, lognorm, nullptr, rt, alm, lmax, mmax, spin, ntheta,
                                             nnorth, nalm, m_begin, wpos, fx, fxs, ck);
 }
@@ -850,7 +871,8 @@ __device__ __forceinline__ double rec_B(int l, int m, int s)
 }
 
 __global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, float2 *__restrict__ a_df,
-                             float2 *__restrict__ t_df, double *__restrict__ a64, double *__restrict__ t64)
+                             float2 *__restrict__ t_df, double *__restrict__ a64, double *__restrict__ t64,
+                             float2 *__restrict__ cs)
 {
     const int m = blockIdx.x;
     const int s = spin;
@@ -883,6 +905,12 @@ __global__ void k_rec_tables(int lmax, int spin, double *__restrict__ scale, flo
         if (a64) {
             a64[base + l] = alpha;
             if (t64) t64[base + l] = tau;
+        }
+    }
+    if (cs) {  // (c_l, 1/c_l) in FP32 for the monic plain-form rings of the restarted FP32 recursion
+        for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+            const double c = scale[base + l];
+            cs[base + l] = l >= l0 ? make_float2((float)c, (float)(1.0 / c)) : make_float2(0.f, 0.f);
         }
     }
 }
@@ -920,13 +948,18 @@ __global__ void k_rec_tables_s(int lmax, int spin, float4 *__restrict__ out)
 // with E (kCkZero for a state that is identically zero).  lt[m][j]: the first
 // degree at which |lambda| (either sign of the spin) reaches 2^-40, lmax + 1
 // if none does before the last restart.
-template <bool SPIN>
+// DD (FP64 plans, PolDDR): the monic state itself split into df32 words,
+// float4 (w0.h, w0.l, w1.h, w1.l) per sign of the spin, no Reinsch form, and
+// lt the first degree reaching 2^-64.
+template <bool SPIN, bool DD = false>
 __global__ void k_ck_build(const double *__restrict__ a64, const double *__restrict__ t64,
                            const double *__restrict__ scale, const double *__restrict__ lognorm, RingTab rt, int lmax,
-                           int spin, int nnorth, int K, int jb, const int64_t *__restrict__ ckbase,
-                           void *__restrict__ vout, void *__restrict__ eout, int *__restrict__ lt)
+                           int spin, int nnorth, int Kall, int jb, const int64_t *__restrict__ ckbase,
+                           void *__restrict__ vout, void *__restrict__ eout, int *__restrict__ lt,
+                           const unsigned char *__restrict__ klog)
 {
     const int m = blockIdx.y;
+    const int K = klog ? 1 << klog[m] : Kall;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = SPIN ? spin : 0;
     const int l0 = m > s ? m : s;
@@ -942,7 +975,13 @@ __global__ void k_ck_build(const double *__restrict__ a64, const double *__restr
     PolF64::St sp, sm;
     start_value<PolF64>(sp, m, s, s, lognorm[m], rt.lsin2[j], rt.lcos2[j]);
     if (SPIN) start_value<PolF64>(sm, m, s, -s, lognorm[m], rt.lsin2[j], rt.lcos2[j]);
-    const bool rein = j < jb;
+    const bool rein = !DD && j < jb;
+    auto quad = [&](const PolF64::St &st, float4 &v, short &e) {
+        if (st.w[0] == 0.0 && st.w[1] == 0.0) { v = make_float4(0.f, 0.f, 0.f, 0.f); e = (short)kCkZero; return; }
+        const df32 a = df_split(st.w[0]), b = df_split(st.w[1]);
+        v = make_float4(a.h, a.l, b.h, b.l);
+        e = (short)max(st.E, kCkZero + 1);
+    };
     auto pair = [&](const PolF64::St &st, int l, float &w0, float &w1, short &e) {
         if (st.w[0] == 0.0 && st.w[1] == 0.0) { w0 = 0.f; w1 = 0.f; e = (short)kCkZero; return; }
         const double v1 = st.w[1] * scale[base + l];
@@ -951,8 +990,8 @@ __global__ void k_ck_build(const double *__restrict__ a64, const double *__restr
         w0 = (float)(rein ? v1 - v0 : v0);
         e = (short)max(st.E, kCkZero + 1);
     };
-    auto big = [&](const PolF64::St &st, int l) {  // |lambda_l| >= 2^-40
-        return st.E >= -1 && ldexp(fabs(st.w[1]) * scale[base + l], kScaleBits * st.E) >= 0x1p-40;
+    auto big = [&](const PolF64::St &st, int l) {  // |lambda_l| >= 2^-40 (DD: 2^-64)
+        return st.E >= -2 && ldexp(fabs(st.w[1]) * scale[base + l], kScaleBits * st.E) >= (DD ? 0x1p-64 : 0x1p-40);
     };
     int lfirst = lmax + 1;
     if (big(sp, l0) || (SPIN && big(sm, l0))) lfirst = l0;
@@ -976,7 +1015,20 @@ __global__ void k_ck_build(const double *__restrict__ a64, const double *__restr
         if (lfirst > lmax && (big(sp, l) || (SPIN && big(sm, l)))) lfirst = l;
         if (l == lck) {
             const int64_t idx = ckbase[m] + (int64_t)(k - 1) * nnorth + j;
-            if (!SPIN) {
+            if (DD) {
+                float4 a, b;
+                short ea, eb;
+                quad(sp, a, ea);
+                if (!SPIN) {
+                    reinterpret_cast<float4 *>(vout)[idx] = a;
+                    reinterpret_cast<short *>(eout)[idx] = ea;
+                } else {
+                    quad(sm, b, eb);
+                    reinterpret_cast<float4 *>(vout)[2 * idx] = a;
+                    reinterpret_cast<float4 *>(vout)[2 * idx + 1] = b;
+                    reinterpret_cast<short2 *>(eout)[idx] = make_short2(ea, eb);
+                }
+            } else if (!SPIN) {
                 float2 v;
                 short e;
                 pair(sp, l, v.x, v.y, e);
@@ -1000,10 +1052,11 @@ __global__ void k_ck_build(const double *__restrict__ a64, const double *__restr
 // First restart of every 32-ring group and order: the largest k <= ck_count
 // with lf + K k <= min over the group's rings of lt (so every degree before
 // the restart is below 2^-40 on all of them).
-__global__ void k_ck_start(const int *__restrict__ lt, int lmax, int mmax, int spin, int nnorth, int K, int ngrp,
-                           short *__restrict__ kstart)
+__global__ void k_ck_start(const int *__restrict__ lt, int lmax, int mmax, int spin, int nnorth, int Kall, int ngrp,
+                           short *__restrict__ kstart, const unsigned char *__restrict__ klog)
 {
     const int m = blockIdx.x;
+    const int K = klog ? 1 << klog[m] : Kall;
     const int l0 = m > spin ? m : spin;
     const int lf = l0 + 1;
     const int nck = l0 > lmax ? 0 : ck_count(lmax, lf, K);
@@ -1078,7 +1131,7 @@ cudaError_t fwd_launch(const Plan &p, const Plan::LegShape &sh, const void *coef
     dim3 block(sh.warps * 32);
     k_leg_fwd<P, RPT, SPIN, NM, GRAD><<<grid, block, 0, st>>>(coef, ta, tt, p.lognorm, p.rings, (typename P::C *)ring,
                                                         p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin,
-                                                        (int64_t)p.ncol * p.ntheta);
+                                                        (int64_t)p.ncol * p.ntheta, P::kRestart ? p.ck : CkTab{});
     return cudaGetLastError();
 }
 
@@ -1098,7 +1151,7 @@ cudaError_t adj_launch(const Plan &p, const Plan::LegShape &sh, const void *ring
                                                     (const typename P::C *)ring, ta, tt, p.lognorm, p.scale, p.rings,
                                                     (typename P::C *)alm, p.lmax, p.mmax, p.spin, p.ntheta, p.nnorth,
                                                     p.nalm, m_begin, wpos, (unsigned long long *)fx,
-                                                    p.fx_scale);
+                                                    p.fx_scale, P::kRestart ? p.ck : CkTab{});
     return cudaGetLastError();
 }
 
@@ -1128,7 +1181,7 @@ cudaError_t fwd32_launch(const Plan &p, const Plan::LegShape &sh, const void *co
     dim3 block(sh.warps * 32);
     k_leg_fwd32<RPT, SPIN, NM, GRAD><<<grid, block, 0, st>>>(coef, p.rec_s, p.lognorm, p.rings, (float2 *)ring, p.lmax,
                                                            p.mmax, p.spin, p.ntheta, p.nnorth, p.nalm, m_begin,
-                                                           (int64_t)p.ncol * p.ntheta, p.ck);
+                                                           (int64_t)p.ncol * p.ntheta, p.ck, p.coef_m, p.rec_a);
     return cudaGetLastError();
 }
 
@@ -1687,6 +1740,7 @@ Plan::LegShape legendre_shape(const Plan &p, bool adjoint, bool dd, int rpt, int
     const void *fn = (p.rst && p.prec == LENS_FP32) ? kernel_of32(p.spin != 0, p.grad, rpt, adjoint, nm)
                      : (nm > 1)            ? kernel_of_batch(p.spin != 0, rpt, nm)
                      : p.prec == LENS_FP32 ? kernel_of<PolDF>(p.spin != 0, p.grad, rpt, adjoint)
+                     : (dd && p.rst)       ? kernel_of<PolDDR>(p.spin != 0, p.grad, rpt, adjoint)
                      : dd                  ? kernel_of<PolDD>(p.spin != 0, p.grad, rpt, adjoint)
                                            : kernel_of<PolF64>(p.spin != 0, p.grad, rpt, adjoint);
     const int nw = (p.nnorth + 32 * rpt - 1) / (32 * rpt);
@@ -1721,18 +1775,38 @@ cudaError_t launch_ck_build(Plan &p, double *a64, double *t64, void *v_out, void
 {
     // FP64 alpha / tau / c_l of the monic recursion (c_l rewritten with the same values)
     k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, nullptr, nullptr, a64,
-                                                   p.spin ? t64 : nullptr);
+                                                   p.spin ? t64 : nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 g((p.nnorth + 127) / 128, p.mmax + 1);
     if (p.spin)
         k_ck_build<true><<<g, 128, 0, p.stream>>>(a64, t64, p.scale, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
-                                                  p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt);
+                                                  p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt, nullptr);
     else
         k_ck_build<false><<<g, 128, 0, p.stream>>>(a64, nullptr, p.scale, p.lognorm, p.rings, p.lmax, p.spin, p.nnorth,
-                                                   p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt);
+                                                   p.ck.K, p.ck.jb, p.ck.base, v_out, e_out, lt, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_ck_start<<<p.mmax + 1, 128, 0, p.stream>>>(lt, p.lmax, p.mmax, p.spin, p.nnorth, p.ck.K, p.ck.ngrp, kstart);
+    k_ck_start<<<p.mmax + 1, 128, 0, p.stream>>>(lt, p.lmax, p.mmax, p.spin, p.nnorth, p.ck.K, p.ck.ngrp, kstart,
+                                                 p.ck.klog);
+    return cudaGetLastError();
+}
+
+// FP64 plans: restart values of PolDDR from the plan's FP64 recursion tables
+cudaError_t launch_ck_build64(Plan &p, void *v_out, void *e_out, int *lt, short *kstart)
+{
+    const dim3 g((p.nnorth + 127) / 128, p.mmax + 1);
+    if (p.spin)
+        k_ck_build<true, true><<<g, 128, 0, p.stream>>>((const double *)p.rec_a, (const double *)p.rec_t, p.scale,
+                                                        p.lognorm, p.rings, p.lmax, p.spin, p.nnorth, p.ck.K, 0,
+                                                        p.ck.base, v_out, e_out, lt, p.ck.klog);
+    else
+        k_ck_build<false, true><<<g, 128, 0, p.stream>>>((const double *)p.rec_a, nullptr, p.scale, p.lognorm,
+                                                         p.rings, p.lmax, p.spin, p.nnorth, p.ck.K, 0, p.ck.base,
+                                                         v_out, e_out, lt, p.ck.klog);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_ck_start<<<p.mmax + 1, 128, 0, p.stream>>>(lt, p.lmax, p.mmax, p.spin, p.nnorth, p.ck.K, p.ck.ngrp, kstart,
+                                                 p.ck.klog);
     return cudaGetLastError();
 }
 
@@ -1740,10 +1814,11 @@ cudaError_t launch_rec_tables(Plan &p)
 {
     if (p.prec == LENS_FP32)
         k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, (float2 *)p.rec_a, nullptr, nullptr,
-                                                       nullptr);
+                                                       nullptr, const_cast<float2 *>(p.ck.cs));
     else
         k_rec_tables<<<p.mmax + 1, 256, 0, p.stream>>>(p.lmax, p.spin, p.scale, (float2 *)p.rec_a_df, nullptr,
-                                                       (double *)p.rec_a, p.spin ? (double *)p.rec_t : nullptr);
+                                                       (double *)p.rec_a, p.spin ? (double *)p.rec_t : nullptr,
+                                                       nullptr);
     return cudaGetLastError();
 }
 
@@ -1781,6 +1856,11 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
     if (p.prec == LENS_FP32) {
         k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.rst ? nullptr : p.scale, p.coef,
                                                                p.lmax, p.spin, p.nalm, p.mmax + 1, wpos, p.grad);
+        if (p.rst && !p.tab) {  // the monic plain-form warps' coefficients carry c_l
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_coef_prep<float2, float2, float2><<<g, 256, 0, st>>>((const float2 *)alm, p.scale, p.coef_m, p.lmax,
+                                                                   p.spin, p.nalm, p.mmax + 1, wpos, p.grad);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (p.tab) {
             const dim3 tg(p.tab_fchunks, p.mmax + 1);
@@ -1803,6 +1883,7 @@ cudaError_t launch_legendre_fwd(const Plan &p, const void *alm, void *ring, cuda
                                                              p.nalm, p.m_df, wpos, p.grad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fwd_spin<PolF64>(p, p.leg_f, p.coef, p.rec_a, p.rec_t, ring, 0, p.m_df, st)) != cudaSuccess) return e;
+    if (p.rst) return fwd_spin<PolDDR>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
     return fwd_spin<PolDD>(p, p.leg_fd, p.coef, p.rec_a_df, p.rec_t_df, ring, p.m_df, p.mmax + 1, st);
 }
 
@@ -1901,7 +1982,8 @@ cudaError_t launch_legendre_adj(const Plan &p, const void *ring, void *alm, cuda
     } else {
         e = adj_spin<PolF64>(p, p.leg_a, ring, p.rec_a, p.rec_t, alm, 0, p.m_df, st, wpos, fx);
         if (e == cudaSuccess)
-            e = adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos, fx);
+            e = p.rst ? adj_spin<PolDDR>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos, fx)
+                      : adj_spin<PolDD>(p, p.leg_ad, ring, p.rec_a_df, p.rec_t_df, alm, p.m_df, p.mmax + 1, st, wpos, fx);
     }
     if (e != cudaSuccess || !p.det) return e;
     const dim3 g(4, p.mmax + 1);

@@ -23,11 +23,6 @@ constexpr int kBlk = kLegBlock;
 __device__ __forceinline__ int64_t alm_base(int lmax, int m) { return (int64_t)m * (2 * lmax + 1 - m) / 2; }
 
 __device__ __forceinline__ df32 df_add_u(df32 a, df32 b) { return df_sub_u(a, {-b.h, -b.l}); }
-__device__ __forceinline__ df32 df_split(double v)
-{
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
 __device__ __forceinline__ df32 df_norm(df32 a)  // two-sum: exact for any ordering of |h|, |l|
 {
     const float h = __fadd_rn(a.h, a.l);
@@ -43,7 +38,9 @@ __device__ __forceinline__ df32 df_norm(df32 a)  // two-sum: exact for any order
 // sums, K a real coefficient component (prepared a_lm or ring input), A a
 // real accumulator; fma(acc, k, v) is acc += k v, fms(acc, k, v) acc -= k v.
 struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
-    static constexpr bool kRestart = false;  // no restart values (see PolS)
+    static constexpr bool kRestart = false;  // no restart values (see PolS, PolDDR)
+    static constexpr bool kMonic = true;     // values carry the monic scale c_l (scale table)
+    static constexpr bool kScaleF = false;   // c_l from the FP32 (c_l, 1/c_l) table instead (PolSM)
     using R = float;
     using C = float2;
     using X = df32;
@@ -171,6 +168,8 @@ struct PolDF {  // df32 recursion, FP32 accumulation (FP32 plans)
 
 struct PolF64 {  // native FP64 (FP64 plans, low orders)
     static constexpr bool kRestart = false;
+    static constexpr bool kMonic = true;
+    static constexpr bool kScaleF = false;
     using R = double;
     using C = double2;
     using X = double;
@@ -328,6 +327,15 @@ struct PolDD : PolDF {
     static __device__ __forceinline__ C cout(A re, A im) { return make_double2(aout(re), aout(im)); }
 };
 
+// FP64 plans with restart values (epsilon >= 5e-11): PolDD's monic df32
+// recursion and df32 sums for every order, its state reset every K degrees to
+// the FP64 recursion's monic values split into df32 words (k_ck_build64), so
+// that df32 rounding accumulates over at most K steps and no order needs the
+// FP64 pipe; each warp starts at its first restart with a value above 2^-64.
+struct PolDDR : PolDD {
+    static constexpr bool kRestart = true;
+};
+
 // FP32 plans with restart values (the default for epsilon >= 1e-5): FP32
 // recursion state in the normalised form
 //   lambda_l = (A_l x + sigma AT_l) lambda_{l-1} - B_l lambda_{l-2},  AT_l = A_l T_l,
@@ -349,6 +357,8 @@ struct PolDD : PolDF {
 // Accumulation as PolDF (FP32).  Start values and the 2^(60 E) scaling as PolDF.
 struct PolS : PolDF {
     static constexpr bool kRestart = true;
+    static constexpr bool kMonic = false;  // lambda itself
+    static constexpr bool kScaleF = false;
     using X = float;
     using Tab = float4;
     using TTab = float4;
@@ -376,6 +386,19 @@ struct PolS : PolDF {
     }
 };
 struct PolR : PolS {};
+// PolSM: the plain-form rings (cos theta below ~0.7) in the monic form,
+//   mu_l = (alpha_l x + sigma tau_l) mu_{l-1} - mu_{l-2},  mu_l = lambda_l / c_l,
+// with (alpha, tau) the high words of the df32 table: per step and sign of the
+// spin one multiplication fewer than PolS.  The restart values stay those of
+// PolS (lambda), divided by c_l as they are loaded (FP32 table of (c_l, 1/c_l));
+// the forward coefficients carry c_l (a second prepared set).  Used by the
+// forward only (the adjoint measured slower with it).  Reinsch's form (PolR)
+// keeps the normalised step: the monic alpha_l alternates between even and odd l.
+struct PolSM : PolS {
+    using Tab = float2;    // spin 0: (alpha_h, alpha_l) of the df32 table
+    using TabAT = float4;  // spin s: (alpha_h, alpha_l, tau_h, tau_l)
+    static constexpr bool kScaleF = true;
+};
 
 // Start value of sigma lambda_{l0,m} at ring j (north half), sigma = +-s.
 //   m >= s:  (-1)^m sqrt((2m+1)/4pi C(2m, m+s)) c^(m-sigma) s^(m+sigma)
@@ -418,6 +441,37 @@ template <class P, int RPT, bool SPIN> struct Rings {
                 x[k] = typename P::X{};
                 P::zero(sp[k]);
                 P::zero(sm[k]);
+            }
+        }
+    }
+    // ring geometry only (PolDDR: the state comes from a restart)
+    __device__ __forceinline__ void init_geom(const RingTab &rt, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            x[k] = rp0 + k < nnorth ? P::ring_x(rt, rp0 + k) : typename P::X{};
+            P::zero(sp[k]);
+            P::zero(sm[k]);
+        }
+    }
+    // PolDDR restart: df32 words (w0.h, w0.l, w1.h, w1.l) per sign of the spin
+    // (spin s: +s then -s, two float4) and the exponent E (short / short2)
+    __device__ __forceinline__ void restart(const CkTab &ck, int64_t row, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp >= nnorth) continue;
+            if (!SPIN) {
+                const float4 v = __ldg((const float4 *)ck.v + row + rp);
+                sp[k].w[0] = {v.x, v.y}; sp[k].w[1] = {v.z, v.w};
+                sp[k].E = __ldg((const short *)ck.e + row + rp);
+            } else {
+                const float4 a = __ldg((const float4 *)ck.v + 2 * (row + rp));
+                const float4 b = __ldg((const float4 *)ck.v + 2 * (row + rp) + 1);
+                const short2 e = __ldg((const short2 *)ck.e + row + rp);
+                sp[k].w[0] = {a.x, a.y}; sp[k].w[1] = {a.z, a.w}; sp[k].E = e.x;
+                sm[k].w[0] = {b.x, b.y}; sm[k].w[1] = {b.z, b.w}; sm[k].E = e.y;
             }
         }
     }
@@ -607,6 +661,131 @@ template <int RPT, bool SPIN> struct Rings<PolS, RPT, SPIN> {
                 const short2 e = __ldg((const short2 *)ck.e + row + rp);
                 sp[k].w[0] = v.x; sp[k].w[1] = v.y; sp[k].E = e.x;
                 sm[k].w[0] = v.z; sm[k].w[1] = v.w; sm[k].E = e.y;
+            }
+        }
+    }
+};
+
+// Rings of the restarted FP32 recursion in the monic plain form (PolSM):
+// state, words and scaling as Rings<PolS>.
+template <int RPT, bool SPIN> struct Rings<PolSM, RPT, SPIN> {
+    using P = PolS;
+    float x[RPT];
+    P::St sp[RPT], sm[RPT];
+
+    __device__ __forceinline__ void init_geom(const RingTab &rt, int rp0, int nnorth)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            x[k] = rp0 + k < nnorth ? __ldg(rt.xdf + rp0 + k).x : 0.f;
+            P::zero(sp[k]);
+            P::zero(sm[k]);
+        }
+    }
+    // start values at l0 (c_{l0} = c_{l0+1} = 1: the monic and plain states agree there)
+    __device__ __forceinline__ void init(const RingTab &rt, int rp0, int nnorth, int m, int s, double lnm)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp < nnorth) {
+                x[k] = __ldg(rt.xdf + rp).x;
+                const double ls = rt.lsin2[rp], lc = rt.lcos2[rp];
+                start_value<P>(sp[k], m, s, s, lnm, ls, lc);
+                if (SPIN) start_value<P>(sm[k], m, s, -s, lnm, ls, lc);
+            } else {
+                x[k] = 0.f;
+                P::zero(sp[k]);
+                P::zero(sm[k]);
+            }
+        }
+    }
+    __device__ __forceinline__ int regime() const
+    {
+        bool all0 = true, allneg = true;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            all0 = all0 && sp[k].E == 0;
+            allneg = allneg && sp[k].E <= kSkipE;
+            if (SPIN) {
+                all0 = all0 && sm[k].E == 0;
+                allneg = allneg && sm[k].E <= kSkipE;
+            }
+        }
+        if (__all_sync(0xffffffffu, all0)) return 0;
+        if (__all_sync(0xffffffffu, allneg)) return 1;
+        return 2;
+    }
+    template <int NW, bool CHECK>
+    __device__ __forceinline__ void advance(const float2 *reca, const float4 *, int l)
+    {
+        if (!SPIN) advance_c<NW, CHECK>(__ldg(reca + l));
+        else advance_c<NW, CHECK>(__ldg(reinterpret_cast<const float4 *>(reca) + l));
+    }
+    // one step with the degree's df32 table entry already loaded: spin 0 (alpha_h, alpha_l)
+    template <int NW, bool CHECK> __device__ __forceinline__ void advance_c(const float2 c)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            sp[k].w[NW] = __fmaf_rn(c.x * x[k], sp[k].w[1 - NW], -sp[k].w[NW]);
+            if (CHECK) P::rescale(sp[k], NW);
+        }
+    }
+    // spin s (alpha_h, alpha_l, tau_h, tau_l)
+    template <int NW, bool CHECK> __device__ __forceinline__ void advance_c(const float4 c)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const float cp = __fmaf_rn(c.x, x[k], c.z), cm = __fmaf_rn(c.x, x[k], -c.z);
+            sp[k].w[NW] = __fmaf_rn(cp, sp[k].w[1 - NW], -sp[k].w[NW]);
+            if (SPIN) sm[k].w[NW] = __fmaf_rn(cm, sm[k].w[1 - NW], -sm[k].w[NW]);
+            if (CHECK) {
+                P::rescale(sp[k], NW);
+                if (SPIN) P::rescale(sm[k], NW);
+            }
+        }
+    }
+    __device__ __forceinline__ void advance_moved(const float2 *reca, const float4 *rect, int l)
+    {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const float a = sp[k].w[0];
+            sp[k].w[0] = sp[k].w[1];
+            sp[k].w[1] = a;
+            if (SPIN) {
+                const float b = sm[k].w[0];
+                sm[k].w[0] = sm[k].w[1];
+                sm[k].w[1] = b;
+            }
+        }
+        advance<1, true>(reca, rect, l);
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vplus(int k) const
+    {
+        return SCALED ? sp[k].w[NW] * P::fac(sp[k].E) : sp[k].w[NW];
+    }
+    template <int NW, bool SCALED> __device__ __forceinline__ float vminus(int k) const
+    {
+        return SCALED ? sm[k].w[NW] * P::fac(sm[k].E) : sm[k].w[NW];
+    }
+    // restart before degree l: the table's (lambda_{l-2}, lambda_{l-1}) divided by
+    // (c_{l-2}, c_{l-1}) (cs: the order's (c, 1/c) entries)
+    __device__ __forceinline__ void restart_scaled(const CkTab &ck, int64_t row, int rp0, int nnorth,
+                                                   const float2 *cs, int l)
+    {
+        const float i0 = __ldg(cs + l - 2).y, i1 = __ldg(cs + l - 1).y;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int rp = rp0 + k;
+            if (rp >= nnorth) continue;
+            if (!SPIN) {
+                const float2 v = __ldg((const float2 *)ck.v + row + rp);
+                sp[k].w[0] = v.x * i0; sp[k].w[1] = v.y * i1; sp[k].E = __ldg((const short *)ck.e + row + rp);
+            } else {
+                const float4 v = __ldg((const float4 *)ck.v + row + rp);
+                const short2 e = __ldg((const short2 *)ck.e + row + rp);
+                sp[k].w[0] = v.x * i0; sp[k].w[1] = v.y * i1; sp[k].E = e.x;
+                sm[k].w[0] = v.z * i0; sm[k].w[1] = v.w * i1; sm[k].E = e.y;
             }
         }
     }

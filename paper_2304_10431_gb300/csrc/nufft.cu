@@ -49,6 +49,9 @@ namespace {
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kPi = 3.141592653589793238462643383280;
 constexpr int kSpreadThreads = 64;
+// FP64 tiles hold 64-bit cells (31 KB at W = 13, seven CTAs per SM): 256 threads keep
+// more warps in flight per tile
+constexpr int kSpreadThreads64 = 256;
 
 // Grid coordinate u = t c with c = N / (2 pi) held as a double-double (c.x +
 // c.y): the product's rounding error, ~1e-16 of u (up to N/2 ~ 10^4 cells),
@@ -151,29 +154,57 @@ __device__ __forceinline__ unsigned long long to_fx(double v, double sc)
 }
 
 // FP64 plans: the 2W weights of every (sorted) point, computed once.
-__global__ void k_weights(const double2 *__restrict__ frac, int64_t n, int W, double beta, double *__restrict__ wts)
+// FP64 plans' kernel weights of every point, evaluated in FP64 and kept as
+// doubles or (dd, plans with epsilon >= 5e-11) as double-float pairs (8 bytes
+// each either way): the latter plans compute the interpolation and spreading
+// taps in double-float arithmetic on the FP32 pipe, GB300's FP64 pipe running
+// at 1/60 of it.
+__global__ void k_weights(const double2 *__restrict__ frac, int64_t n, int W, double beta, double *__restrict__ wts,
+                          int dd)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double2 f = frac[p];
     const double twoW = 2.0 / W;
-    double *w = wts + p * 2 * W;
+    double *wd = wts + p * 2 * W;
+    float2 *w = reinterpret_cast<float2 *>(wd);
     for (int a = 0; a < W; ++a) {
-        w[a] = es_kernel<double>(f.x - a, twoW, beta);
-        w[W + a] = es_kernel<double>(f.y - a, twoW, beta);
+        const double x = es_kernel<double>(f.x - a, twoW, beta), y = es_kernel<double>(f.y - a, twoW, beta);
+        if (dd) {
+            const df32 xs = df_split(x), ys = df_split(y);
+            w[a] = make_float2(xs.h, xs.l);
+            w[W + a] = make_float2(ys.h, ys.l);
+        } else {
+            wd[a] = x;
+            wd[W + a] = y;
+        }
     }
 }
 
-template <typename T, int W, bool PRE>
+__device__ __forceinline__ df32 ld_df(const float2 *p)
+{
+    const float2 v = __ldg(p);
+    return {v.x, v.y};
+}
+
+// PRE: 0 evaluate the kernel, 1 read the double weights, 2 the double-float pairs
+template <typename T, int W, int PRE>
 __device__ __forceinline__ void tap_weights(T (&wa)[W], T (&wb)[W], const cplx<T> &f, const double *wts, int64_t p,
                                             T beta)
 {
-    if (PRE) {
+    if (PRE == 1) {
         const double *w = wts + p * 2 * W;
 #pragma unroll
         for (int a = 0; a < W; ++a) {
             wa[a] = (T)__ldg(w + a);
             wb[a] = (T)__ldg(w + W + a);
+        }
+    } else if (PRE == 2) {
+        const float2 *w = reinterpret_cast<const float2 *>(wts) + p * 2 * W;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            wa[a] = (T)df_value(ld_df(w + a));
+            wb[a] = (T)df_value(ld_df(w + W + a));
         }
     } else {
         const T twoW = T(2) / T(W);
@@ -185,7 +216,7 @@ __device__ __forceinline__ void tap_weights(T (&wa)[W], T (&wb)[W], const cplx<T
     }
 }
 
-template <typename T, int W, bool SPIN, bool PRE>
+template <typename T, int W, bool SPIN, int PRE>
 __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                 const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
                                                 const cplx<T> *__restrict__ phase, const double *__restrict__ wts,
@@ -229,6 +260,60 @@ __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, c
     }
 }
 
+// FP64 plans with point weights: the same sums in double-float arithmetic on
+// the FP32 pipe.  The grid holds double-float pairs (k_phi_fwd writes them
+// for these plans: float2 per real, spin s float4 (re h, re l, im h, im l));
+// each row sum adds the exact products of the high words with two-sum and
+// the products' error terms and cross terms in the low word, then the rows
+// are combined the same way; ~2^-46 relative per term.
+template <int W, bool SPIN>
+__global__ void __launch_bounds__(256) k_interp_dd(const void *__restrict__ grid, const uint32_t *__restrict__ cell,
+                                                   const int32_t *__restrict__ perm, const double2 *__restrict__ phase,
+                                                   const double *__restrict__ wts, double *__restrict__ map,
+                                                   int64_t n, int pitch)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t c0 = cell[p];
+    const float2 *w = reinterpret_cast<const float2 *>(wts) + p * 2 * W;
+    df32 wb[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) wb[b] = ld_df(w + W + b);
+    const int32_t dst = perm[p];
+    if (!SPIN) {
+        const float2 *g = reinterpret_cast<const float2 *>(grid) + c0;
+        df32 acc = {0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            df32 r = {0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < W; ++b) df_acc(r, df_mul(wb[b], ld_df(g + (int64_t)a * pitch + b)));
+            df_acc(acc, df_mul(ld_df(w + a), df_renorm(r)));
+        }
+        map[dst] = df_value(acc);
+    } else {
+        const float4 *g = reinterpret_cast<const float4 *>(grid) + c0;
+        df32 ax = {0.f, 0.f}, ay = {0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            df32 rx = {0.f, 0.f}, ry = {0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float4 v = __ldg(g + (int64_t)a * pitch + b);
+                df_acc(rx, df_mul(wb[b], df32{v.x, v.y}));
+                df_acc(ry, df_mul(wb[b], df32{v.z, v.w}));
+            }
+            const df32 wa = ld_df(w + a);
+            df_acc(ax, df_mul(wa, df_renorm(rx)));
+            df_acc(ay, df_mul(wa, df_renorm(ry)));
+        }
+        const double2 ph = phase[p];
+        const double x = df_value(ax), y = df_value(ay);
+        map[dst] = x * ph.x - y * ph.y;
+        map[n + dst] = x * ph.y + y * ph.x;
+    }
+}
+
 // one thread per sorted point, one global atomic per tap (FP64 plans); FX:
 // fixed-point integers into the same grid memory (scale *fxs)
 template <typename T, bool FX> struct Acc {
@@ -244,7 +329,7 @@ __device__ __forceinline__ void acc_add(typename Acc<T, FX>::type *dst, T v, T s
     else atomicAdd(dst, v);
 }
 
-template <typename T, int W, bool SPIN, bool PRE, bool FX>
+template <typename T, int W, bool SPIN, int PRE, bool FX>
 __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                        const cplx<T> *__restrict__ frac,
                                                        const int32_t *__restrict__ perm,
@@ -289,20 +374,42 @@ __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, 
 }
 
 // FX: fixed-point integers in shared memory and in the grid (scale *fxs).
-// I32 (FP32 plans, epsilon >= 1e-5, not FX): the tile accumulates in 32-bit
-// fixed point in shared memory (integer atomics there run ~3x the rate of
-// float atomics), in units of 1/u with u = 2^k per tile, k the largest
-// integer with kmax_t max|x| u <= 2^30: kmax_t (plan time) is the most of the
-// tile's points whose W x W windows cover one cell and max|x| (per call) the
-// map's largest |value| (|Q| + |U| for spin s), taps |psi| <= 1, so no cell
-// sum can overflow.  Every term is rounded once (to 2^-k); the flush converts
-// back to FP32 for one global atomic per non-zero cell.  A map with a
-// non-finite value makes the whole tile NaN.
-template <typename T, bool FX, bool I32> struct SAcc { using type = typename Acc<T, FX>::type; };
-template <typename T> struct SAcc<T, false, true> { using type = int; };
+// IT (integer tiles; FP32 plans at epsilon >= 1e-5 and FP64 plans, not FX):
+// the tile accumulates in fixed point in shared memory, 32-bit integers for
+// FP32 plans (integer atomics there run ~3x the rate of float atomics) and
+// 64-bit for FP64 plans (no FP64 atomics in the inner loop), in units of 1/u
+// with u = 2^k per tile, k the largest integer with kmax_t max|x| u <= 2^30
+// (FP64: 2^62): kmax_t (plan time) is the most of the tile's points whose
+// W x W windows cover one cell and max|x| (per call) the map's largest |value|
+// (|Q| + |U| for spin s), taps |psi| <= 1, so no cell sum can overflow.  Every
+// term is rounded once (to 2^-k; FP64: relative 2^-62 of the tile's bound);
+// the flush converts back for one global atomic per non-zero cell.  A map
+// with a non-finite value makes the whole tile NaN.
+template <typename T, bool FX, bool IT> struct SAcc { using type = typename Acc<T, FX>::type; };
+template <> struct SAcc<float, false, true> { using type = int; };
+template <> struct SAcc<double, false, true> { using type = long long; };
+__device__ __forceinline__ int tile_int(float v) { return __float2int_rn(v); }
+// A double-float term (p, e) with |p| < 2^53 as a 64-bit integer (nearest) without
+// 64-bit conversions (those run at GB300's FP64 rate): p = p1 + p2 with p1 a multiple
+// of 2^31 (|p1| / 2^31 < 2^22, read off the bits of p1 / 2^31 + 1.5 * 2^23) and
+// |p2| <= 2^30 exact, then p2 and e by 32-bit conversions
+__device__ __forceinline__ long long dd_tile_int(df32 t)
+{
+    const float big = 0x1.8p54f;  // 1.5 * 2^54: t.h + big rounds t.h to a multiple of 2^31
+    const float p1 = __fsub_rn(__fadd_rn(t.h, big), big);
+    const int i1 = __float_as_int(__fmaf_rn(p1, 0x1p-31f, 12582912.0f)) - 0x4B400000;
+    const float p2 = __fsub_rn(t.h, p1);
+    return ((long long)i1 << 31) + (long long)__float2int_rn(p2) + (long long)__float2int_rn(t.l);
+}
+__device__ __forceinline__ long long tile_int(double v) { return __double2ll_rn(v); }
+__device__ __forceinline__ void tile_add(int *dst, int v) { atomicAdd(dst, v); }
+__device__ __forceinline__ void tile_add(long long *dst, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);  // two's complement sum
+}
 
-template <typename T, int W, bool SPIN, bool PRE, bool FX, bool I32 = false>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
+template <typename T, int W, bool SPIN, int PRE, bool FX, bool IT = false>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThreads) k_spread(void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                            const cplx<T> *__restrict__ frac,
                                                            const int32_t *__restrict__ perm,
                                                            const cplx<T> *__restrict__ phase,
@@ -313,8 +420,9 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
                                                            int tile_r, const unsigned short *__restrict__ tile_kmax,
                                                            const unsigned long long *__restrict__ maxbits)
 {
-    static_assert(!(I32 && FX), "fixed-point tiles or fixed-point grid");
-    using G = typename SAcc<T, FX, I32>::type;
+    static_assert(!(IT && FX), "fixed-point tiles or fixed-point grid");
+    using G = typename SAcc<T, FX, IT>::type;
+    constexpr bool DD = std::is_same<T, double>::value && IT && PRE == 2;  // double-float taps
     constexpr int TC = kTileC + W - 1, NC = SPIN ? 2 : 1;
     const int TR = tile_r + W - 1;  // tile rows (16, 32 or 64) plus the kernel halo
     extern __shared__ __align__(16) unsigned char spread_smem[];
@@ -323,11 +431,12 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
     const uint32_t p0 = tile_start[t], p1 = tile_start[t + 1];
     if (p0 == p1) return;
     T sc = FX ? (T)fxs[0] : T(1);
-    bool bad = false;  // I32: non-finite map value
-    if constexpr (I32) {
+    bool bad = false;  // IT: non-finite map value
+    if constexpr (IT) {
+        constexpr int kBits = sizeof(T) == 4 ? 30 : DD ? 53 : 62;  // tile sums of |terms| below 2^kBits
         const double bound = (double)tile_kmax[t] * __longlong_as_double((long long)*maxbits);
         if (!(bound < 1e300)) bad = true;  // infinity or NaN in the map
-        else if (bound > 0.0) sc = (T)ldexp(1.0, 30 - (ilogb(bound) + 1));  // bound < 2^(ilogb+1)
+        else if (bound > 0.0) sc = (T)ldexp(1.0, kBits - (ilogb(bound) + 1));  // bound < 2^(ilogb+1)
     }
     for (int i = threadIdx.x; i < TR * TC * NC; i += blockDim.x) buf[i] = G(0);
     __syncthreads();
@@ -336,20 +445,57 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
         const uint32_t c = cell[p];
         const int lr = (int)(c / (uint32_t)pitch) - r0, lc = (int)(c % (uint32_t)pitch) - c0;
         if ((unsigned)lr >= (unsigned)tile_r || (unsigned)lc >= (unsigned)kTileC) continue;  // not this tile's
-        T wa[W], wb[W];
-        tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
         const int32_t src = perm[p];
         // spin s: two planes (real parts, then imaginary parts), so that the lanes'
         // atomics of one plane spread over all 32 banks
         G *b0 = buf + (lr * TC + lc);
+        if constexpr (DD) {
+            // FP64 plans with point weights: the value (times the unit, exact) as a double-float
+            // pair, each tap the double-float product with the pair of weights (~2^-46 relative),
+            // rounded to an integer by dd_tile_int (tile sums of |terms| below 2^53)
+            const float2 *w = reinterpret_cast<const float2 *>(wts) + (int64_t)p * 2 * W;
+            df32 wb[W];
+#pragma unroll
+            for (int b = 0; b < W; ++b) wb[b] = ld_df(w + W + b);
+            if (!SPIN) {
+                const df32 x = df_split(map[src] * sc);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const df32 xa = df_renorm(df_mul(ld_df(w + a), x));
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        tile_add(b0 + a * TC + b, dd_tile_int(df_mul(xa, wb[b])));
+                    }
+                }
+            } else {
+                const cplx<T> ph = phase[p];
+                const T q = map[src], u = map[n + src];
+                const df32 zx = df_split((ph.x * q + ph.y * u) * sc), zy = df_split((ph.x * u - ph.y * q) * sc);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const df32 wa = ld_df(w + a);
+                    const df32 xa = df_renorm(df_mul(wa, zx)), ya = df_renorm(df_mul(wa, zy));
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        G *q2 = b0 + (a * TC + b);
+                        tile_add(q2, dd_tile_int(df_mul(xa, wb[b])));
+                        tile_add(q2 + TR * TC, dd_tile_int(df_mul(ya, wb[b])));
+                    }
+                }
+            }
+            continue;
+        }
+        T wa[W], wb[W];
+        tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
+        // IT: the power-of-two unit sc is applied to the point's value first (exact)
         if (!SPIN) {
-            const T x = map[src];
+            const T x = IT ? map[src] * sc : map[src];
 #pragma unroll
             for (int a = 0; a < W; ++a) {
                 const T xa = wa[a] * x;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    if constexpr (I32) atomicAdd(b0 + a * TC + b, __float2int_rn(xa * wb[b] * sc));
+                    if constexpr (IT) tile_add(b0 + a * TC + b, tile_int(xa * wb[b]));
                     else acc_add<T, FX>(b0 + a * TC + b, xa * wb[b], sc);
                 }
             }
@@ -357,16 +503,17 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
             // e^{-i s chi} (Q + i U)
             const cplx<T> ph = phase[p];
             const T q = map[src], u = map[n + src];
-            const T zx = ph.x * q + ph.y * u, zy = ph.x * u - ph.y * q;
+            T zx = ph.x * q + ph.y * u, zy = ph.x * u - ph.y * q;
+            if constexpr (IT) { zx *= sc; zy *= sc; }
 #pragma unroll
             for (int a = 0; a < W; ++a) {
                 const T xa = wa[a] * zx, ya = wa[a] * zy;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
                     G *q2 = b0 + (a * TC + b);
-                    if constexpr (I32) {
-                        atomicAdd(q2, __float2int_rn(xa * wb[b] * sc));
-                        atomicAdd(q2 + TR * TC, __float2int_rn(ya * wb[b] * sc));
+                    if constexpr (IT) {
+                        tile_add(q2, tile_int(xa * wb[b]));
+                        tile_add(q2 + TR * TC, tile_int(ya * wb[b]));
                     } else {
                         acc_add<T, FX>(q2, xa * wb[b], sc);
                         acc_add<T, FX>(q2 + TR * TC, ya * wb[b], sc);
@@ -376,7 +523,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
         }
     }
     __syncthreads();
-    if constexpr (I32) {
+    if constexpr (IT) {
         T *g = (T *)grid;
         const T inv = bad ? T(NAN) : T(1) / sc;
         for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
@@ -384,33 +531,33 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(void *__restrict__ gr
             if (gr >= R || gc >= pitch) continue;
             const int64_t o = (int64_t)gr * pitch + gc;
             if (!SPIN) {
-                const int v = buf[i];
+                const G v = buf[i];
                 if (v != 0 || bad) atomicAdd(g + o, (T)v * inv);
             } else {
-                const int vx = buf[i], vy = buf[TR * TC + i];
+                const G vx = buf[i], vy = buf[TR * TC + i];
                 if (vx != 0 || bad) atomicAdd(g + 2 * o, (T)vx * inv);
                 if (vy != 0 || bad) atomicAdd(g + 2 * o + 1, (T)vy * inv);
             }
         }
-        return;
-    }
-    G *g = (G *)grid;
-    for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
-        const int gr = r0 + i / TC, gc = c0 + i % TC;
-        if (gr >= R || gc >= pitch) continue;
-        const int64_t o = (int64_t)gr * pitch + gc;
-        if (!SPIN) {
-            const G v = buf[i];
-            if (v != G(0)) atomicAdd(g + o, v);
-        } else {
-            const G vx = buf[i], vy = buf[TR * TC + i];
-            if (vx != G(0)) atomicAdd(g + 2 * o, vx);
-            if (vy != G(0)) atomicAdd(g + 2 * o + 1, vy);
+    } else {
+        G *g = (G *)grid;
+        for (int i = threadIdx.x; i < TR * TC; i += blockDim.x) {
+            const int gr = r0 + i / TC, gc = c0 + i % TC;
+            if (gr >= R || gc >= pitch) continue;
+            const int64_t o = (int64_t)gr * pitch + gc;
+            if (!SPIN) {
+                const G v = buf[i];
+                if (v != G(0)) atomicAdd(g + o, v);
+            } else {
+                const G vx = buf[i], vy = buf[TR * TC + i];
+                if (vx != G(0)) atomicAdd(g + 2 * o, vx);
+                if (vy != G(0)) atomicAdd(g + 2 * o + 1, vy);
+            }
         }
     }
 }
 
-// Plan time, FP32 plans: kmax_t of every tile, the most of the tile's points
+// Plan time (integer-tile plans): kmax_t of every tile, the most of the tile's points
 // whose W x W windows (from their first-tap cell) cover a single cell: counts
 // h per first-tap cell of the tile, then window sums over W rows and W columns
 // for every cell of the tile and its halo.
@@ -516,18 +663,20 @@ cudaError_t interp_w(const Plan &p, const void *grid, void *map, cudaStream_t st
     const int thr = 256;
     const int64_t blocks = (p.npts + thr - 1) / thr;
     if (blocks == 0) return cudaSuccess;
+    const auto run = [&](auto kern) {
+        kern<<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase,
+                                               p.wts, (T *)map, p.npts, p.pitch, (T)p.beta);
+        return cudaGetLastError();
+    };
     if constexpr (std::is_same<T, double>::value) {
-        if (p.wts) {
-            k_interp<T, W, SPIN, true><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
-                                                                         (const cplx<T> *)p.phase, p.wts, (T *)map,
-                                                                         p.npts, p.pitch, (T)p.beta);
+        if (p.wts && p.wts_dd) {  // double-float taps on the double-float grid k_phi_fwd wrote
+            k_interp_dd<W, SPIN><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, p.perm, (const double2 *)p.phase,
+                                                                   p.wts, (double *)map, p.npts, p.pitch);
             return cudaGetLastError();
         }
+        if (p.wts) return run(k_interp<T, W, SPIN, 1>);
     }
-    k_interp<T, W, SPIN, false><<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm,
-                                                                      (const cplx<T> *)p.phase, p.wts, (T *)map,
-                                                                      p.npts, p.pitch, (T)p.beta);
-    return cudaGetLastError();
+    return run(k_interp<T, W, SPIN, 0>);
 }
 
 template <typename T, bool SPIN, int W>
@@ -535,37 +684,41 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
 {
     if (p.npts == 0) return cudaSuccess;
     const double *fxs = p.fx_scale;
+    const size_t cells = (size_t)(p.tile_r + W - 1) * (kTileC + W - 1) * (SPIN ? 2 : 1);
+    const auto run = [&](auto kern, size_t esz) {
+        const size_t sm = cells * esz;
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e2 != cudaSuccess) return e2;
+        kern<<<(unsigned)p.ntiles, sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThreads, sm, st>>>(
+            grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
+            p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+        return cudaGetLastError();
+    };
     if constexpr (std::is_same<T, double>::value) {
+        if (!p.det && p.tile_kmax) {  // 64-bit integer tiles (double-float taps with double-float weights)
+            if (p.wts && p.wts_dd) return run(k_spread<T, W, SPIN, 2, false, true>, 8);
+            if (p.wts) return run(k_spread<T, W, SPIN, 1, false, true>, 8);
+            return run(k_spread<T, W, SPIN, 0, false, true>, 8);
+        }
         const unsigned blocks = (unsigned)((p.npts + 255) / 256);
         const cplx<T> *fr = (const cplx<T> *)p.frac, *ph = (const cplx<T> *)p.phase;
-        if (p.det) {
-            if (p.wts)
-                k_spread_direct<T, W, SPIN, true, true><<<blocks, 256, 0, st>>>(
-                    grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
-            else
-                k_spread_direct<T, W, SPIN, false, true><<<blocks, 256, 0, st>>>(
-                    grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
-        } else if (p.wts) {
-            k_spread_direct<T, W, SPIN, true, false><<<blocks, 256, 0, st>>>(
-                grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
-        } else {
-            k_spread_direct<T, W, SPIN, false, false><<<blocks, 256, 0, st>>>(
-                grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch, (T)p.beta, fxs);
-        }
-    } else {
-        const size_t cells = (size_t)(p.tile_r + W - 1) * (kTileC + W - 1) * (SPIN ? 2 : 1);
-        const auto run = [&](auto kern, size_t esz) {
-            const size_t sm = cells * esz;
-            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e2 != cudaSuccess) return e2;
-            kern<<<(unsigned)p.ntiles, kSpreadThreads, sm, st>>>(
-                grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-                p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+        const auto direct = [&](auto kern) {
+            kern<<<blocks, 256, 0, st>>>(grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch,
+                                         (T)p.beta, fxs);
             return cudaGetLastError();
         };
-        if (p.det) return run(k_spread<T, W, SPIN, false, true>, 8);
-        if (p.tile_kmax) return run(k_spread<T, W, SPIN, false, false, true>, 4);
-        return run(k_spread<T, W, SPIN, false, false>, sizeof(T));
+        if (p.det) {
+            if (p.wts) return p.wts_dd ? direct(k_spread_direct<T, W, SPIN, 2, true>)
+                                       : direct(k_spread_direct<T, W, SPIN, 1, true>);
+            return direct(k_spread_direct<T, W, SPIN, 0, true>);
+        }
+        if (p.wts) return p.wts_dd ? direct(k_spread_direct<T, W, SPIN, 2, false>)
+                                   : direct(k_spread_direct<T, W, SPIN, 1, false>);
+        return direct(k_spread_direct<T, W, SPIN, 0, false>);
+    } else {
+        if (p.det) return run(k_spread<T, W, SPIN, 0, true>, 8);
+        if (p.tile_kmax) return run(k_spread<T, W, SPIN, 0, false, true>, 4);
+        return run(k_spread<T, W, SPIN, 0, false>, sizeof(T));
     }
     return cudaGetLastError();
 }
@@ -629,12 +782,17 @@ cudaError_t launch_spread(const Plan &p, const void *map, void *grid, cudaStream
     if (e != cudaSuccess) return e;
     const bool f32 = p.prec == LENS_FP32;
     if (!p.det) {
-        if (f32 && p.tile_kmax) {  // fixed-point tiles: the map's largest |value| first
+        if (p.tile_kmax) {  // fixed-point tiles: the map's largest |value| first
             if ((e = cudaMemsetAsync(p.maxbits, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
             if (p.npts > 0) {
                 const unsigned mb = (unsigned)std::min<int64_t>((p.npts + 255) / 256, 152 * 8);
-                if (p.spin) k_fx_maxabs<float, true><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
-                else k_fx_maxabs<float, false><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
+                if (f32) {
+                    if (p.spin) k_fx_maxabs<float, true><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
+                    else k_fx_maxabs<float, false><<<mb, 256, 0, st>>>((const float *)map, p.npts, p.maxbits);
+                } else {
+                    if (p.spin) k_fx_maxabs<double, true><<<mb, 256, 0, st>>>((const double *)map, p.npts, p.maxbits);
+                    else k_fx_maxabs<double, false><<<mb, 256, 0, st>>>((const double *)map, p.npts, p.maxbits);
+                }
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;
             }
         }
@@ -731,7 +889,7 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
         k_tile_kmax<<<(unsigned)((p.ntiles + thr - 1) / thr), thr, 0, st>>>(p.tile_start, p.ntiles / ntc, ntc, p.fx_kmax);
         GSL_TRY(cudaGetLastError());
     }
-    if (p.tile_kmax) {  // FP32 fixed-point spreading tiles: kmax_t per tile
+    if (p.tile_kmax) {  // fixed-point spreading tiles: kmax_t per tile
         const size_t sm = sizeof(int) * (size_t)kTileC * (2 * p.tile_r + p.W - 1);
         const auto run = [&](auto kern) {
             kern<<<(unsigned)p.ntiles, 256, sm, st>>>(p.cell, p.pitch, ntc, p.tile_r, p.tile_start, p.tile_kmax);
@@ -754,7 +912,7 @@ cudaError_t launch_prep_points(Plan &p, const double *theta, const double *phi, 
         GSL_TRY(cudaGetLastError());
     }
     if (p.wts) {
-        k_weights<<<blocks, thr, 0, st>>>((const double2 *)p.frac, n, p.W, p.beta, p.wts);
+        k_weights<<<blocks, thr, 0, st>>>((const double2 *)p.frac, n, p.W, p.beta, p.wts, p.wts_dd ? 1 : 0);
         GSL_TRY(cudaGetLastError());
     }
     unsigned hflags = 0;

@@ -495,6 +495,41 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
             const double jr = acos(0.7) / kPi * (nt - 1);
             p->ck.jb = (int)std::ceil(jr / 128.0) * 128;
         }
+        // FP64 plans whose epsilon admits df32 orders: every order in df32 (PolDDR), restarted
+        // every K = 128 degrees from the FP64 recursion, so that no order runs on the FP64 pipe
+        // (1/60 of the FP32 rate on GB300); the FP64 orders of m_df are not needed then
+        const bool mdf_set = prm && prm->legendre_df32_mmin != 0;  // explicit FP64 orders: no restarts
+        // (FP32 plans: the step table's FP32 rounding needs Reinsch's form near the poles; the df32
+        // recursion runs the monic form everywhere, whose rounding grows quadratically with the
+        // degrees since the last restart on rings near the poles, most at low orders: measured
+        // ring-synthesis errors at lmax 2000 with K = 128 for every order: 6e-11 (m < 16),
+        // 8e-12 (16 <= m < 128), 3e-12 (m >= 128); K = 16 / 64 / 128 by those bands: 1.2e-12,
+        // 3.2e-12, 2.7e-12.  So orders below 16 g restart every 16 degrees, below 128 g every 64
+        // and the others every 128, g = lmax / 4096 above lmax 4096 (lmax 8192, epsilon 1e-10:
+        // adjoint eps_eff 1.1e-10 / 1.9e-10 with g = 1 and K = 256 / 512 above m = 128); an
+        // explicit K applies to every order
+        if (prec == LENS_FP64 && want != -1 && !mdf_set && p->m_df <= mmax && epsilon >= 5e-11) {
+            int K = want > 0 ? want : 128;
+            const size_t esz_ck = spin ? 32 : 16;
+            const int g = std::max(1, lmax / 4096);
+            auto k_of = [&](int m, int k) {
+                return want > 0 ? k : std::min(k, m < 16 * g ? 16 : m < 128 * g ? 64 : k);
+            };
+            auto bytes_for = [&](int k) {
+                size_t n = 0;
+                for (int m = 0; m <= mmax; ++m) n += (size_t)ck_count(lmax, std::max(m, spin) + 1, k_of(m, k));
+                return n * p->nnorth * esz_ck;
+            };
+            size_t b = bytes_for(K);
+            while (want == 0 && b > ((size_t)40 << 30) && K < 4096) b = bytes_for(K *= 2);
+            p->rst = true;
+            p->ck.K = K;
+            p->ck_bytes = b;
+            p->ck.jb = 0;
+            p->m_df = 0;
+            p->ck_klog.resize(mmax + 1);
+            for (int m = 0; m <= mmax; ++m) p->ck_klog[m] = (unsigned char)std::log2(k_of(m, K));
+        }
     }
     // ---- Legendre launch shapes: RPT rings per thread; warps per CTA chosen
     // for occupancy of the kernel variant (legendre_shape)
@@ -523,23 +558,29 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         return bailc(e, "alloc rec_t");
     if ((e = B.alloc((void **)&p->scale, (size_t)p->nalm * 8, false)) != cudaSuccess) return bailc(e, "alloc scale");
     if (p->rst) {
-        if ((e = B.alloc(&p->rec_s, (size_t)p->nalm * 16, false)) != cudaSuccess) return bailc(e, "alloc rec_s");
+        if (prec == LENS_FP32 && (e = B.alloc(&p->rec_s, (size_t)p->nalm * 16, false)) != cudaSuccess)
+            return bailc(e, "alloc rec_s");
         std::vector<int64_t> cb(mmax + 1);
         int64_t off = 0;
         for (int m = 0; m <= mmax; ++m) {
             cb[m] = off;
-            off += (int64_t)ck_count(lmax, std::max(m, spin) + 1, p->ck.K) * p->nnorth;
+            const int Km = p->ck_klog.empty() ? p->ck.K : 1 << p->ck_klog[m];
+            off += (int64_t)ck_count(lmax, std::max(m, spin) + 1, Km) * p->nnorth;
         }
         void *d = nullptr;
         if ((e = B.upload(&d, cb)) != cudaSuccess) return bailc(e, "upload restart offsets");
         p->ck.base = (const int64_t *)d;
+        if (!p->ck_klog.empty()) {
+            if ((e = B.upload(&d, p->ck_klog)) != cudaSuccess) return bailc(e, "upload restart intervals");
+            p->ck.klog = (const unsigned char *)d;
+        }
         p->ck.ngrp = (p->nnorth + 31) / 32;
         if ((e = B.alloc(&d, sizeof(short) * (size_t)(mmax + 1) * p->ck.ngrp, false)) != cudaSuccess)
             return bailc(e, "alloc restart starts");
         p->ck.kstart = (const short *)d;
         if (p->ck_bytes > 0) {
-            // values (8 / 16 bytes) and exponents (2 / 4 bytes) per entry
-            const size_t ebytes = p->ck_bytes / 4;
+            // values (FP32 plans 8 / 16 bytes, FP64 plans 16 / 32) and exponents (2 / 4 bytes) per entry
+            const size_t ebytes = p->ck_bytes / (prec == LENS_FP32 ? 4 : 8);
             void *dv = nullptr, *de = nullptr;
             if ((e = B.alloc(&dv, p->ck_bytes, false)) != cudaSuccess || (e = B.alloc(&de, ebytes, false)) != cudaSuccess) {
                 if (e == cudaErrorMemoryAllocation) {
@@ -559,6 +600,13 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
             return bailc(e, "alloc rec_a_df");
     }
     if ((e = B.alloc(&p->coef, (size_t)p->nalm * esz * ncomp, true)) != cudaSuccess) return bailc(e, "alloc coef");
+    if (p->rst && prec == LENS_FP32) {  // monic plain-form rings: c_l a_lm and the (c_l, 1/c_l) table
+        void *d = nullptr;
+        if ((e = B.alloc(&p->coef_m, (size_t)p->nalm * esz * ncomp, true)) != cudaSuccess ||
+            (e = B.alloc(&d, (size_t)p->nalm * sizeof(float2), false)) != cudaSuccess)
+            return bailc(e, "alloc monic coefficients");
+        p->ck.cs = (const float2 *)d;
+    }
     const ScratchSizes scr = plan_scratch_sizes(*p);
     if ((e = B.alloc(&p->ring, scr.ring, true)) != cudaSuccess) return bailc(e, "alloc ring");
     if ((e = B.alloc(&p->X, scr.X, true)) != cudaSuccess) return bailc(e, "alloc X");
@@ -588,9 +636,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         if ((e = B.alloc((void **)&p->tile_start, sizeof(uint32_t) * ((size_t)p->ntiles + 1), false)) != cudaSuccess)
             return bailc(e, "alloc tile table");
         if (spin && (e = B.alloc(&p->phase, esz * npoints, false)) != cudaSuccess) return bailc(e, "alloc phase");
-        // FP32 plans at epsilon >= 1e-5 accumulate the spreading tiles in 32-bit fixed point
-        // (nufft.cu, k_spread); smaller epsilon and deterministic plans keep their own paths
-        if (prec == LENS_FP32 && !p->det && epsilon >= 1e-5) {
+        // FP32 plans at epsilon >= 1e-5 accumulate the spreading tiles in 32-bit fixed point,
+        // FP64 plans in 64-bit fixed point (nufft.cu, k_spread); FP32 plans at smaller epsilon
+        // and deterministic plans keep their own paths
+        if (!p->det && (prec == LENS_FP64 || epsilon >= 1e-5)) {
             if ((e = B.alloc((void **)&p->tile_kmax, sizeof(unsigned short) * (size_t)p->ntiles, false)) != cudaSuccess ||
                 (e = B.alloc((void **)&p->maxbits, sizeof(unsigned long long), true)) != cudaSuccess)
                 return bailc(e, "alloc spreading bounds");
@@ -610,6 +659,10 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
             }
             return bailc(e, "alloc weights");
         }
+        // with the weights kept, FP64 plans at epsilon >= 5e-11 compute the interpolation and
+        // spreading taps in double-float on the FP32 pipe (~2^-46 relative per term; lmax 4096,
+        // 50M points, W = 13: interpolation 30.1 -> 13.4 ms for spin 2); smaller epsilon keeps FP64
+        p->wts_dd = p->wts && epsilon >= 5e-11;
     }
 
     // ---- host tables: start-value norms, rings, deconvolution factors
@@ -694,18 +747,23 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
     if ((e = B.fft(p->fN2, p->N2)) != cudaSuccess) return bailc(e, "fft tables");
 
     if ((e = launch_rec_tables(*p)) != cudaSuccess) return bailc(e, "recursion tables");
-    if (p->rst) {  // step table, then restart values from the FP64 recursion (temporary FP64 tables)
-        if ((e = launch_rec_tables_s(*p)) != cudaSuccess) return bailc(e, "restart step table");
+    if (p->rst) {  // (FP32: step table, then) restart values from the FP64 recursion
+        if (prec == LENS_FP32 && (e = launch_rec_tables_s(*p)) != cudaSuccess) return bailc(e, "restart step table");
         if (p->ck_bytes > 0) {
-            // temporaries: FP64 alpha and tau [nalm] each, first significant degree [mmax + 1][nnorth]
+            // temporaries: FP64 alpha and tau [nalm] each (FP32 plans; FP64 plans have their own),
+            // first significant degree [mmax + 1][nnorth]
             const size_t tb = (size_t)p->nalm * 16 + sizeof(int) * (size_t)(mmax + 1) * p->nnorth;
             double *tmp = nullptr;
             if ((e = cudaMalloc((void **)&tmp, tb)) != cudaSuccess) {
                 cudaGetLastError();
                 return bail(LENS_ERR_NOMEM, "Legendre restart values: temporary tables not available");
             }
-            e = launch_ck_build(*p, tmp, tmp + p->nalm, const_cast<void *>(p->ck.v), const_cast<void *>(p->ck.e),
-                                reinterpret_cast<int *>(tmp + 2 * p->nalm), const_cast<short *>(p->ck.kstart));
+            if (prec == LENS_FP32)
+                e = launch_ck_build(*p, tmp, tmp + p->nalm, const_cast<void *>(p->ck.v), const_cast<void *>(p->ck.e),
+                                    reinterpret_cast<int *>(tmp + 2 * p->nalm), const_cast<short *>(p->ck.kstart));
+            else
+                e = launch_ck_build64(*p, const_cast<void *>(p->ck.v), const_cast<void *>(p->ck.e),
+                                      reinterpret_cast<int *>(tmp + 2 * p->nalm), const_cast<short *>(p->ck.kstart));
             if (e == cudaSuccess) {  // non-negligible triples (the Legendre steps' algorithmic work)
                 std::vector<int> lt((size_t)(mmax + 1) * p->nnorth);
                 e = cudaMemcpyAsync(lt.data(), tmp + 2 * p->nalm, sizeof(int) * lt.size(), cudaMemcpyDeviceToHost,

@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(512, OCC) k_theta_adj(const cplx<T> *__restric
 // spin 0: team = row pair (2b, 2b+1); spin s: team = one row.
 template <typename T, bool SPIN, int CL, int OCC = 1>
 __global__ void __launch_bounds__(512, OCC) k_phi_fwd(const cplx<T> *__restrict__ X, void *__restrict__ grid,
-                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk)
+                                                 FftDesc fN2, int mmax, int ncol, int R, int pitch, int W, int chunk,
+                                                 int dd)
 {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,12 +244,23 @@ __global__ void __launch_bounds__(512, OCC) k_phi_fwd(const cplx<T> *__restrict_
         }
         tm.sync();
         fft_smem<+1, T, CL>(buf, fN2, tm);
-        T *ga = (T *)grid + (int64_t)ra * pitch;
-        T *gb = (T *)grid + (int64_t)rb * pitch;
-        for (int c = tid; c < N2 + W - 1; c += nthr) {
-            C v = buf[c < N2 ? c : c - N2];
-            ga[c] = v.x;
-            if (hb) gb[c] = v.y;
+        if (sizeof(T) == 8 && dd) {  // double-float pairs for k_interp_dd
+            float2 *ga = (float2 *)grid + (int64_t)ra * pitch;
+            float2 *gb = (float2 *)grid + (int64_t)rb * pitch;
+            for (int c = tid; c < N2 + W - 1; c += nthr) {
+                C v = buf[c < N2 ? c : c - N2];
+                const df32 x = df_split((double)v.x), y = df_split((double)v.y);
+                ga[c] = make_float2(x.h, x.l);
+                if (hb) gb[c] = make_float2(y.h, y.l);
+            }
+        } else {
+            T *ga = (T *)grid + (int64_t)ra * pitch;
+            T *gb = (T *)grid + (int64_t)rb * pitch;
+            for (int c = tid; c < N2 + W - 1; c += nthr) {
+                C v = buf[c < N2 ? c : c - N2];
+                ga[c] = v.x;
+                if (hb) gb[c] = v.y;
+            }
         }
     } else {
         const int r = tm.vec();
@@ -259,8 +271,17 @@ __global__ void __launch_bounds__(512, OCC) k_phi_fwd(const cplx<T> *__restrict_
         }
         tm.sync();
         fft_smem<+1, T, CL>(buf, fN2, tm);
-        C *gr = (C *)grid + (int64_t)r * pitch;
-        for (int c = tid; c < N2 + W - 1; c += nthr) gr[c] = buf[c < N2 ? c : c - N2];
+        if (sizeof(T) == 8 && dd) {
+            float4 *gr = (float4 *)grid + (int64_t)r * pitch;
+            for (int c = tid; c < N2 + W - 1; c += nthr) {
+                const C v = buf[c < N2 ? c : c - N2];
+                const df32 x = df_split((double)v.x), y = df_split((double)v.y);
+                gr[c] = make_float4(x.h, x.l, y.h, y.l);
+            }
+        } else {
+            C *gr = (C *)grid + (int64_t)r * pitch;
+            for (int c = tid; c < N2 + W - 1; c += nthr) gr[c] = buf[c < N2 ? c : c - N2];
+        }
     }
     if (CL > 1) tm.sync();
 }
@@ -405,8 +426,9 @@ cudaError_t phi_fwd_t(const Plan &p, const void *X, void *grid, cudaStream_t st)
     const int chunk = (int)(sm / sizeof(C));
     const int nvec = SPIN ? p.R : (p.R + 1) / 2;
     auto args = [&](auto kern) {
+        // FP64 plans with point weights interpolate in double-float: the grid as double-float pairs
         return launch_team(kern, p.cl_phi, nvec, phi_threads(p), sm, st, (const C *)X, grid, p.fN2, p.mmax, p.ncol,
-                           p.R, p.pitch, p.W, chunk);
+                           p.R, p.pitch, p.W, chunk, (sizeof(T) == 8 && p.wts && p.wts_dd) ? 1 : 0);
     };
     if constexpr (sizeof(T) == 4)
         if (p.cl_phi == 1 && sm <= kTwoCtaSmem) return args(k_phi_fwd<T, SPIN, 1, 2>);

@@ -407,7 +407,9 @@ def test_deterministic_adjoint_is_bit_reproducible(spin, grad, prec, eps):
     outs = [det.adjoint(gpu_map(det, y)).cpu().numpy() for _ in range(3)]
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
     a_ref = ref.adjoint(gpu_map(ref, y)).cpu().numpy()
-    assert rel(outs[0], a_ref) <= (1e-6 if prec == "fp32" else 1e-13)
+    # FP64 (epsilon >= 5e-11): the atomic path's spreading taps are double-float products (~2^-46
+    # relative), the deterministic path's FP64 ones: measured 5e-13
+    assert rel(outs[0], a_ref) <= (1e-6 if prec == "fp32" else 2e-12)
     k = np.arange(0, n, 499)
     ys = np.zeros_like(y)
     ys[:, k] = y[:, k]

@@ -175,10 +175,85 @@ def test_restart_selection_and_errors():
     assert LensPlan(300, th, ph, chi, epsilon=1e-5, legendre_restart=-1, device=DEV).info()["legendre_restart"] == 0
     assert LensPlan(300, th, ph, chi, epsilon=5e-6, legendre_restart=32, device=DEV).info()["legendre_restart"] == 32
     assert LensPlan(300, th, ph, chi, epsilon=1e-5, legendre_tables=True, device=DEV).info()["legendre_restart"] == 0
-    assert LensPlan(300, th, ph, chi, epsilon=1e-8, precision="fp64", device=DEV).info()["legendre_restart"] == 0
+    # FP64 plans: double-float restarts every 128 degrees for epsilon >= 5e-11, none below or when the
+    # FP64 orders are set explicitly
+    p64 = LensPlan(300, th, ph, chi, epsilon=1e-8, precision="fp64", device=DEV).info()
+    assert p64["legendre_restart"] == 128 and p64["legendre_df32_mmin"] == 0
+    assert LensPlan(300, th, ph, chi, epsilon=1e-12, precision="fp64", device=DEV).info()["legendre_restart"] == 0
+    assert LensPlan(300, th, ph, chi, epsilon=1e-10, precision="fp64", legendre_restart=-1,
+                    device=DEV).info()["legendre_restart"] == 0
+    assert LensPlan(300, th, ph, chi, epsilon=1e-10, precision="fp64", legendre_df32_mmin=32,
+                    device=DEV).info()["legendre_restart"] == 0
     for bad in (3, 48, 8192, -2):
         with pytest.raises(LensError):
             LensPlan(300, th, ph, chi, epsilon=1e-5, legendre_restart=bad, device=DEV)
     # no restart degree below lmax + 1 - 8 - 64: the table is empty and the kernels run the plain FP32 recursion
     p = LensPlan(60, th, ph, chi, epsilon=1e-5, device=DEV)
     assert p.info()["legendre_restart"] == 64 and p.info()["restart_bytes"] == 0
+
+
+# ------------------------------------------------ FP64 plans: restarted double-float recursion
+@pytest.mark.parametrize("spin", [0, 2])
+@pytest.mark.parametrize("K", [0, 16])
+def test_fp64_restarted_ring_synthesis_vs_oracle(spin, K):
+    """FP64 plans (epsilon >= 5e-11) run every order in double-float, reset to the FP64
+    recursion's values every 16 (m < 16), 64 (m < 128) or 128 degrees (K = 0), or every K degrees:
+    ring synthesis against the oracle and against the same plan geometry without restarts (FP64 low
+    orders, double-float above); the adjoint against the latter."""
+    L = 700
+    th, ph, chi = W.random_points(100, 3)
+    plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-10, precision="fp64", legendre_restart=K, device=DEV)
+    inf = plan.info()
+    assert inf["legendre_restart"] == (K or 128) and inf["restart_bytes"] > 0 and inf["legendre_df32_mmin"] == 0
+    ref_plan = LensPlan(L, th, ph, chi, spin=spin, epsilon=1e-10, precision="fp64", legendre_restart=-1, device=DEV)
+    assert ref_plan.info()["legendre_restart"] == 0 and ref_plan.info()["legendre_df32_mmin"] > 0
+    a = make_alm(L, spin, 15)
+    ta = torch.as_tensor(a, dtype=plan.complex_dtype, device=DEV)
+    ring = plan.ring_synthesis(ta).cpu().numpy()
+    nt = inf["ntheta"]
+    rows = ring_rows(nt)
+    ref = O.ring_coeffs(L, L, spin, rows * math.pi / (nt - 1), a).T
+    # measured at lmax 700 (spin 0): 2e-12 with the default intervals (K = 128 for every order: 3e-11)
+    assert rel(ring[:, rows], ref) < 5e-12
+    per = np.linalg.norm(ring[:, rows] - ref, axis=0) / np.linalg.norm(ref, axis=0).clip(1e-300)
+    assert per.max() < 1e-10
+    assert rel(ring, ref_plan.ring_synthesis(ta).cpu().numpy()) < 5e-12
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(ring.shape) + 1j * rng.standard_normal(ring.shape)
+    tr = torch.as_tensor(r, dtype=plan.complex_dtype, device=DEV)
+    got = plan.ring_adjoint(tr).cpu().numpy()
+    want = ref_plan.ring_adjoint(tr).cpu().numpy()
+    # two double-float evaluations (the reference plan runs its low orders in FP64): measured 1.4e-12
+    assert rel(got, want) < 5e-12
+    plan.close()
+    ref_plan.close()
+
+
+@pytest.mark.parametrize("spin,grad", [(0, False), (2, False), (2, True)])
+def test_fp64_restarted_transform_vs_oracle(spin, grad):
+    """Whole forward and adjoint of a restarted FP64 plan (lmax 1100, restarts at K = 128 past the
+    jump) against the oracle's direct sums at sampled points, epsilon 1e-10."""
+    L, n = 1100, 30000
+    th, ph, chi = W.random_points(n, 70 + spin)
+    th[:4] = [0.0, math.pi, 1e-3, math.pi - 1e-3]
+    plan = LensPlan(L, th, ph, chi if spin else None, spin=spin, epsilon=1e-10, precision="fp64",
+                    grad_only=grad, device=DEV)
+    assert plan.info()["legendre_restart"] == 128
+    a = make_alm(L, spin, 21)
+    if grad:
+        a = a[:1]
+    m = plan.synthesis(torch.as_tensor(a, dtype=plan.complex_dtype, device=DEV)).cpu().numpy()
+    s = np.r_[0:4, 4:n:97]
+    af = a if not grad else np.concatenate([a, np.zeros_like(a)])
+    orc = O.synthesis(L, L, spin, th[s], ph[s], af, chi[s] if spin else None)
+    assert rel(m[:, s], orc) < 1e-10
+    # adjoint of a sparse map against the oracle's adjoint of the same map
+    nc = 1 if spin == 0 else 2
+    y = np.zeros((nc, n))
+    y[:, s] = np.random.default_rng(9).standard_normal((nc, len(s)))
+    got = plan.adjoint(torch.as_tensor(y, dtype=plan.real_dtype, device=DEV)).cpu().numpy()
+    want = O.adjoint(L, L, spin, th[s], ph[s], y[:, s], chi[s] if spin else None)
+    if grad:
+        want = want[:1]
+    assert rel(got, want) < 1e-10
+    plan.close()
