@@ -234,20 +234,28 @@ def stage_units(info, npts, spin, prec):
 def fp64_arithmetic(info):
     """What the FP64 plan's steps compute in (the Legendre part depends on epsilon)."""
     if info["legendre_restart"]:
-        leg = ("double-float (pairs of FP32) Legendre recursion and sums for every order, restarted every %d "
-               "degrees from FP64-recursion values" % info["legendre_restart"])
+        leg = ("double-float (pairs of FP32) Legendre recursion and sums for every order, restarted from "
+               "FP64-recursion values every 16 / 64 / %d degrees (low / middle / other orders)"
+               % info["legendre_restart"])
     else:
         leg = ("FP64 Legendre recursion for orders m < %d, double-float (pairs of FP32) above"
                % info["legendre_df32_mmin"])
-    return leg + "; FP64 FFTs, kernel weights and interpolation/spreading"
+    taps = ("double-float interpolation and spreading taps (64-bit integer spreading tiles)"
+            if info["epsilon"] >= 5e-11 and info["point_weight_bytes"] else "FP64 interpolation and spreading taps")
+    return leg + "; FP64 FFTs and kernel weights; " + taps
 
 
 def kernel_launches(info, prec):
     """Kernels one synthesis + one adjoint launch on a (non-deterministic) plan: synthesis = coefficient
-    preparation, Legendre, theta, phi, interpolation; adjoint = spreading, phi, theta, Legendre; FP64
-    plans with double-float orders split each Legendre step into two launches (memsets not counted)."""
+    preparation (twice for the restarted FP32 recursion: plain and monic coefficients), Legendre, theta,
+    phi, interpolation; adjoint = the map's largest |value| (fixed-point spreading tiles: FP32 plans at
+    epsilon >= 1e-5, FP64 plans), spreading, phi, theta, Legendre; FP64 plans with FP64 low orders split
+    each Legendre step into two launches (memsets not counted)."""
     leg = 2 if (prec == "fp64" and 0 < info["legendre_df32_mmin"] <= info["mmax"]) else 1
-    return (4 + leg) + (3 + leg)
+    prep = 2 if (prec == "fp32" and info["legendre_restart"] and not info["legendre_table_bytes"]) else 1
+    det = bool(info["flags"] & 2)
+    maxabs = 1 if (not det and (prec == "fp64" or info["epsilon"] >= 1e-5)) else 0
+    return (prep + 3 + leg) + (maxabs + 3 + leg)
 
 
 # ------------------------------------------------------------------ ranks

@@ -108,7 +108,8 @@ typedef struct {
     double beta;    /* ES kernel shape parameter */
     int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
     int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1 or 2; also 4
-                              for FP32 plans with the restarted FP32 recursion) */
+                              for FP32 plans with the restarted FP32 recursion; FP64 plans: for
+                              the FP64 and the double-float orders) */
     int legendre_rpt_adj;  /* rings per thread of the adjoint Legendre kernel (as above) */
     int legendre_df32_mmin; /* FP64 plans: orders m >= this value use the double-float Legendre
                                recursion (0 = choose, -1 = never) */

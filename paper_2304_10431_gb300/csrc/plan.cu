@@ -540,7 +540,8 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         (adj ? p->leg_a : p->leg_f) =
             legendre_shape(*p, adj != 0, false, want ? want : legendre_rpt(prec, spin, adj != 0, p->rst));
         if (prec == LENS_FP64)
-            (adj ? p->leg_ad : p->leg_fd) = legendre_shape(*p, adj != 0, true, legendre_rpt_dd(spin, adj != 0));
+            (adj ? p->leg_ad : p->leg_fd) =
+                legendre_shape(*p, adj != 0, true, (want && want <= 2) ? want : legendre_rpt_dd(spin, adj != 0));
     }
     if (prec == LENS_FP32) {  // synthesis of 2 / 4 maps sharing one recursion
         p->leg_fb[0] = legendre_shape(*p, false, false, p->leg_f.rpt, 2);
