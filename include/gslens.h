@@ -458,8 +458,9 @@ int lens_adjoint_host_async(lens_plan p, const void *map_h, void *alm_h, int nma
  * device address is looked up on the first call made on each device, which
  * should therefore come before any stream capture.  Every call shares the
  * array: calls that overlap on the GPU race.  The call still uses the plan's
- * own prepared-coefficient buffer and status flags (allocated when the plan
- * was created), so it must not overlap any other call on the same plan.
+ * own prepared-coefficient buffers (plain and, with the restarted FP32
+ * recursion, monic) and status flags (allocated when the plan was created),
+ * so it must not overlap any other call on the same plan.
  */
 int lens_synthesis_static(lens_plan p, const void *alm_d, void *map_d, void *stream);
 

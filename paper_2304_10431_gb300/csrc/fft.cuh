@@ -340,6 +340,29 @@ __device__ __forceinline__ void twiddle(cplx<T> (&x)[R], const cplx<T> *__restri
     }
 }
 
+// Butterfly b = g Lp + j of a stage, for b = tid, tid + nthr, ...: (g, j) are
+// stepped by (nthr / Lp, nthr % Lp) with one carry instead of a division per
+// butterfly.
+struct BflyIndex {
+    int g, j, dg, dj, Lp;
+    __device__ __forceinline__ BflyIndex(int tid, int nthr, int Lp_) : Lp(Lp_)
+    {
+        g = tid / Lp;
+        j = tid - g * Lp;
+        dg = nthr / Lp;
+        dj = nthr - dg * Lp;
+    }
+    __device__ __forceinline__ void next()
+    {
+        g += dg;
+        j += dj;
+        if (j >= Lp) {
+            j -= Lp;
+            ++g;
+        }
+    }
+};
+
 template <int R, int DIR, typename T, class B>
 __device__ __forceinline__ void fft_stage(const B &buf, int N, int Lp, const cplx<T> *__restrict__ tw, int tid,
                                           int nthr)
@@ -347,9 +370,10 @@ __device__ __forceinline__ void fft_stage(const B &buf, int N, int Lp, const cpl
     const int L = Lp * R;
     const int nb = N / R;
     const int tstep = N / L;
-    for (int b = tid; b < nb; b += nthr) {
-        const int g = b / Lp;
-        const int j = b - g * Lp;
+    BflyIndex ix(tid, nthr, Lp);
+    for (int b = tid; b < nb; b += nthr, ix.next()) {
+        const int g = ix.g;
+        const int j = ix.j;
         const int base = g * L + j;
         cplx<T> x[R];
 #pragma unroll
@@ -410,9 +434,10 @@ __device__ __forceinline__ void fft_stage_dif(const B &buf, int N, int Lp, const
     const int L = Lp * R;
     const int nb = N / R;
     const int tstep = N / L;
-    for (int b = tid; b < nb; b += nthr) {
-        const int g = b / Lp;
-        const int j = b - g * Lp;
+    BflyIndex ix(tid, nthr, Lp);
+    for (int b = tid; b < nb; b += nthr, ix.next()) {
+        const int g = ix.g;
+        const int j = ix.j;
         const int base = g * L + j;
         cplx<T> x[R];
 #pragma unroll

@@ -788,8 +788,11 @@ __global__ void __launch_bounds__(512) k_leg_adj(const typename P::C *__restrict
 }
 
 // Restarted FP32 recursion (see k_leg_fwd32).
+// At most 80 registers: the spin-s kernel (97 registers unconstrained) then keeps 24
+// instead of 16 warps per SM (lmax 4096: spin 2 14.39 -> 13.68 ms, spin 0 5.38 -> 5.26 ms;
+// 96 registers: 13.64 / 5.35 ms).
 template <int RPT, bool SPIN, bool GRAD = false>
-__global__ void __launch_bounds__(512) k_leg_adj32(const float2 *__restrict__ ring, const void *__restrict__ rec_s,
+__global__ void __maxnreg__(80) k_leg_adj32(const float2 *__restrict__ ring, const void *__restrict__ rec_s,
                                                    const double *__restrict__ lognorm, RingTab rt,
                                                    float2 *__restrict__ alm, int lmax, int mmax, int spin, int ntheta,
                                                    int nnorth, int64_t nalm, int m_begin, double wpos,
