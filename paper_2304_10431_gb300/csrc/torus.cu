@@ -28,11 +28,9 @@
 namespace gsl {
 namespace {
 
-__device__ __forceinline__ int pmod(int a, int n)
-{
-    int r = a % n;
-    return r < 0 ? r + n : r;
-}
+// a mod n for -n <= a < 2n (every use: a row r_lo + rr with -W <= r_lo and rr < R < N1,
+// or an order m with |m| <= mmax < N2): one wrap instead of a division
+__device__ __forceinline__ int pmod(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 template <typename C, int CL> __device__ __forceinline__ Buf<C, CL> make_buf(C *local, int chunk);
 // theta transforms: FP32 single-CTA vectors use the padded layout
