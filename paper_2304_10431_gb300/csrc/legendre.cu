@@ -542,9 +542,11 @@ template <class P, int RPT, bool SPIN, bool GRAD = false> struct AdjIn {
 // times the monic scale c_l and the order weight wm, into a_lm (spin 0) or
 // G, C (spin s); with fx (deterministic plans) into the fixed-point sums fx
 // (same layout, units of 1 / fxu) instead.
+// wmf: (float) wm, formed once by the caller, so that FP32 plans without a scale table
+// add their sums with no FP64 arithmetic here.
 template <class P, bool SPIN, int NV>
 __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *out, const double *__restrict__ sc,
-                                      double wm, int64_t base, int64_t nalm, int m, int lb, int lmax,
+                                      double wm, float wmf, int64_t base, int64_t nalm, int m, int lb, int lmax,
                                       decltype(P::fac(0)) sgs, unsigned long long *fx, double fxu)
 {
     using A = typename P::A;
@@ -559,6 +561,12 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
     if (!SPIN) {
         if ((lane & ((1 << SH) - 1)) == 0 && l <= lmax && !(m == 0 && c == 1)) {
             const int64_t dst = 2 * (base + l) + c;
+            if constexpr (std::is_same<typename P::A, float>::value) {
+                if (!sc && !fx) {
+                    atomicAdd(out + dst, tot * wmf);
+                    return;
+                }
+            }
             const double cl = sc ? __ldg(sc + l) : 1.0;
             if (fx) P::atomic_add_fx(fx + dst, tot, cl * wm, fxu);
             else P::atomic_add(out + dst, tot, cl * wm);
@@ -578,6 +586,12 @@ __device__ __forceinline__ void flush(typename P::A (&part)[NV], typename P::R *
             else if (c == 2) { val = P::ascale(P::aadd(other, P::ascale(tot, -sgs)), h); dst = 2 * (nalm + base + l) + 1; }
             else { val = P::ascale(P::aadd(other, P::ascale(tot, sgs)), -h); dst = 2 * (nalm + base + l); }
             if (!(m == 0 && (c == 1 || c == 2))) {
+                if constexpr (std::is_same<typename P::A, float>::value) {
+                    if (!sc && !fx) {
+                        atomicAdd(out + dst, val * wmf);
+                        return;
+                    }
+                }
                 const double cl = sc ? __ldg(sc + l) : 1.0;
                 if (fx) P::atomic_add_fx(fx + dst, val, cl * wm, fxu);
                 else P::atomic_add(out + dst, val, cl * wm);
@@ -597,8 +611,8 @@ template <int NV> constexpr int kRowStride = NV + 4;
 
 template <bool SPIN, int NV>
 __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float *out, const double *__restrict__ sc,
-                                           double wm, int64_t base, int64_t nalm, int m, int lb, int lmax, float sgs,
-                                           unsigned long long *fx, double fxu)
+                                           double wm, float wmf, int64_t base, int64_t nalm, int m, int lb, int lmax,
+                                           float sgs, unsigned long long *fx, double fxu)
 {
     static_assert(NV == 16 || NV == 32, "NV must be 16 or 32");
     constexpr int NCOMP = SPIN ? 4 : 2;
@@ -629,9 +643,8 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
     if (!SPIN) {
         if (lane < NV && l <= lmax && !(m == 0 && c == 1)) {
             const int64_t dst = 2 * (base + l) + c;
-            const double cl = sc ? __ldg(sc + l) : 1.0;
-            if (fx) PolDF::atomic_add_fx(fx + dst, tot, cl * wm, fxu);
-            else atomicAdd(out + dst, tot * (float)(cl * wm));
+            if (fx) PolDF::atomic_add_fx(fx + dst, tot, (sc ? __ldg(sc + l) : 1.0) * wm, fxu);
+            else atomicAdd(out + dst, tot * (sc ? (float)(__ldg(sc + l) * wm) : wmf));
         }
     } else {
         const float other = __shfl_xor_sync(0xffffffffu, tot, 2);  // U <-> V of the same l
@@ -643,9 +656,8 @@ __device__ __forceinline__ void flush_smem(float (&part)[NV], float *wbuf, float
             else if (c == 2) { val = 0.5f * (other - sgs * tot); dst = 2 * (nalm + base + l) + 1; }
             else { val = -0.5f * (other + sgs * tot); dst = 2 * (nalm + base + l); }
             if (!(m == 0 && (c == 1 || c == 2))) {
-                const double cl = sc ? __ldg(sc + l) : 1.0;
-                if (fx) PolDF::atomic_add_fx(fx + dst, val, cl * wm, fxu);
-                else atomicAdd(out + dst, val * (float)(cl * wm));
+                if (fx) PolDF::atomic_add_fx(fx + dst, val, (sc ? __ldg(sc + l) : 1.0) * wm, fxu);
+                else atomicAdd(out + dst, val * (sc ? (float)(__ldg(sc + l) * wm) : wmf));
             }
         }
     }
@@ -705,6 +717,7 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
     R *out = reinterpret_cast<R *>(alm);
     const int lf = l0 + 1;
     const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
+    const float wmf = (float)wm;
     const double fxu = fx ? fxs[1 + m] : 0.0;  // deterministic plans: fixed-point unit of order m
 
     Rings<P, RPT, SPIN> st;
@@ -728,7 +741,7 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
 #pragma unroll
         for (int c = 0; c < NCOMP; ++c) p0[c] = P::azero();
         in.add_rt(st, true, p0);  // l0 = lf - 1
-        flush<P, FSPIN, NCOMP>(p0, out, sc, wm, base, nalm, m, l0, lmax, sgs, fx, fxu);
+        flush<P, FSPIN, NCOMP>(p0, out, sc, wm, wmf, base, nalm, m, l0, lmax, sgs, fx, fxu);
     }
     A part[NV];
     // measured at lmax 4096: spin s 42.8 -> 41.6 ms; spin 0 (16 values per lane)
@@ -756,10 +769,10 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
         if (reg == 0) adj_block<P, RPT, SPIN, 0, GRAD>(st, in, part, reca, rect, l);
         else adj_block<P, RPT, SPIN, 2, GRAD>(st, in, part, reca, rect, l);
         if constexpr (kSmemFlush)
-            flush_smem<FSPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, base, nalm, m, l, lmax, sgs, fx,
+            flush_smem<FSPIN, NV>(part, wbuf, reinterpret_cast<float *>(alm), sc, wm, wmf, base, nalm, m, l, lmax, sgs, fx,
                                   fxu);
         else
-            flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs, fx, fxu);
+            flush<P, FSPIN, NV>(part, out, sc, wm, wmf, base, nalm, m, l, lmax, sgs, fx, fxu);
     }
     if (l <= lmax) {  // tail: fewer than kBlk degrees, general path
 #pragma unroll
@@ -771,7 +784,7 @@ __device__ __forceinline__ void leg_adj_body(const typename P::C *__restrict__ r
                 in.add_rt(st, (j & 1) != 0, part + j * NCOMP);
             }
         }
-        flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, l, lmax, sgs, fx, fxu);
+        flush<P, FSPIN, NV>(part, out, sc, wm, wmf, base, nalm, m, l, lmax, sgs, fx, fxu);
     }
 }
 
@@ -1647,6 +1660,7 @@ __global__ void __launch_bounds__(256) k_tab_adj(const float2 *__restrict__ ring
     const float sgs = (s & 1) ? -1.f : 1.f;
     const int lf = l0 + 1;
     const double wm = (m > 0 ? wpos : 1.0) * (GRAD ? -0.5 : 1.0);
+    const float wmf = (float)wm;
     const double fxu = fx ? fxs[1 + m] : 0.0;
     float *out = reinterpret_cast<float *>(alm);
     AdjIn<P, kTabG, SPIN, GRAD> in;
@@ -1701,9 +1715,9 @@ __global__ void __launch_bounds__(256) k_tab_adj(const float2 *__restrict__ ring
         if (unit == UPB - 1 || !more) {
             const int blk = lb - unit * kTabS;
             if constexpr (FSPIN)
-                flush_smem<FSPIN, NV>(part, wbuf, out, sc, wm, base, nalm, m, blk, lmax, sgs, fx, fxu);
+                flush_smem<FSPIN, NV>(part, wbuf, out, sc, wm, wmf, base, nalm, m, blk, lmax, sgs, fx, fxu);
             else
-                flush<P, FSPIN, NV>(part, out, sc, wm, base, nalm, m, blk, lmax, sgs, fx, fxu);
+                flush<P, FSPIN, NV>(part, out, sc, wm, wmf, base, nalm, m, blk, lmax, sgs, fx, fxu);
         }
     }
 }
