@@ -145,6 +145,16 @@ template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta
     const T q = T(1) - t * t;
     return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
 }
+// FP32: the fast exponential (__expf, a few 1e-7 relative) instead of expf: the FP32 rounding
+// of its argument beta (sqrt(q) - 1), up to |beta| ~ 20, already perturbs the result by ~1e-6
+// relative; interpolation and spreading evaluate the same function, so the pair stays exact
+// transposes of each other
+template <> __device__ __forceinline__ float es_kernel<float>(float z, float twoW, float beta)
+{
+    const float t = z * twoW;
+    const float q = 1.f - t * t;
+    return q > 0.f ? __expf(beta * (sqrtf(q) - 1.f)) : 0.f;
+}
 
 // fixed-point term: v 2^k (exact, 2^k a power of two) rounded to an integer
 __device__ __forceinline__ unsigned long long to_fx(float v, float sc) { return (unsigned long long)__float2ll_rn(v * sc); }
