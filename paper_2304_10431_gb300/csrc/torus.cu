@@ -71,6 +71,29 @@ template <> __device__ __forceinline__ Buf<double2, 4> make_buf<double2, 4>(doub
 // with one (no CTA exits while a partner may still read its part).
 
 // ----------------------------------------------------------------- theta fwd
+// Columns c and c + 1 have opposite parities (-1)^(m+s), so one complex
+// transform serves both: with G = G_a + i G_b (G_a the even, G_b the odd
+// doubled column, the odd column's pole samples zero as its symmetry requires)
+// Z = FFT(G) splits as Z_k = C_a(k) + i C_b(k), Z_-k = C_a(k) - i C_b(k), so
+// C_c(k) = (Z_k + par_c Z_-k) / 2 and (Z_k + par_c Z_-k) / 2i; the weighted
+// coefficients recombine as B_k = b_1(k) + i b_2(k), B_-k = par_1 b_1(k) +
+// i par_2 b_2(k), and the rows of the inverse transform Y = y_1 + i y_2 split
+// the same way, y_c(r) = (Y_r + par_c Y_-r) / 2 (resp. / 2i).  One length-M and
+// one length-N1 transform per pair of columns instead of per column.
+template <typename T> __device__ __forceinline__ cplx<T> pack_i(cplx<T> a, cplx<T> b)  // a + i b
+{
+    return mkc(a.x - b.y, a.y + b.x);
+}
+// (u + p v) / 2 and (u + q v) / 2i for q = -p: the parts of the two columns
+template <typename T>
+__device__ __forceinline__ void split_pair(cplx<T> u, cplx<T> v, T p1, cplx<T> &x1, cplx<T> &x2)
+{
+    const cplx<T> s = mkc(T(0.5) * (u.x + p1 * v.x), T(0.5) * (u.y + p1 * v.y));  // (u + p1 v) / 2
+    const cplx<T> d = mkc(T(0.5) * (u.x - p1 * v.x), T(0.5) * (u.y - p1 * v.y));  // (u + p2 v) / 2, p2 = -p1
+    x1 = s;
+    x2 = mkc(d.y, -d.x);  // d / i
+}
+
 template <typename T, int CL, int OCC = 1>
 __global__ void __launch_bounds__(512, OCC) k_theta_fwd(const cplx<T> *__restrict__ ring, cplx<T> *__restrict__ X,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
@@ -82,46 +105,75 @@ __global__ void __launch_bounds__(512, OCC) k_theta_fwd(const cplx<T> *__restric
     const Team<CL> tm;
     if (CL > 1) tm.sync();
     const auto buf = ThetaBuf<C, CL>::make(reinterpret_cast<C *>(smem_raw), chunk);
-    const int c = tm.vec();
-    const int mc = spin == 0 ? c : c - mmax;
-    const T par = ((mc + spin) & 1) ? T(-1) : T(1);
-    const int M = fM.n, N1 = fN1.n;
+    const int c1 = 2 * tm.vec(), c2 = c1 + 1;
+    const bool has2 = c2 < ncol;
+    const int mc = spin == 0 ? c1 : c1 - mmax;
+    const T p1 = ((mc + spin) & 1) ? T(-1) : T(1), p2 = -p1;
+    const int M = fM.n, N1 = fN1.n, N = ntheta - 1;
     const int tid = tm.tid, nthr = tm.nthr;
-    const C *F = ring + (int64_t)c * ntheta;
+    const C *F1 = ring + (int64_t)c1 * ntheta;
+    const C *F2 = ring + (int64_t)c2 * ntheta;
+    const C zero = mkc(T(0), T(0));
 
     for (int i = tid; i < M; i += nthr) {
-        C v = i < ntheta ? F[i] : cscale(F[M - i], par);
-        buf[__ldg(fM.perm + i)] = v;
+        const int j = i < ntheta ? i : M - i;
+        const bool pole = j == 0 || j == N;
+        C a = F1[j], b = has2 ? F2[j] : zero;
+        if (i >= ntheta) { a = cscale(a, p1); b = cscale(b, p2); }
+        if (pole) { if (p1 < T(0)) a = zero; else b = zero; }
+        buf[__ldg(fM.perm + i)] = pack_i<T>(a, b);
     }
     tm.sync();
-    fft_smem<-1, T, CL>(buf, fM, tm);  // natural order c_k * M
+    fft_smem<-1, T, CL>(buf, fM, tm);  // natural order: Z_k * M
 
-    // move k < 0 from M + k to N1 + k (top first: never overwrites an unread
-    // source, since N1 >= M), scaling every kept k by w1(k) w2(m); when the two
-    // ranges are disjoint (N1 - lmax >= M) in one pass and one barrier (the
-    // zeroing below covers the source range)
-    const T wm = w2[c];
+    // split (k, -k), weight by w1(k) w2(m) per column, recombine at k and N1 - k; the
+    // other positions become zero.  In one pass when the source range of the negative
+    // frequencies [M - lmax, M) lies below their target [N1 - lmax, N1)
+    const T wa = w2[c1], wb = has2 ? w2[c2] : T(0);
+    auto pair_at = [&](int k, C zk, C zm, C &bk, C &bm) {
+        C x1, x2;
+        split_pair<T>(zk, zm, p1, x1, x2);
+        const T wk = w1[k + lmax];
+        x1 = cscale(x1, wk * wa);
+        x2 = cscale(x2, wk * wb);
+        bk = pack_i<T>(x1, x2);
+        bm = pack_i<T>(cscale(x1, p1), cscale(x2, p2));
+    };
     if (N1 - lmax >= M) {
-        for (int k = -1 - tid; k >= -lmax; k -= nthr) buf[N1 + k] = cscale(buf[M + k], w1[k + lmax] * wm);
+        for (int k = tid; k <= lmax; k += nthr) {
+            C bk, bm;
+            pair_at(k, buf[k], buf[k == 0 ? 0 : M - k], bk, bm);
+            buf[k] = bk;
+            if (k > 0) buf[N1 - k] = bm;
+        }
         tm.sync();
+        for (int i = lmax + 1 + tid; i < N1 - lmax; i += nthr) buf[i] = zero;
     } else {
-        for (int k0 = -1; k0 >= -lmax; k0 -= nthr) {
-            const int k = k0 - tid;
-            C v = mkc(T(0), T(0));
-            if (k >= -lmax) v = cscale(buf[M + k], w1[k + lmax] * wm);
+        // overlapping ranges: N1 - k is the source M - k' of k' = k - (N1 - M) <= k, so the
+        // chunks run from k = 0 up
+        for (int k0 = 0; k0 <= lmax; k0 += nthr) {
+            const int k = k0 + tid;
+            C bk = zero, bm = zero;
+            if (k <= lmax) pair_at(k, buf[k], buf[k == 0 ? 0 : M - k], bk, bm);
             tm.sync();
-            if (k >= -lmax) buf[N1 + k] = v;
+            if (k <= lmax) {
+                buf[k] = bk;
+                if (k > 0) buf[N1 - k] = bm;
+            }
             tm.sync();
         }
+        for (int i = lmax + 1 + tid; i < N1 - lmax; i += nthr) buf[i] = zero;
     }
-    for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
-    for (int i = lmax + 1 + tid; i < N1 - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
     tm.sync();
-    fft_smem_dif<+1, T, CL>(buf, fN1, tm);  // y_r at position perm_N1[r]
+    fft_smem_dif<+1, T, CL>(buf, fN1, tm);  // Y_r at position perm_N1[r]
 
     for (int rr = tid; rr < R; rr += nthr) {
         const int r = pmod(r_lo + rr, N1);
-        X[(int64_t)rr * ncol + c] = buf[__ldg(fN1.perm + r)];
+        const int rm = r == 0 ? 0 : N1 - r;
+        C y1, y2;
+        split_pair<T>(buf[__ldg(fN1.perm + r)], buf[__ldg(fN1.perm + rm)], p1, y1, y2);
+        X[(int64_t)rr * ncol + c1] = y1;
+        if (has2) X[(int64_t)rr * ncol + c2] = y2;
     }
     if (CL > 1) tm.sync();
 }
@@ -153,6 +205,11 @@ __global__ void __launch_bounds__(512) k_theta_coeffs(const cplx<T> *__restrict_
 }
 
 // ----------------------------------------------------------------- theta adj
+// Adjoint of the paired forward: the rows of each column are symmetrised first,
+// h~_c(r) = h_c(r) + par_c h_c(-r) (the fold of the forward's doubling moved
+// before the transforms, with which it commutes), packed h~_1 + i h~_2 and
+// split after each transform as in the forward; the even column's pole rings
+// take half of the symmetric result, the odd column's pole rings zero.
 template <typename T, int CL, int OCC = 1>
 __global__ void __launch_bounds__(512, OCC) k_theta_adj(const cplx<T> *__restrict__ X, cplx<T> *__restrict__ ring,
                                                     FftDesc fM, FftDesc fN1, const T *__restrict__ w1,
@@ -164,46 +221,83 @@ __global__ void __launch_bounds__(512, OCC) k_theta_adj(const cplx<T> *__restric
     const Team<CL> tm;
     if (CL > 1) tm.sync();
     const auto buf = ThetaBuf<C, CL>::make(reinterpret_cast<C *>(smem_raw), chunk);
-    const int c = tm.vec();
-    const int mc = spin == 0 ? c : c - mmax;
-    const T par = ((mc + spin) & 1) ? T(-1) : T(1);
-    const int M = fM.n, N1 = fN1.n;
+    const int c1 = 2 * tm.vec(), c2 = c1 + 1;
+    const bool has2 = c2 < ncol;
+    const int mc = spin == 0 ? c1 : c1 - mmax;
+    const T p1 = ((mc + spin) & 1) ? T(-1) : T(1), p2 = -p1;
+    const int M = fM.n, N1 = fN1.n, N = ntheta - 1;
     const int tid = tm.tid, nthr = tm.nthr;
+    const C zero = mkc(T(0), T(0));
 
-    for (int i = tid; i < N1; i += nthr) buf[i] = mkc(T(0), T(0));
-    tm.sync();
-    for (int rr = tid; rr < R; rr += nthr) {
-        const int r = pmod(r_lo + rr, N1);
-        buf[__ldg(fN1.perm + r)] = X[(int64_t)rr * ncol + c];
+    // row r of a column: X[rr] with rr = r - r_lo (mod N1) when rr < R, else zero
+    auto row = [&](int r, int c) -> C {
+        const int rr = pmod(r - r_lo, N1);
+        return rr < R ? X[(int64_t)rr * ncol + c] : zero;
+    };
+    for (int r = tid; r <= N1 / 2; r += nthr) {
+        const int rm = r == 0 ? 0 : N1 - r;
+        const C a = row(r, c1), am = row(rm, c1);
+        const C b = has2 ? row(r, c2) : zero, bm = has2 ? row(rm, c2) : zero;
+        C h1 = cadd(a, cscale(am, p1)), h2 = cadd(b, cscale(bm, p2));
+        if (rm == r) { h1 = cscale(a, T(1) + p1); h2 = cscale(b, T(1) + p2); }
+        buf[__ldg(fN1.perm + r)] = pack_i<T>(h1, h2);
+        if (rm != r) buf[__ldg(fN1.perm + rm)] = pack_i<T>(cscale(h1, p1), cscale(h2, p2));
     }
     tm.sync();
     fft_smem<-1, T, CL>(buf, fN1, tm);  // natural order
 
-    // move k < 0 from N1 + k down to M + k (lowest first), scale by w1 w2; in
-    // one pass without barriers when the ranges are disjoint (N1 - lmax >= M)
-    const T wm = w2[c];
+    // split (k, -k), weight, recombine at k and M - k (positions of the length-M
+    // transform); in one pass when [N1 - lmax, N1) lies above [M - lmax, M)
+    const T wa = w2[c1], wb = has2 ? w2[c2] : T(0);
+    auto pair_at = [&](int k, C zk, C zm, C &bk, C &bm) {
+        C x1, x2;
+        split_pair<T>(zk, zm, p1, x1, x2);
+        const T wk = w1[k + lmax];
+        x1 = cscale(x1, wk * wa);
+        x2 = cscale(x2, wk * wb);
+        bk = pack_i<T>(x1, x2);
+        bm = pack_i<T>(cscale(x1, p1), cscale(x2, p2));
+    };
     if (N1 - lmax >= M) {
-        for (int k = -lmax + tid; k <= -1; k += nthr) buf[M + k] = cscale(buf[N1 + k], w1[k + lmax] * wm);
+        for (int k = tid; k <= lmax; k += nthr) {
+            C bk, bm;
+            pair_at(k, buf[k], buf[k == 0 ? 0 : N1 - k], bk, bm);
+            buf[k] = bk;
+            if (k > 0) buf[M - k] = bm;
+        }
+        tm.sync();
+        for (int i = lmax + 1 + tid; i < M - lmax; i += nthr) buf[i] = zero;
     } else {
-        for (int k0 = -lmax; k0 <= -1; k0 += nthr) {
-            const int k = k0 + tid;
-            C v = mkc(T(0), T(0));
-            if (k <= -1) v = cscale(buf[N1 + k], w1[k + lmax] * wm);
+        // overlapping ranges: M - k is the source N1 - k' of k' = k + N1 - M >= k, so the
+        // chunks run from the highest k down
+        for (int k0 = lmax; k0 >= 0; k0 -= nthr) {
+            const int k = k0 - tid;
+            C bk = zero, bm = zero;
+            if (k >= 0) pair_at(k, buf[k], buf[k == 0 ? 0 : N1 - k], bk, bm);
             tm.sync();
-            if (k <= -1) buf[M + k] = v;
+            if (k >= 0) {
+                buf[k] = bk;
+                if (k > 0) buf[M - k] = bm;
+            }
             tm.sync();
         }
+        for (int i = lmax + 1 + tid; i < M - lmax; i += nthr) buf[i] = zero;
     }
-    for (int k = tid; k <= lmax; k += nthr) buf[k] = cscale(buf[k], w1[k + lmax] * wm);
-    for (int i = lmax + 1 + tid; i < M - lmax; i += nthr) buf[i] = mkc(T(0), T(0));
     tm.sync();
-    fft_smem_dif<+1, T, CL>(buf, fM, tm);  // H_j at position perm_M[j]
+    fft_smem_dif<+1, T, CL>(buf, fM, tm);  // V_j at position perm_M[j]
 
-    C *F = ring + (int64_t)c * ntheta;
+    C *F1 = ring + (int64_t)c1 * ntheta;
+    C *F2 = ring + (int64_t)c2 * ntheta;
     for (int j = tid; j < ntheta; j += nthr) {
-        C v = buf[__ldg(fM.perm + j)];
-        if (j > 0 && j < ntheta - 1) v = cadd(v, cscale(buf[__ldg(fM.perm + (M - j))], par));
-        F[j] = v;
+        const int jm = j == 0 ? 0 : M - j;
+        C g1, g2;
+        split_pair<T>(buf[__ldg(fM.perm + j)], buf[__ldg(fM.perm + jm)], p1, g1, g2);
+        if (j == 0 || j == N) {  // pole rings: half of the symmetric sum (even), zero (odd)
+            g1 = p1 > T(0) ? cscale(g1, T(0.5)) : zero;
+            g2 = p2 > T(0) ? cscale(g2, T(0.5)) : zero;
+        }
+        F1[j] = g1;
+        if (has2) F2[j] = g2;
     }
     if (CL > 1) tm.sync();
 }
@@ -391,7 +485,7 @@ cudaError_t theta_fwd_t(const Plan &p, const void *ring, void *X, cudaStream_t s
     const size_t sm = theta_smem_bytes(p);
     const int chunk = (int)(sm / sizeof(C));
     auto args = [&](auto kern) {
-        return launch_team(kern, p.cl_theta, p.ncol, kThetaThreads, sm, st, (const C *)ring, (C *)X, p.fM, p.fN1,
+        return launch_team(kern, p.cl_theta, (p.ncol + 1) / 2, kThetaThreads, sm, st, (const C *)ring, (C *)X, p.fM, p.fN1,
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
@@ -407,7 +501,7 @@ cudaError_t theta_adj_t(const Plan &p, const void *X, void *ring, cudaStream_t s
     const size_t sm = theta_smem_bytes(p);
     const int chunk = (int)(sm / sizeof(C));
     auto args = [&](auto kern) {
-        return launch_team(kern, p.cl_theta, p.ncol, kThetaThreads, sm, st, (const C *)X, (C *)ring, p.fM, p.fN1,
+        return launch_team(kern, p.cl_theta, (p.ncol + 1) / 2, kThetaThreads, sm, st, (const C *)X, (C *)ring, p.fM, p.fN1,
                            (const T *)p.w1, (const T *)p.w2, p.ntheta, p.lmax, p.mmax, p.spin, p.ncol, p.r_lo, p.R,
                            chunk);
     };
