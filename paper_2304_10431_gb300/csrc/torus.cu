@@ -1,7 +1,8 @@
 // Torus steps of the general SHT (Sect. 3 "doubling" and "FFT", and their
 // adjoints "FFT" and "undoubling").
 //
-// Forward, per m column (theta kernel):
+// Forward, per m column (theta kernel; two adjacent columns of opposite parity
+// share each transform, see k_theta_fwd):
 //   doubled ring sequence G_j, j in [0, M), M = 2 ntheta - 2:
 //       G_j = F_m(theta_j) for j < ntheta,  G_{M-j} = (-1)^{m+s} F_m(theta_j)
 //   (mirror theta -> 2 pi - theta, phi -> phi + pi; odd spins flip sign),
