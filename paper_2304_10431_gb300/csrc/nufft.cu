@@ -52,6 +52,8 @@ constexpr int kSpreadThreads = 64;
 // FP64 tiles hold 64-bit cells (31 KB at W = 13, seven CTAs per SM): 256 threads keep
 // more warps in flight per tile
 constexpr int kSpreadThreads64 = 256;
+// FP64 double-float spreading tiles stage this many points at a time (offset + value pair)
+constexpr int kDDBatch = 512;
 
 // Grid coordinate u = t c with c = N / (2 pi) held as a double-double (c.x +
 // c.y): the product's rounding error, ~1e-16 of u (up to N/2 ~ 10^4 cells),
@@ -451,7 +453,52 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThr
     for (int i = threadIdx.x; i < TR * TC * NC; i += blockDim.x) buf[i] = G(0);
     __syncthreads();
     const int r0 = (t / ntc) * tile_r, c0 = (t % ntc) * kTileC;
-    for (uint32_t p = p0 + threadIdx.x; p < (bad ? p0 : p1); p += blockDim.x) {
+    if constexpr (DD && SPIN) {
+        // FP64 plans with point weights, spin s: work items (point, kernel row) instead of points, so
+        // that the threads of a tile finish together (a tile holds 2-3 points per thread, and
+        // one point per thread more meant a wait at the barrier) and the unrolled body is one
+        // row of W taps.  Per batch of points: each point's value times the unit (exact) as a
+        // double-float pair and its cell offset in shared memory; then the items.  Each tap is
+        // the double-float product of the row value and the weight pair (~2^-46 relative),
+        // rounded to an integer by dd_tile_int (tile sums of |terms| below 2^53).
+        int *soff = reinterpret_cast<int *>(buf + ((TR * TC * NC + 1) & ~1));  // 16-byte aligned
+        float4 *sval = reinterpret_cast<float4 *>(soff + kDDBatch);
+        for (uint32_t pb = p0; pb < (bad ? p0 : p1); pb += kDDBatch) {
+            const int nb = (int)min((uint32_t)kDDBatch, p1 - pb);
+            for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+                const uint32_t p = pb + q;
+                const uint32_t c = cell[p];
+                const int lr = (int)(c / (uint32_t)pitch) - r0, lc = (int)(c % (uint32_t)pitch) - c0;
+                const bool mine = (unsigned)lr < (unsigned)tile_r && (unsigned)lc < (unsigned)kTileC;
+                soff[q] = mine ? lr * TC + lc : -1;
+                if (!mine) continue;
+                const int32_t src = perm[p];
+                const cplx<T> ph = phase[p];
+                const T qv = map[src], u = map[n + src];
+                const df32 zx = df_split((ph.x * qv + ph.y * u) * sc), zy = df_split((ph.x * u - ph.y * qv) * sc);
+                sval[q] = make_float4(zx.h, zx.l, zy.h, zy.l);
+            }
+            __syncthreads();
+            for (int it = threadIdx.x; it < nb * W; it += blockDim.x) {
+                const int q = it / W, a = it - q * W;
+                const int off = soff[q];
+                if (off < 0) continue;
+                const float2 *w = reinterpret_cast<const float2 *>(wts) + (int64_t)(pb + q) * 2 * W;
+                const df32 wa = ld_df(w + a);
+                const float4 v = sval[q];
+                G *row = buf + off + a * TC;
+                const df32 xa = df_renorm(df_mul(wa, df32{v.x, v.y})), ya = df_renorm(df_mul(wa, df32{v.z, v.w}));
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const df32 wb = ld_df(w + W + b);
+                    tile_add(row + b, dd_tile_int(df_mul(xa, wb)));
+                    tile_add(row + b + TR * TC, dd_tile_int(df_mul(ya, wb)));
+                }
+            }
+            __syncthreads();  // the batch's staging is rewritten next
+        }
+    }
+    for (uint32_t p = p0 + threadIdx.x; p < ((bad || (DD && SPIN)) ? p0 : p1); p += blockDim.x) {
         const uint32_t c = cell[p];
         const int lr = (int)(c / (uint32_t)pitch) - r0, lc = (int)(c % (uint32_t)pitch) - c0;
         if ((unsigned)lr >= (unsigned)tile_r || (unsigned)lc >= (unsigned)kTileC) continue;  // not this tile's
@@ -459,39 +506,21 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThr
         // spin s: two planes (real parts, then imaginary parts), so that the lanes'
         // atomics of one plane spread over all 32 banks
         G *b0 = buf + (lr * TC + lc);
-        if constexpr (DD) {
-            // FP64 plans with point weights: the value (times the unit, exact) as a double-float
-            // pair, each tap the double-float product with the pair of weights (~2^-46 relative),
-            // rounded to an integer by dd_tile_int (tile sums of |terms| below 2^53)
+        if constexpr (DD && !SPIN) {
+            // FP64 plans with point weights, spin 0: the value (times the unit, exact) as a
+            // double-float pair, each tap the double-float product with the pair of weights
+            // (~2^-46 relative), rounded to an integer by dd_tile_int (tile sums of |terms|
+            // below 2^53)
             const float2 *w = reinterpret_cast<const float2 *>(wts) + (int64_t)p * 2 * W;
             df32 wb[W];
 #pragma unroll
             for (int b = 0; b < W; ++b) wb[b] = ld_df(w + W + b);
-            if (!SPIN) {
-                const df32 x = df_split(map[src] * sc);
+            const df32 x = df_split(map[src] * sc);
 #pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const df32 xa = df_renorm(df_mul(ld_df(w + a), x));
+            for (int a = 0; a < W; ++a) {
+                const df32 xa = df_renorm(df_mul(ld_df(w + a), x));
 #pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        tile_add(b0 + a * TC + b, dd_tile_int(df_mul(xa, wb[b])));
-                    }
-                }
-            } else {
-                const cplx<T> ph = phase[p];
-                const T q = map[src], u = map[n + src];
-                const df32 zx = df_split((ph.x * q + ph.y * u) * sc), zy = df_split((ph.x * u - ph.y * q) * sc);
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const df32 wa = ld_df(w + a);
-                    const df32 xa = df_renorm(df_mul(wa, zx)), ya = df_renorm(df_mul(wa, zy));
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        G *q2 = b0 + (a * TC + b);
-                        tile_add(q2, dd_tile_int(df_mul(xa, wb[b])));
-                        tile_add(q2 + TR * TC, dd_tile_int(df_mul(ya, wb[b])));
-                    }
-                }
+                for (int b = 0; b < W; ++b) tile_add(b0 + a * TC + b, dd_tile_int(df_mul(xa, wb[b])));
             }
             continue;
         }
@@ -706,6 +735,17 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
     };
     if constexpr (std::is_same<T, double>::value) {
         if (!p.det && p.tile_kmax) {  // 64-bit integer tiles (double-float taps with double-float weights)
+            if (p.wts && p.wts_dd && SPIN) {  // plus the staged points: int offset and float4 value each
+                const size_t extra = (size_t)kDDBatch * (sizeof(int) + sizeof(float4));
+                const auto kern = k_spread<T, W, SPIN, 2, false, true>;
+                const size_t sm = ((cells + 1) & ~(size_t)1) * 8 + extra;
+                cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e2 != cudaSuccess) return e2;
+                kern<<<(unsigned)p.ntiles, kSpreadThreads64, sm, st>>>(
+                    grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map,
+                    p.npts, p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+                return cudaGetLastError();
+            }
             if (p.wts && p.wts_dd) return run(k_spread<T, W, SPIN, 2, false, true>, 8);
             if (p.wts) return run(k_spread<T, W, SPIN, 1, false, true>, 8);
             return run(k_spread<T, W, SPIN, 0, false, true>, 8);
