@@ -15,6 +15,14 @@ constexpr int kMaxFftStages = 24;
 constexpr int kScaleBits = 60;       // exponent step of the scaled Legendre recursion
 constexpr int kLegBlock = 8;         // degrees per unrolled block of the Legendre kernels
 constexpr int kTileR = 32, kTileC = 32;  // default grid tile of the point sort (rows x columns)
+constexpr int kMaxW = 16;                 // largest kernel support
+
+// FP32 plans: the weight of kernel tap a (0 <= a < W) as a polynomial of degree W + 1 in
+// t = 2 frac - (W - 1), t in [-1, 1] (frac = u - ceil(u - W/2) in (W/2 - 1, W/2]);
+// c[a (W + 2) + k] multiplies t^k.  Passed to the NUFFT kernels by value.
+struct KerPoly {
+    float c[kMaxW * (kMaxW + 2)];
+};
 
 // One FFT length: radix sequence (DIT stage order), twiddles e^{-2 pi i t/n}
 // and the digit-reversal table (input element i is stored at position perm[i]).
@@ -91,6 +99,7 @@ struct Plan {
     int N1 = 0, N2 = 0;
     int W = 0;
     double beta = 0, sigma = 0;
+    KerPoly kpoly{};      // FP32 plans: polynomial kernel weights (fitted at plan creation)
     int r_lo = 0, R = 0;  // kept torus rows r in [r_lo, r_lo + R)
     int pitch = 0;        // grid row stride (elements)
     int cl_theta = 1, cl_phi = 1;  // CTAs per FFT vector (2: a cluster sharing the vector)

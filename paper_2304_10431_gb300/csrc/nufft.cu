@@ -147,15 +147,15 @@ template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta
     const T q = T(1) - t * t;
     return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
 }
-// FP32: the fast exponential (__expf, a few 1e-7 relative) instead of expf: the FP32 rounding
-// of its argument beta (sqrt(q) - 1), up to |beta| ~ 20, already perturbs the result by ~1e-6
-// relative; interpolation and spreading evaluate the same function, so the pair stays exact
-// transposes of each other
-template <> __device__ __forceinline__ float es_kernel<float>(float z, float twoW, float beta)
+// FP32 plans: the kernel weight of tap a by Horner's rule in t = 2 frac - (W - 1) from the plan's
+// polynomial coefficients (W + 1 fused multiply-adds; interpolation and spreading read the same
+// coefficients, so the pair stay exact transposes of each other)
+template <int W> __device__ __forceinline__ float ker_poly(const KerPoly &kp, int a, float t)
 {
-    const float t = z * twoW;
-    const float q = 1.f - t * t;
-    return q > 0.f ? __expf(beta * (sqrtf(q) - 1.f)) : 0.f;
+    float acc = kp.c[a * (W + 2) + W + 1];
+#pragma unroll
+    for (int k = W; k >= 0; --k) acc = fmaf(acc, t, kp.c[a * (W + 2) + k]);
+    return acc;
 }
 
 // fixed-point term: v 2^k (exact, 2^k a power of two) rounded to an integer
@@ -202,7 +202,7 @@ __device__ __forceinline__ df32 ld_df(const float2 *p)
 // PRE: 0 evaluate the kernel, 1 read the double weights, 2 the double-float pairs
 template <typename T, int W, int PRE>
 __device__ __forceinline__ void tap_weights(T (&wa)[W], T (&wb)[W], const cplx<T> &f, const double *wts, int64_t p,
-                                            T beta)
+                                            T beta, const KerPoly &kp)
 {
     if (PRE == 1) {
         const double *w = wts + p * 2 * W;
@@ -218,6 +218,13 @@ __device__ __forceinline__ void tap_weights(T (&wa)[W], T (&wb)[W], const cplx<T
             wa[a] = (T)df_value(ld_df(w + a));
             wb[a] = (T)df_value(ld_df(w + W + a));
         }
+    } else if constexpr (std::is_same<T, float>::value) {
+        const float tx = fmaf(2.f, f.x, -(float)(W - 1)), ty = fmaf(2.f, f.y, -(float)(W - 1));
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            wa[a] = ker_poly<W>(kp, a, tx);
+            wb[a] = ker_poly<W>(kp, a, ty);
+        }
     } else {
         const T twoW = T(2) / T(W);
 #pragma unroll
@@ -232,13 +239,14 @@ template <typename T, int W, bool SPIN, int PRE>
 __global__ void __launch_bounds__(256) k_interp(const void *__restrict__ grid, const uint32_t *__restrict__ cell,
                                                 const cplx<T> *__restrict__ frac, const int32_t *__restrict__ perm,
                                                 const cplx<T> *__restrict__ phase, const double *__restrict__ wts,
-                                                T *__restrict__ map, int64_t n, int pitch, T beta)
+                                                T *__restrict__ map, int64_t n, int pitch, T beta,
+                                                const __grid_constant__ KerPoly kp)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t c0 = cell[p];
     T wa[W], wb[W];
-    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
+    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta, kp);
     const int32_t dst = perm[p];
     if (!SPIN) {
         const T *g = (const T *)grid + c0;
@@ -347,7 +355,8 @@ __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, 
                                                        const int32_t *__restrict__ perm,
                                                        const cplx<T> *__restrict__ phase,
                                                        const double *__restrict__ wts, const T *__restrict__ map,
-                                                       int64_t n, int pitch, T beta, const double *__restrict__ fxs)
+                                                       int64_t n, int pitch, T beta, const double *__restrict__ fxs,
+                                                       const __grid_constant__ KerPoly kp)
 {
     using G = typename Acc<T, FX>::type;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(256) k_spread_direct(void *__restrict__ grid, 
     const T sc = FX ? (T)fxs[0] : T(1);
     const uint32_t c0 = cell[p];
     T wa[W], wb[W];
-    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
+    tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta, kp);
     const int32_t src = perm[p];
     if (!SPIN) {
         const T x = map[src];
@@ -430,7 +439,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThr
                                                            const uint32_t *__restrict__ tile_start, T beta,
                                                            const double *__restrict__ fxs,
                                                            int tile_r, const unsigned short *__restrict__ tile_kmax,
-                                                           const unsigned long long *__restrict__ maxbits)
+                                                           const unsigned long long *__restrict__ maxbits,
+                                                           const __grid_constant__ KerPoly kp)
 {
     static_assert(!(IT && FX), "fixed-point tiles or fixed-point grid");
     using G = typename SAcc<T, FX, IT>::type;
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThr
             continue;
         }
         T wa[W], wb[W];
-        tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta);
+        tap_weights<T, W, PRE>(wa, wb, PRE ? cplx<T>{} : frac[p], wts, p, beta, kp);
         // IT: the power-of-two unit sc is applied to the point's value first (exact)
         if (!SPIN) {
             const T x = IT ? map[src] * sc : map[src];
@@ -704,7 +714,7 @@ cudaError_t interp_w(const Plan &p, const void *grid, void *map, cudaStream_t st
     if (blocks == 0) return cudaSuccess;
     const auto run = [&](auto kern) {
         kern<<<(unsigned)blocks, thr, 0, st>>>(grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase,
-                                               p.wts, (T *)map, p.npts, p.pitch, (T)p.beta);
+                                               p.wts, (T *)map, p.npts, p.pitch, (T)p.beta, p.kpoly);
         return cudaGetLastError();
     };
     if constexpr (std::is_same<T, double>::value) {
@@ -730,7 +740,7 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
         if (e2 != cudaSuccess) return e2;
         kern<<<(unsigned)p.ntiles, sizeof(T) == 8 ? kSpreadThreads64 : kSpreadThreads, sm, st>>>(
             grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map, p.npts,
-            p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+            p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits, p.kpoly);
         return cudaGetLastError();
     };
     if constexpr (std::is_same<T, double>::value) {
@@ -743,7 +753,8 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
                 if (e2 != cudaSuccess) return e2;
                 kern<<<(unsigned)p.ntiles, kSpreadThreads64, sm, st>>>(
                     grid, p.cell, (const cplx<T> *)p.frac, p.perm, (const cplx<T> *)p.phase, p.wts, (const T *)map,
-                    p.npts, p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits);
+                    p.npts, p.pitch, p.R, p.ntile_c, p.tile_start, (T)p.beta, fxs, p.tile_r, p.tile_kmax, p.maxbits,
+                    p.kpoly);
                 return cudaGetLastError();
             }
             if (p.wts && p.wts_dd) return run(k_spread<T, W, SPIN, 2, false, true>, 8);
@@ -754,7 +765,7 @@ cudaError_t spread_w(const Plan &p, const void *map, void *grid, cudaStream_t st
         const cplx<T> *fr = (const cplx<T> *)p.frac, *ph = (const cplx<T> *)p.phase;
         const auto direct = [&](auto kern) {
             kern<<<blocks, 256, 0, st>>>(grid, p.cell, fr, p.perm, ph, p.wts, (const T *)map, p.npts, p.pitch,
-                                         (T)p.beta, fxs);
+                                         (T)p.beta, fxs, p.kpoly);
             return cudaGetLastError();
         };
         if (p.det) {
