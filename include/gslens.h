@@ -537,6 +537,16 @@ int lens_profile_reset(void);
 /* Number of a_lm for (lmax, mmax). */
 int64_t lens_nalm(int lmax, int mmax);
 
+/* The polynomial kernel weights FP32 plans evaluate (host only, no device work).
+ * The NUFFT steps of Sect. 3 weight tap a (0 <= a < W) of a point by the ES kernel
+ * phi(x) = exp(beta (sqrt(1 - x^2) - 1)), x = (frac - a) 2 / W, frac = u - ceil(u - W/2) the
+ * point's offset in grid cells.  FP32 plans replace phi by a polynomial of degree W + 1 in
+ * t = 2 frac - (W - 1) per tap, fitted at plan creation (interpolation at the W + 2
+ * Chebyshev points); this call returns those coefficients as the plan stores them:
+ * coef[a (W + 2) + k] multiplies t^k, W (W + 2) floats written (caller-owned).
+ * LENS_ERR_INVALID for W outside [4, 16], beta <= 0 or coef NULL. */
+int lens_kernel_poly(int W, double beta, float *coef);
+
 const char *lens_status_string(int status);
 int lens_get_last_error(void);
 const char *lens_last_error_message(void);

@@ -54,6 +54,7 @@ EXPORTS = {
     "lens_profile_read": (_i32, [_vp, _vp, _i32]),
     "lens_profile_reset": (_i32, []),
     "lens_nalm": (_i64, [_i32, _i32]),
+    "lens_kernel_poly": (_i32, [_i32, _f64, _vp]),
     "lens_status_string": (ctypes.c_char_p, [_i32]),
     "lens_get_last_error": (_i32, []),
     "lens_last_error_message": (ctypes.c_char_p, []),

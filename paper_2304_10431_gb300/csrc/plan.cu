@@ -269,6 +269,15 @@ int64_t lens_nalm(int lmax, int mmax)
     return (int64_t)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
 }
 
+int lens_kernel_poly(int W, double beta, float *coef)
+{
+    if (W < 4 || W > kMaxW || !(beta > 0) || !coef) return fail(LENS_ERR_INVALID, "W in [4, 16], beta > 0, coef");
+    KerPoly kp;
+    ker_poly_fit(W, beta, kp);
+    for (int i = 0; i < W * (W + 2); ++i) coef[i] = kp.c[i];
+    return LENS_OK;
+}
+
 const char *lens_status_string(int s)
 {
     switch (s) {
