@@ -141,12 +141,14 @@ __global__ void k_tile_bounds(const uint32_t *__restrict__ skey, int64_t n, int 
     for (int64_t t = lo + 1; t <= hi; ++t) start[t] = (uint32_t)p;
 }
 
+// the ES kernel of tap offset z (FP64 plans)
 template <typename T> __device__ __forceinline__ T es_kernel(T z, T twoW, T beta)
 {
     const T t = z * twoW;
     const T q = T(1) - t * t;
     return q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
 }
+
 // FP32 plans: the kernel weight of tap a by Horner's rule in t = 2 frac - (W - 1) from the plan's
 // polynomial coefficients (W + 1 fused multiply-adds; interpolation and spreading read the same
 // coefficients, so the pair stay exact transposes of each other)
@@ -165,8 +167,7 @@ __device__ __forceinline__ unsigned long long to_fx(double v, double sc)
     return (unsigned long long)__double2ll_rn(v * sc);
 }
 
-// FP64 plans: the 2W weights of every (sorted) point, computed once.
-// FP64 plans' kernel weights of every point, evaluated in FP64 and kept as
+// FP64 plans' 2W kernel weights of every (sorted) point, computed once, evaluated in FP64 and kept as
 // doubles or (dd, plans with epsilon >= 5e-11) as double-float pairs (8 bytes
 // each either way): the latter plans compute the interpolation and spreading
 // taps in double-float arithmetic on the FP32 pipe, GB300's FP64 pipe running
