@@ -105,7 +105,9 @@ typedef struct lens_plan_s *lens_plan;
 typedef struct {
     double sigma;   /* oversampling factor of the NUFFT grid (1.2 .. 2.5) */
     int W;          /* kernel support in grid cells (4 .. 16) */
-    double beta;    /* ES kernel shape parameter */
+    double beta;    /* ES kernel shape parameter (FP32 plans: LENS_ERR_INVALID if the
+                       polynomial kernel weights, see lens_kernel_poly, miss the kernel by
+                       more than 4 max(e^-beta, 1e-7), e.g. W 4 with beta 16) */
     int ntheta;     /* rings of the equiangular grid (>= lmax + 2) */
     int legendre_rpt_fwd;  /* rings per thread of the Legendre synthesis kernel (1 or 2; also 4
                               for FP32 plans with the restarted FP32 recursion; FP64 plans: for

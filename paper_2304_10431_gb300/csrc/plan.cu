@@ -151,6 +151,23 @@ void ker_poly_fit(int W, double beta, KerPoly &kp)
     }
 }
 
+// Largest |polynomial - phi| over the taps (polynomials evaluated in double at 256 points
+// of t per tap).  With the default beta = pi W (1 - 1/(2 sigma)), sigma <= 2.5, it stays
+// within e^-beta; a beta far from it at small W can leave the interpolant well above that.
+double ker_poly_error(int W, double beta, const KerPoly &kp)
+{
+    double err = 0;
+    for (int a = 0; a < W; ++a)
+        for (int i = 0; i < 256; ++i) {
+            const double t = -1.0 + (i + 0.5) / 128.0;
+            double v = kp.c[a * (W + 2) + W + 1];
+            for (int k = W; k >= 0; --k) v = v * t + kp.c[a * (W + 2) + k];
+            const double x = (0.5 * t + 0.5 * (W - 1) - a) * 2.0 / W, q = 1.0 - x * x;
+            err = std::max(err, std::fabs(v - (q > 0 ? exp(beta * (sqrt(q) - 1.0)) : 0.0)));
+        }
+    return err;
+}
+
 // Kernel support for a target accuracy at oversampling sigma:
 // smallest W with 3 exp(-pi W sqrt(1 - 1/sigma)) <= eps (Barnett et al.'s
 // estimate with a safety factor measured against direct summation).
@@ -491,7 +508,20 @@ int lens_plan_create_ex(lens_plan *out, int lmax, int mmax, int spin, int64_t np
         p->sigma = std::min(s1, s2);
     }
     p->beta = (prm && prm->beta > 0) ? prm->beta : kPi * p->W * (1.0 - 0.5 / p->sigma);
-    if (p->prec == LENS_FP32) ker_poly_fit(p->W, p->beta, p->kpoly);
+    if (p->prec == LENS_FP32) {
+        ker_poly_fit(p->W, p->beta, p->kpoly);
+        // an explicit beta is checked; the default one stays within the kernel's own error
+        // (at W <= 5 with the large sigma of tiny grids, ~1e-4 against the epsilon >= 7e-4
+        // such plans serve)
+        const double err = ker_poly_error(p->W, p->beta, p->kpoly), lim = 4.0 * std::max(exp(-p->beta), 1e-7);
+        if (prm && prm->beta > 0 && err > lim) {
+            char msg[200];
+            snprintf(msg, sizeof msg,
+                     "FP32 plans: beta %.3g at W %d is outside what the polynomial kernel weights reproduce "
+                     "(error %.1e > %.1e); use the default beta or an FP64 plan", p->beta, p->W, err, lim);
+            return bail(LENS_ERR_INVALID, msg);
+        }
+    }
     p->r_lo = -p->W;
     p->R = p->N1 / 2 + 2 * p->W + 1;
     p->pitch = ((p->N2 + p->W - 1) + 31) / 32 * 32;

@@ -66,3 +66,36 @@ def test_polynomial_weights_argument_checks():
     assert lib.lens_kernel_poly(17, 10.0, out.ctypes.data) == 1
     assert lib.lens_kernel_poly(8, 0.0, out.ctypes.data) == 1
     assert lib.lens_kernel_poly(8, 10.0, ctypes.c_void_p()) == 1
+
+
+def horner_f64(c, t):
+    acc = np.full(t.shape, np.float64(c[-1]))
+    for k in range(len(c) - 2, -1, -1):
+        acc = acc * t + np.float64(c[k])
+    return acc
+
+
+@pytest.mark.parametrize("W", list(range(4, 17)))
+def test_default_beta_is_accepted(W):
+    # plan creation refuses an explicit FP32 beta whose polynomials miss phi by more than
+    # 4 max(e^-beta, 1e-7); the default beta = pi W (1 - 1/(2 sigma)) meets that bound with
+    # a factor 2 to spare for every oversampling factor the cost model picks (1.2 .. 2.5)
+    lib = _native.load()
+    t = -1.0 + (np.arange(256) + 0.5) / 128.0
+    for sigma in np.linspace(1.2, 2.5, 14):
+        beta = np.pi * W * (1.0 - 0.5 / sigma)
+        c = kernel_poly(lib, W, beta)
+        err = max(np.abs(horner_f64(c[a], t) - es_kernel((0.5 * t + 0.5 * (W - 1) - a) * 2.0 / W, beta)).max()
+                  for a in range(W))
+        assert err < 0.5 * 4.0 * max(np.exp(-beta), 1e-7), (W, sigma, err)
+
+
+def test_fp32_plan_refuses_a_beta_the_polynomials_cannot_follow():
+    # the check runs before any device work, so it needs no GPU
+    lib = _native.load()
+    h = ctypes.c_void_p()
+    prm = _native.PlanParams(1.5, 4, 16.0, 0, 0, 0, 0, 0, 0, 0, 0, 0)  # sigma, W, beta
+    st = lib.lens_plan_create_ex(ctypes.byref(h), 64, 64, 0, 0, None, None, None, 1e-2, 0, 0, None,
+                                 ctypes.byref(prm))
+    assert st == 1
+    assert b"polynomial kernel weights" in lib.lens_last_error_message()
